@@ -1,0 +1,346 @@
+#!/usr/bin/env python3
+"""Throughput of table-free GMM rANS coding on one GB300.
+
+One step = encode + decode of one synthetic latent of 192 x 32 x 48 =
+294,912 symbols (a 768 x 512 image at stride 16), K = 3 mixture components
+with fp32 parameters, 1024 interleaved rANS streams: per-symbol interval
+kernel, rANS encode, offset scan, compaction, then binary-search decode.
+Inputs are resident in HBM; L2 is flushed (256 MiB write) between steps,
+outside the timed events.
+
+Prints one JSON line. `value` is symbols round-tripped (encoded + decoded)
+per second, summed over ranks; encode and decode rates are reported beside
+it. `--impl reference` times the CPU oracle on the same latent instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(name="latent_192x32x48_k3_s1024", C=192, H=32, W=48, K=3, S=1024, seed=1002)
+# FP32 operations per quantised-CDF evaluation, counted from the definition:
+# per component: z (sub, mul), clamp (2), grid rounding (3), |.|, 1+px (fma),
+# reciprocal, Horner (4 fma), *t, x*x and *-1/2 (2), exp (mul, rint, 2 fma,
+# 7 fma, exponent add), q (mul), mirror (2), weight fma = 32;
+# per evaluation: b = j - 1/2 (2), min(., 1), *T', floor, convert, add (5).
+OPS_PER_COMPONENT = 32
+OPS_PER_EVAL = 7
+FP32_LANES_PER_SM = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="fgmm", choices=["fgmm", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=30)
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.out = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "50",
+                 "-i", str(self.gpu)], stdout=self.out, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.1)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.out.close()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(lat, S, budget_s=8.0):
+    """The CPU oracle (single thread, as it stands) on the same latent."""
+    import oracle
+    t0 = time.perf_counter()
+    reps = 0
+    while True:
+        words, offsets = oracle.encode(lat.params, lat.symbols, S)
+        out, st = oracle.decode(lat.params, words, offsets, S)
+        assert st == 0
+        reps += 1
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": reps * lat.N / dt / 1e6, "unit": "Msymbols/s", "cores": 1, "kind": "oracle",
+            "sample": f"{reps} encode+decode round trip(s) of the full {lat.N}-symbol latent, single thread"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_2509_18815_gb300 import synth
+    import oracle
+    oracle.build()
+    lat = synth.make_latent(WORKLOAD["C"], WORKLOAD["H"], WORKLOAD["W"], WORKLOAD["K"], WORKLOAD["seed"])
+    S = WORKLOAD["S"]
+    for _ in range(args.warmup):
+        w, o = oracle.encode(lat.params, lat.symbols, S)
+        oracle.decode(lat.params, w, o, S)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        w, o = oracle.encode(lat.params, lat.symbols, S)
+        out, st = oracle.decode(lat.params, w, o, S)
+        times.append(time.perf_counter() - t0)
+        assert st == 0
+    ms = 1e3 * sum(times) / len(times)
+    value = lat.N / (ms * 1e-3) / 1e6
+    print(json.dumps({
+        "impl": "reference", "metric": "encode+decode Msymbols/s (round trip)", "value": value,
+        "unit": "Msymbols/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD["name"], "symbols": lat.N, "K": 3, "S": S, "params": "fp32"},
+        "cpu_baseline": {"value": value, "unit": "Msymbols/s", "cores": 1, "kind": "oracle",
+                         "sample": f"each step one encode+decode of the full {lat.N}-symbol latent"},
+        "e2e": {"value": value, "unit": "Msymbols/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def run_fgmm(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2509_18815_gb300 import _abi, build, codec, synth
+    build.build()
+    import ctypes
+
+    lat = synth.make_latent(WORKLOAD["C"], WORKLOAD["H"], WORKLOAD["W"], WORKLOAD["K"], WORKLOAD["seed"])
+    S, N, K = WORKLOAD["S"], lat.N, WORKLOAD["K"]
+    dev = torch.device("cuda", local)
+    dp = torch.from_numpy(lat.params).to(dev)
+    ds = torch.from_numpy(lat.symbols).to(dev)
+    h = codec.handle(dev)
+    desc = codec.latent(dp)
+    cap = codec.encode_bound_words(N, S)
+    words = torch.empty(cap, dtype=torch.int16, device=dev)
+    offsets = torch.empty(S // 32 + 1, dtype=torch.int64, device=dev)
+    total = torch.empty(1, dtype=torch.int64, device=dev)
+    out = torch.empty(N, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream()
+    sptr = ctypes.c_void_p(stream.cuda_stream)
+    L = ctypes.byref(desc)
+
+    def enc():
+        h.check(_abi.fgmm_encode(h.ptr, L, ds.data_ptr(), S, words.data_ptr(), cap, offsets.data_ptr(),
+                                 total.data_ptr(), sptr))
+
+    def dec():
+        h.check(_abi.fgmm_decode(h.ptr, L, words.data_ptr(), cap, offsets.data_ptr(), S, out.data_ptr(), sptr))
+
+    launches_per_step = 4 + 1   # interval, rANS encode, scan, compaction; decode
+
+    # correctness gate and algorithmic work (CDF evaluations) outside timing
+    enc(); dec(); h.sync()
+    assert torch.equal(out.cpu(), ds.cpu()), "round trip failed"
+    n_words = int(total.item())
+    codec.stats_enable(True, h); codec.stats_read(h)
+    dec(); h.sync()
+    cdf_evals, nsym = codec.stats_read(h)
+    codec.stats_enable(False, h)
+
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    for _ in range(max(args.warmup, 3)):
+        enc(); dec()
+    h.sync()
+    if world > 1:
+        dist.barrier()
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    t_wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.fill_(i & 0xff)
+        ev[i][0].record(stream)
+        enc()
+        ev[i][1].record(stream)
+        dec()
+        ev[i][2].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    t_wall = time.perf_counter() - t_wall0
+    clk = clocks.stop()
+    h.sync()
+    t_enc = [ev[i][0].elapsed_time(ev[i][1]) for i in range(args.steps)]
+    t_dec = [ev[i][1].elapsed_time(ev[i][2]) for i in range(args.steps)]
+    ms_enc = sum(t_enc) / len(t_enc)
+    ms_dec = sum(t_dec) / len(t_dec)
+    ms_step = ms_enc + ms_dec
+    if world > 1:
+        t = torch.tensor([ms_step, ms_enc, ms_dec], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step, ms_enc, ms_dec = [float(x) for x in t.tolist()]
+
+    # end to end through the C ABI from pinned host buffers: H2D parameters
+    # and symbols, encode, D2H stream; H2D stream, decode, D2H symbols
+    hp = torch.from_numpy(lat.params).pin_memory()
+    hs = torch.from_numpy(lat.symbols).pin_memory()
+    hw = torch.empty(cap, dtype=torch.int16).pin_memory()
+    ho = torch.empty(S // 32 + 1, dtype=torch.int64).pin_memory()
+    ht = torch.empty(1, dtype=torch.int64).pin_memory()
+    hout = torch.empty(N, dtype=torch.int32).pin_memory()
+    dwords = torch.empty(cap, dtype=torch.int16, device=dev)
+    doff = torch.empty(S // 32 + 1, dtype=torch.int64, device=dev)
+    e2e_t = []
+    h2d = d2h = 0
+    for i in range(args.e2e_steps + 2):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        dp.copy_(hp, non_blocking=True)
+        ds.copy_(hs, non_blocking=True)
+        enc()
+        ht.copy_(total, non_blocking=True)
+        ho.copy_(offsets, non_blocking=True)
+        stream.synchronize()
+        nw = int(ht.item())
+        hw[:nw].copy_(words[:nw], non_blocking=True)
+        dwords[:nw].copy_(hw[:nw], non_blocking=True)
+        doff.copy_(ho, non_blocking=True)
+        h.check(_abi.fgmm_decode(h.ptr, L, dwords.data_ptr(), nw, doff.data_ptr(), S, out.data_ptr(), sptr))
+        hout.copy_(out, non_blocking=True)
+        stream.synchronize()
+        dt = time.perf_counter() - t0
+        if i >= 2:
+            e2e_t.append(dt)
+        h2d = hp.numel() * 4 + hs.numel() * 4 + nw * 2 + ho.numel() * 8
+        d2h = 8 + ho.numel() * 8 + nw * 2 + hout.numel() * 4
+    h.sync()
+    assert torch.equal(hout, hs), "end-to-end round trip failed"
+    e2e_ms = 1e3 * statistics.median(e2e_t)
+    if world > 1:
+        t = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+
+    value = world * N / (ms_step * 1e-3) / 1e6
+    props = torch.cuda.get_device_properties(dev)
+    peaks = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    alu_peak = props.multi_processor_count * FP32_LANES_PER_SM * sm_max * 1e6 / 1e12   # Tops/s
+    ops = cdf_evals * (OPS_PER_COMPONENT * K + OPS_PER_EVAL)
+    achieved = ops / (ms_dec * 1e-3) / 1e12
+    result = {
+        "metric": "encode+decode Msymbols/s (round trip)",
+        "value": value,
+        "unit": "Msymbols/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": max(args.warmup, 3),
+        "ms_per_step": ms_step,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD["name"], "symbols": N, "K": K, "S": S, "params": "fp32",
+                   "l2": "flushed between steps (256 MiB write outside the timed events)"},
+        "encode_msym_s": world * N / (ms_enc * 1e-3) / 1e6,
+        "decode_msym_s": world * N / (ms_dec * 1e-3) / 1e6,
+        "ms_encode": ms_enc,
+        "ms_decode": ms_dec,
+        "bits_per_symbol": 16.0 * n_words / N,
+        "cdf_evals_per_symbol": cdf_evals / max(nsym, 1),
+        "gpu_launches": launches_per_step * args.steps,
+        "wall_s_timed_region": t_wall,
+        "e2e": {"value": world * N / (e2e_ms * 1e-3) / 1e6, "unit": "Msymbols/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "roofline": {"kernel": "fgmm_rans_dec_kernel", "bound": "alu", "achieved": achieved, "peak": alu_peak,
+                     "unit": "Tops/s (FP32 lane ops)", "frac": achieved / alu_peak, "traffic": None,
+                     "peak_source": f"derived: {props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
+                                    f"{sm_max:.0f} MHz"},
+        "clocks": clk,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        result["cpu_baseline"] = cpu_baseline(lat, S)
+    if rank == 0:
+        print(json.dumps(result))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_fgmm(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,88 @@
+"""ctypes declarations of the C ABI in include/fgmm.h (libfgmm.so).
+
+Argument marshalling only: every computation happens in the CUDA library.
+Loading fails loudly if the library has not been built; there is no
+fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libfgmm.so")
+
+FGMM_OK = 0
+FGMM_ERR_INVALID_ARG = 1
+FGMM_ERR_BAD_PARAMS = 2
+FGMM_ERR_CAPACITY = 3
+FGMM_ERR_CORRUPT = 4
+FGMM_ERR_TIMEOUT = 5
+FGMM_ERR_CUDA = 6
+FGMM_ERR_NO_MEMORY = 7
+FGMM_DTYPE_F32 = 0
+FGMM_DTYPE_BF16 = 1
+FGMM_MAX_K = 4
+
+
+class fgmm_latent(ctypes.Structure):
+    _fields_ = [("K", ctypes.c_int32), ("dtype", ctypes.c_int32), ("N", ctypes.c_int64),
+                ("params", ctypes.c_void_p)]
+
+
+P = ctypes.c_void_p
+I32 = ctypes.c_int32
+I64 = ctypes.c_int64
+LATP = ctypes.POINTER(fgmm_latent)
+
+# name -> (restype, argtypes); every function include/fgmm.h declares.
+SIGNATURES = {
+    "fgmm_create": (I32, [ctypes.POINTER(P)]),
+    "fgmm_destroy": (None, [P]),
+    "fgmm_status_string": (ctypes.c_char_p, [I32]),
+    "fgmm_last_error": (ctypes.c_char_p, [P]),
+    "fgmm_sync_status": (I32, [P, P]),
+    "fgmm_phi": (I32, [P, P, P, I64, P]),
+    "fgmm_phi_grid": (I32, [P, I64, P, I64, P]),
+    "fgmm_freqs": (I32, [P, LATP, P, P, P]),
+    "fgmm_encode_bound_words": (I64, [I64, I32]),
+    "fgmm_encode": (I32, [P, LATP, P, I32, P, I64, P, P, P]),
+    "fgmm_decode": (I32, [P, LATP, P, I64, P, I32, P, P]),
+    "fgmm_stats_enable": (I32, [P, I32]),
+    "fgmm_stats_read": (I32, [P, P, P]),
+}
+
+_lib = None
+
+
+class FgmmError(RuntimeError):
+    def __init__(self, status: int, msg: str = ""):
+        self.status = status
+        super().__init__(f"fgmm status {status}: {msg}")
+
+
+def lib():
+    """The loaded libfgmm.so (raises if it is missing)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libfgmm.so not built at {LIB_PATH}; run __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _bind(name):
+    def call(*args):
+        return getattr(lib(), name)(*args)
+    call.__name__ = name
+    call.__doc__ = f"C ABI entry point {name} (include/fgmm.h)."
+    return call
+
+
+for _name in SIGNATURES:
+    globals()[_name] = _bind(_name)

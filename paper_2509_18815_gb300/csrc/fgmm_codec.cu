@@ -1,0 +1,570 @@
+// fgmm_codec.cu -- table-free GMM rANS encode / decode for sm_103a.
+//
+// Encode (Sec. III-A: evaluate the CDF at the coded symbol, then rANS, Eq. 3)
+// runs in four launches:
+//   1. fgmm_interval_kernel: one thread per symbol computes the symbol's
+//      quantised-CDF interval (start, freq). Fully data-parallel over N.
+//   2. fgmm_rans_enc_kernel: one warp per 32-stream segment, one lane per
+//      stream, steps T-1 .. 0. The sequential part is integer-only; the
+//      renormalisation words of a sub-phase are compacted with a warp ballot
+//      and popc rank and appended to the segment's scratch buffer.
+//   3. fgmm_scan_kernel: exclusive prefix sum of the segment lengths.
+//   4. fgmm_compact_kernel: copies segments to their offsets.
+// Decode (Sec. III-A: binary search over the same on-the-fly CDF) is one
+// launch, fgmm_rans_dec_kernel: one warp per segment, one lane per stream,
+// steps 0 .. T-1, each step a binary search over the symbol's quantised CDF
+// followed by the inverse rANS step and a ballot-ranked backward refill.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstring>
+
+#include "fgmm_device.cuh"
+#include "fgmm_internal.h"
+
+using namespace fgmm;
+
+namespace {
+
+constexpr uint32_t kFull = 0xffffffffu;
+
+// ---------------------------------------------------------------------------
+// Phi-hat evaluation (tests and sweeps).
+// ---------------------------------------------------------------------------
+__global__ void phi_kernel(const float* __restrict__ z, float* __restrict__ out, int64_t n)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = phi_hat(z[i]);
+}
+
+__global__ void phi_grid_kernel(int64_t i0, float* __restrict__ out, int64_t n)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = phi_hat(__fmul_rn((float)(i0 + i), 0x1p-22f));
+}
+
+// ---------------------------------------------------------------------------
+// 1. Intervals: sf[n] = start | freq << 16.
+// ---------------------------------------------------------------------------
+template <int K, typename T>
+__global__ void __launch_bounds__(256) fgmm_interval_kernel(const T* __restrict__ params, int64_t N,
+                                                            const int32_t* __restrict__ sym,
+                                                            uint32_t* __restrict__ sf, int32_t* err)
+{
+    for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x) {
+        Mix<K> m;
+        if (!load_mix<K>(params, N, n, m)) set_error(err, kErrBadParams);
+        uint32_t st, fr;
+        interval_of<K>(m, __ldg(sym + n), st, fr);
+        sf[n] = st | (fr << 16);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// 2. Interleaved rANS encoder, one warp per segment.
+// ---------------------------------------------------------------------------
+
+// Codes (start, freq) on the lanes where `part` holds. Lanes whose state
+// would overflow first emit their low 16 bits; the words of the sub-phase
+// land in ascending lane order at out[base ...].
+__device__ __forceinline__ void enc_put(uint32_t& x, uint32_t start, uint32_t freq, bool part,
+                                        uint16_t* __restrict__ out, int64_t& base, uint32_t lt)
+{
+    const bool need = part && x >= (freq << 16);
+    const uint32_t m = __ballot_sync(kFull, need);
+    if (need) {
+        out[base + __popc(m & lt)] = (uint16_t)(x & 0xffffu);
+        x >>= 16;
+    }
+    base += __popc(m);
+    if (part) {
+        const uint32_t q = x / freq;
+        x = (q << 16) + (x - q * freq) + start;
+    }
+}
+
+__global__ void __launch_bounds__(64) fgmm_rans_enc_kernel(const uint32_t* __restrict__ sf,
+                                                           const int32_t* __restrict__ sym, int64_t N, int32_t S,
+                                                           int64_t T, uint16_t* __restrict__ seg_words,
+                                                           int64_t seg_cap, int64_t* __restrict__ seg_len,
+                                                           int64_t nseg)
+{
+    const int64_t g = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (g >= nseg) return;
+    uint16_t* out = seg_words + g * seg_cap;
+    const uint32_t lt = lanemask_lt();
+    uint32_t x = kL;
+    int64_t base = 0;
+    int64_t n = (T - 1) * (int64_t)S + g * 32 + lane;
+    for (int64_t t = T - 1; t >= 0; --t, n -= S) {
+        const bool act = n < N;
+        const uint32_t v = act ? __ldg(sf + n) : 0u;
+        const uint32_t start = v & 0xffffu, freq = v >> 16;
+        const bool esc = act && (start + freq == kM);
+        if (__ballot_sync(kFull, esc)) {
+            const uint32_t raw = esc ? (uint32_t)__ldg(sym + n) : 0u;
+            enc_put(x, raw & 0xffffu, 1u, esc, out, base, lt);
+            enc_put(x, raw >> 16, 1u, esc, out, base, lt);
+        }
+        enc_put(x, start, freq, act, out, base, lt);
+    }
+    out[base + 2 * lane] = (uint16_t)(x & 0xffffu);
+    out[base + 2 * lane + 1] = (uint16_t)(x >> 16);
+    if (lane == 0) seg_len[g] = base + 64;
+}
+
+// ---------------------------------------------------------------------------
+// 3. Exclusive prefix sum of segment lengths (one block).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) fgmm_scan_kernel(const int64_t* __restrict__ seg_len, int64_t nseg,
+                                                         int64_t* __restrict__ offsets, int64_t* total_out,
+                                                         int64_t cap, int32_t* err)
+{
+    __shared__ int64_t warp_tot[32];
+    __shared__ int64_t carry;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    if (tid == 0) carry = 0;
+    __syncthreads();
+    for (int64_t base = 0; base < nseg; base += blockDim.x) {
+        const int64_t i = base + tid;
+        const int64_t v = i < nseg ? seg_len[i] : 0;
+        int64_t inc = v;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int64_t o = __shfl_up_sync(kFull, inc, d);
+            if (lane >= d) inc += o;
+        }
+        if (lane == 31) warp_tot[wid] = inc;
+        __syncthreads();
+        if (wid == 0) {
+            const int nw = blockDim.x >> 5;
+            int64_t w = lane < nw ? warp_tot[lane] : 0;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const int64_t o = __shfl_up_sync(kFull, w, d);
+                if (lane >= d) w += o;
+            }
+            if (lane < nw) warp_tot[lane] = w;   // inclusive over warps
+        }
+        __syncthreads();
+        const int64_t before = carry + (wid > 0 ? warp_tot[wid - 1] : 0);
+        if (i < nseg) offsets[i] = before + inc - v;
+        __syncthreads();
+        if (tid == blockDim.x - 1) carry = before + inc;
+        __syncthreads();
+    }
+    if (tid == 0) {
+        offsets[nseg] = carry;
+        *total_out = carry;
+        if (carry > cap) set_error(err, kErrCapacity);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// 4. Segment compaction: one warp per segment.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) fgmm_compact_kernel(const uint16_t* __restrict__ seg_words, int64_t seg_cap,
+                                                           const int64_t* __restrict__ seg_len,
+                                                           const int64_t* __restrict__ offsets, int64_t nseg,
+                                                           uint16_t* __restrict__ words, int64_t cap)
+{
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    for (int64_t g = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; g < nseg; g += nwarps) {
+        const int64_t len = seg_len[g], dst = offsets[g];
+        if (dst + len > cap) continue;   // capacity error already recorded
+        const uint16_t* src = seg_words + g * seg_cap;
+        for (int64_t i = lane; i < len; i += 32) words[dst + i] = src[i];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Decoder, one warp per segment.
+// ---------------------------------------------------------------------------
+
+// Refill after a decode sub-phase: the lanes (among `part`) whose state fell
+// below 2^16 take the last c unread words, the lane of rank r word ptr-c+r.
+// A read below the segment start is never performed; it marks the stream bad.
+__device__ __forceinline__ void dec_refill(uint32_t& x, bool part, const uint16_t* __restrict__ words,
+                                           int64_t& ptr, int64_t beg, bool& bad, uint32_t lt)
+{
+    const bool need = part && x < kL;
+    const uint32_t m = __ballot_sync(kFull, need);
+    if (m) {
+        const int c = __popc(m);
+        if (need) {
+            const int64_t idx = ptr - c + __popc(m & lt);
+            uint32_t w = 0;
+            if (idx >= beg) w = __ldg(words + idx);
+            else bad = true;
+            x = (x << 16) | w;
+        }
+        ptr -= c;
+    }
+}
+
+template <int K, typename T>
+__global__ void __launch_bounds__(64) fgmm_rans_dec_kernel(const T* __restrict__ params, int64_t N, int32_t S,
+                                                           int64_t T_steps, const uint16_t* __restrict__ words,
+                                                           int64_t n_words, const int64_t* __restrict__ offsets,
+                                                           int64_t nseg, int32_t* __restrict__ out, int32_t* err,
+                                                           unsigned long long* stats)
+{
+    const int64_t g = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (g >= nseg) return;
+    const int64_t beg = offsets[g], end = offsets[g + 1];
+    if (!(beg >= 0 && end <= n_words && end - beg >= 64)) {
+        if (lane == 0) set_error(err, kErrCorrupt);
+        return;
+    }
+    const uint32_t lt = lanemask_lt();
+    uint32_t x = (uint32_t)__ldg(words + end - 64 + 2 * lane) | ((uint32_t)__ldg(words + end - 63 + 2 * lane) << 16);
+    int64_t ptr = end - 64;
+    bool bad = false, badp = false;
+    int probes = 0, decoded = 0;
+    int64_t n = g * 32 + lane;
+    for (int64_t t = 0; t < T_steps; ++t, n += S) {
+        const bool act = n < N;
+        int32_t s = 0;
+        bool esc = false;
+        if (act) {
+            ++decoded;
+            Mix<K> m;
+            badp |= !load_mix<K>(params, N, n, m);
+            const uint32_t slot = x & 0xffffu;
+            uint32_t st, fr;
+            esc = search_slot<K>(m, slot, s, st, fr, probes);
+            x = fr * (x >> 16) + slot - st;
+        }
+        dec_refill(x, act, words, ptr, beg, bad, lt);
+        if (__ballot_sync(kFull, esc)) {
+            uint32_t hi16 = 0, lo16 = 0;
+            if (esc) { hi16 = x & 0xffffu; x >>= 16; }
+            dec_refill(x, esc, words, ptr, beg, bad, lt);
+            if (esc) { lo16 = x & 0xffffu; x >>= 16; }
+            dec_refill(x, esc, words, ptr, beg, bad, lt);
+            if (esc) s = (int32_t)((hi16 << 16) | lo16);
+        }
+        if (act) out[n] = s;
+    }
+    const bool fail = bad || x != kL || ptr != beg;
+    if (__ballot_sync(kFull, fail) && lane == 0) set_error(err, kErrCorrupt);
+    if (__ballot_sync(kFull, badp) && lane == 0) set_error(err, kErrBadParams);
+    if (stats) {
+        int p = probes, d = decoded;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            p += __shfl_xor_sync(kFull, p, o);
+            d += __shfl_xor_sync(kFull, d, o);
+        }
+        if (lane == 0) {
+            atomicAdd(stats, (unsigned long long)p);
+            atomicAdd(stats + 1, (unsigned long long)d);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Host-side dispatch helpers.
+// ---------------------------------------------------------------------------
+inline int grid_for(int64_t n, int threads, int max_blocks)
+{
+    int64_t b = (n + threads - 1) / threads;
+    if (b < 1) b = 1;
+    if (b > max_blocks) b = max_blocks;
+    return (int)b;
+}
+
+template <int K, typename T>
+void launch_interval(const fgmm_latent* lat, const int32_t* sym, uint32_t* sf, int32_t* err, int sms,
+                     cudaStream_t st)
+{
+    if (lat->N == 0) return;
+    const int threads = 256;
+    fgmm_interval_kernel<K, T><<<grid_for(lat->N, threads, sms * 16), threads, 0, st>>>(
+        static_cast<const T*>(lat->params), lat->N, sym, sf, err);
+}
+
+template <typename T>
+void dispatch_interval(const fgmm_latent* lat, const int32_t* sym, uint32_t* sf, int32_t* err, int sms,
+                       cudaStream_t st)
+{
+    switch (lat->K) {
+    case 1: launch_interval<1, T>(lat, sym, sf, err, sms, st); break;
+    case 2: launch_interval<2, T>(lat, sym, sf, err, sms, st); break;
+    case 3: launch_interval<3, T>(lat, sym, sf, err, sms, st); break;
+    default: launch_interval<4, T>(lat, sym, sf, err, sms, st); break;
+    }
+}
+
+void launch_interval_any(const fgmm_latent* lat, const int32_t* sym, uint32_t* sf, int32_t* err, int sms,
+                         cudaStream_t st)
+{
+    if (lat->dtype == FGMM_DTYPE_BF16) dispatch_interval<__nv_bfloat16>(lat, sym, sf, err, sms, st);
+    else dispatch_interval<float>(lat, sym, sf, err, sms, st);
+}
+
+// Warps per block for the per-segment kernels: one warp per block while the
+// segments do not fill the SMs, so that each warp has an SM to itself.
+inline int seg_threads(int64_t nseg, int sms) { return nseg <= 2 * (int64_t)sms ? 32 : 64; }
+
+template <int K, typename T>
+void launch_dec(const fgmm_latent* lat, int32_t S, const uint16_t* words, int64_t n_words, const int64_t* offsets,
+                int32_t* out, int32_t* err, unsigned long long* stats, int sms, cudaStream_t st)
+{
+    const int64_t nseg = S / 32;
+    const int64_t steps = (lat->N + S - 1) / S;
+    const int threads = seg_threads(nseg, sms);
+    const int64_t blocks = (nseg * 32 + threads - 1) / threads;
+    fgmm_rans_dec_kernel<K, T><<<(unsigned)blocks, threads, 0, st>>>(static_cast<const T*>(lat->params), lat->N, S,
+                                                                      steps, words, n_words, offsets, nseg, out, err,
+                                                                      stats);
+}
+
+template <typename T>
+void dispatch_dec(const fgmm_latent* lat, int32_t S, const uint16_t* words, int64_t n_words, const int64_t* offsets,
+                  int32_t* out, int32_t* err, unsigned long long* stats, int sms, cudaStream_t st)
+{
+    switch (lat->K) {
+    case 1: launch_dec<1, T>(lat, S, words, n_words, offsets, out, err, stats, sms, st); break;
+    case 2: launch_dec<2, T>(lat, S, words, n_words, offsets, out, err, stats, sms, st); break;
+    case 3: launch_dec<3, T>(lat, S, words, n_words, offsets, out, err, stats, sms, st); break;
+    default: launch_dec<4, T>(lat, S, words, n_words, offsets, out, err, stats, sms, st); break;
+    }
+}
+
+inline int64_t steps_of(int64_t N, int32_t S) { return N > 0 ? (N + S - 1) / S : 0; }
+
+// Per-segment scratch capacity: at most three words per lane and step (an
+// escape emits for two chunks and the main symbol) plus the flush block;
+// rounded to 8 words so that every segment starts 16-byte aligned.
+inline int64_t seg_cap_words(int64_t T) { return (int64_t)align_up((size_t)(3 * 32 * T + 64), 8); }
+
+}  // namespace
+
+// ===========================================================================
+// Shared host helpers.
+// ===========================================================================
+namespace fgmm {
+
+fgmm_status ws_reserve(fgmm_handle* h, size_t bytes, cudaStream_t stream)
+{
+    if (bytes <= h->ws_bytes) return FGMM_OK;
+    cudaError_t e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "ws_reserve sync");
+    if (h->ws) cudaFree(h->ws);
+    h->ws = nullptr;
+    h->ws_bytes = 0;
+    const size_t want = align_up(bytes + bytes / 4, (size_t)1 << 20);
+    e = cudaMalloc(&h->ws, want);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        h->ws = nullptr;
+        return fail(h, FGMM_ERR_NO_MEMORY, "workspace allocation failed");
+    }
+    h->ws_bytes = want;
+    return FGMM_OK;
+}
+
+fgmm_status check_latent(fgmm_handle* h, const fgmm_latent* lat)
+{
+    if (!h) return FGMM_ERR_INVALID_ARG;
+    if (!lat) return fail(h, FGMM_ERR_INVALID_ARG, "latent is NULL");
+    if (lat->K < 1 || lat->K > FGMM_MAX_K) return fail(h, FGMM_ERR_INVALID_ARG, "K must be in [1, 4]");
+    if (lat->dtype != FGMM_DTYPE_F32 && lat->dtype != FGMM_DTYPE_BF16)
+        return fail(h, FGMM_ERR_INVALID_ARG, "dtype must be FGMM_DTYPE_F32 or FGMM_DTYPE_BF16");
+    if (lat->N < 0 || lat->N > ((int64_t)1 << 40)) return fail(h, FGMM_ERR_INVALID_ARG, "N out of range");
+    if (lat->N > 0 && !lat->params) return fail(h, FGMM_ERR_INVALID_ARG, "params is NULL");
+    return FGMM_OK;
+}
+
+}  // namespace fgmm
+
+// ===========================================================================
+// C ABI.
+// ===========================================================================
+extern "C" {
+
+fgmm_status fgmm_create(fgmm_handle** out)
+{
+    if (!out) return FGMM_ERR_INVALID_ARG;
+    *out = nullptr;
+    fgmm_handle* h = new fgmm_handle();
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_err, sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMemset(h->d_err, 0, sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_stats, 4 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(h->d_stats, 0, 4 * sizeof(unsigned long long));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        if (h->d_err) cudaFree(h->d_err);
+        if (h->d_stats) cudaFree(h->d_stats);
+        delete h;
+        return FGMM_ERR_CUDA;
+    }
+    *out = h;
+    return FGMM_OK;
+}
+
+void fgmm_destroy(fgmm_handle* h)
+{
+    if (!h) return;
+    cudaDeviceSynchronize();
+    if (h->ws) cudaFree(h->ws);
+    if (h->d_err) cudaFree(h->d_err);
+    if (h->d_stats) cudaFree(h->d_stats);
+    delete h;
+}
+
+const char* fgmm_status_string(int32_t status)
+{
+    switch (status) {
+    case FGMM_OK: return "ok";
+    case FGMM_ERR_INVALID_ARG: return "invalid argument";
+    case FGMM_ERR_BAD_PARAMS: return "invalid mixture parameter (NaN/Inf, negative weight, or scale <= 0)";
+    case FGMM_ERR_CAPACITY: return "output buffer too small";
+    case FGMM_ERR_CORRUPT: return "corrupt or truncated stream";
+    case FGMM_ERR_TIMEOUT: return "bounded wait timed out";
+    case FGMM_ERR_CUDA: return "CUDA error";
+    case FGMM_ERR_NO_MEMORY: return "out of device memory";
+    default: return "unknown status";
+    }
+}
+
+const char* fgmm_last_error(const fgmm_handle* h) { return h ? h->last_error.c_str() : "null handle"; }
+
+fgmm_status fgmm_sync_status(fgmm_handle* h, void* stream)
+{
+    if (!h) return FGMM_ERR_INVALID_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "fgmm_sync_status");
+    int32_t v = 0;
+    e = cudaMemcpy(&v, h->d_err, sizeof v, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(h, e, "fgmm_sync_status read");
+    if (v != 0) {
+        e = cudaMemset(h->d_err, 0, sizeof(int32_t));
+        if (e != cudaSuccess) return cuda_fail(h, e, "fgmm_sync_status clear");
+        h->last_error = fgmm_status_string(v);
+    }
+    return static_cast<fgmm_status>(v);
+}
+
+fgmm_status fgmm_stats_enable(fgmm_handle* h, int32_t on)
+{
+    if (!h) return FGMM_ERR_INVALID_ARG;
+    h->stats_on = on != 0;
+    return FGMM_OK;
+}
+
+fgmm_status fgmm_stats_read(fgmm_handle* h, uint64_t* out, void* stream)
+{
+    if (!h || !out) return FGMM_ERR_INVALID_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaStreamSynchronize(st);
+    unsigned long long v[2] = {0, 0};
+    if (e == cudaSuccess) e = cudaMemcpy(v, h->d_stats, sizeof v, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemset(h->d_stats, 0, 2 * sizeof(unsigned long long));
+    if (e != cudaSuccess) return cuda_fail(h, e, "fgmm_stats_read");
+    out[0] = v[0];
+    out[1] = v[1];
+    return FGMM_OK;
+}
+
+fgmm_status fgmm_phi(fgmm_handle* h, const float* z, float* out, int64_t n, void* stream)
+{
+    if (!h) return FGMM_ERR_INVALID_ARG;
+    if (n < 0 || (n > 0 && (!z || !out))) return fail(h, FGMM_ERR_INVALID_ARG, "fgmm_phi: bad arguments");
+    if (n == 0) return FGMM_OK;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    phi_kernel<<<grid_for(n, 256, h->num_sms * 16), 256, 0, st>>>(z, out, n);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? FGMM_OK : cuda_fail(h, e, "fgmm_phi launch");
+}
+
+fgmm_status fgmm_phi_grid(fgmm_handle* h, int64_t i0, float* out, int64_t n, void* stream)
+{
+    if (!h) return FGMM_ERR_INVALID_ARG;
+    if (n < 0 || (n > 0 && !out) || i0 < -(int64_t)(1 << 30) || i0 + n > (int64_t)(1 << 30))
+        return fail(h, FGMM_ERR_INVALID_ARG, "fgmm_phi_grid: bad arguments");
+    if (n == 0) return FGMM_OK;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    phi_grid_kernel<<<grid_for(n, 256, h->num_sms * 16), 256, 0, st>>>(i0, out, n);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? FGMM_OK : cuda_fail(h, e, "fgmm_phi_grid launch");
+}
+
+fgmm_status fgmm_freqs(fgmm_handle* h, const fgmm_latent* lat, const int32_t* symbols, uint32_t* sf, void* stream)
+{
+    fgmm_status s = check_latent(h, lat);
+    if (s != FGMM_OK) return s;
+    if (lat->N > 0 && (!symbols || !sf)) return fail(h, FGMM_ERR_INVALID_ARG, "fgmm_freqs: NULL buffer");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    launch_interval_any(lat, symbols, sf, h->d_err, h->num_sms, st);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? FGMM_OK : cuda_fail(h, e, "fgmm_freqs launch");
+}
+
+int64_t fgmm_encode_bound_words(int64_t N, int32_t S)
+{
+    if (S <= 0 || S % 32 != 0 || N < 0) return -1;
+    const int64_t T = steps_of(N, S);
+    return (int64_t)(S / 32) * (3 * 32 * T + 64);
+}
+
+fgmm_status fgmm_encode(fgmm_handle* h, const fgmm_latent* lat, const int32_t* symbols, int32_t S, uint16_t* words,
+                        int64_t words_cap, int64_t* offsets, int64_t* n_words_out, void* stream)
+{
+    fgmm_status s = check_latent(h, lat);
+    if (s != FGMM_OK) return s;
+    if (S <= 0 || S % 32 != 0) return fail(h, FGMM_ERR_INVALID_ARG, "S must be a positive multiple of 32");
+    if (!offsets || !n_words_out || words_cap < 0 || (words_cap > 0 && !words) || (lat->N > 0 && !symbols))
+        return fail(h, FGMM_ERR_INVALID_ARG, "fgmm_encode: NULL buffer");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int64_t N = lat->N, nseg = S / 32, T = steps_of(N, S);
+    const int64_t cap = seg_cap_words(T);
+    // workspace: intervals [N] u32 | segment scratch [nseg][cap] u16 | lengths [nseg] i64
+    const size_t o_sf = 0;
+    const size_t o_seg = align_up(o_sf + sizeof(uint32_t) * (size_t)N, 256);
+    const size_t o_len = align_up(o_seg + sizeof(uint16_t) * (size_t)(nseg * cap), 256);
+    const size_t bytes = o_len + sizeof(int64_t) * (size_t)nseg;
+    s = ws_reserve(h, bytes, st);
+    if (s != FGMM_OK) return s;
+    char* ws = static_cast<char*>(h->ws);
+    uint32_t* sf = reinterpret_cast<uint32_t*>(ws + o_sf);
+    uint16_t* seg = reinterpret_cast<uint16_t*>(ws + o_seg);
+    int64_t* len = reinterpret_cast<int64_t*>(ws + o_len);
+
+    launch_interval_any(lat, symbols, sf, h->d_err, h->num_sms, st);
+    const int thr = seg_threads(nseg, h->num_sms);
+    fgmm_rans_enc_kernel<<<(unsigned)((nseg * 32 + thr - 1) / thr), thr, 0, st>>>(sf, symbols, N, S, T, seg, cap,
+                                                                                  len, nseg);
+    fgmm_scan_kernel<<<1, 1024, 0, st>>>(len, nseg, offsets, n_words_out, words_cap, h->d_err);
+    fgmm_compact_kernel<<<grid_for(nseg * 32, 256, h->num_sms * 8), 256, 0, st>>>(seg, cap, len, offsets, nseg,
+                                                                                  words, words_cap);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? FGMM_OK : cuda_fail(h, e, "fgmm_encode launch");
+}
+
+fgmm_status fgmm_decode(fgmm_handle* h, const fgmm_latent* lat, const uint16_t* words, int64_t n_words,
+                        const int64_t* offsets, int32_t S, int32_t* symbols_out, void* stream)
+{
+    fgmm_status s = check_latent(h, lat);
+    if (s != FGMM_OK) return s;
+    if (S <= 0 || S % 32 != 0) return fail(h, FGMM_ERR_INVALID_ARG, "S must be a positive multiple of 32");
+    if (!offsets || n_words < 0 || (n_words > 0 && !words) || (lat->N > 0 && !symbols_out))
+        return fail(h, FGMM_ERR_INVALID_ARG, "fgmm_decode: NULL buffer");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    unsigned long long* stats = h->stats_on ? h->d_stats : nullptr;
+    if (lat->dtype == FGMM_DTYPE_BF16)
+        dispatch_dec<__nv_bfloat16>(lat, S, words, n_words, offsets, symbols_out, h->d_err, stats, h->num_sms, st);
+    else
+        dispatch_dec<float>(lat, S, words, n_words, offsets, symbols_out, h->d_err, stats, h->num_sms, st);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? FGMM_OK : cuda_fail(h, e, "fgmm_decode launch");
+}
+
+}  // extern "C"

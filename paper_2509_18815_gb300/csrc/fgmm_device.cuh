@@ -1,0 +1,220 @@
+// fgmm_device.cuh -- device-side arithmetic of the table-free GMM coder.
+//
+// Everything here is the per-symbol quantised mixture CDF that the encoder
+// evaluates at the coded symbol and the decoder searches (Sec. III-A), with
+// the Gaussian CDF replaced by the Abramowitz & Stegun 26.2.17 approximation
+// (Sec. III-B, Eq. 8). Every floating-point step is written with an explicit
+// round-to-nearest intrinsic (__fmul_rn, __fsub_rn, __fmaf_rn, __frcp_rn) so
+// that no contraction or reassociation can change a bit: the coded stream is
+// a function of these exact IEEE operations, and any decoder that performs
+// the same operations reproduces it.
+#pragma once
+
+#include <cstdint>
+#include <cuda_bf16.h>
+
+namespace fgmm {
+
+constexpr int kMaxK = 4;
+constexpr uint32_t kProbBits = 16;
+constexpr uint32_t kM = 1u << kProbBits;   // total frequency
+constexpr uint32_t kL = 1u << 16;          // rANS lower bound / initial state
+constexpr int kYmax = 255;                 // window clamp (alphabet [-255, 255])
+constexpr float kR = 8.0f;                 // window half-width in scales
+constexpr float kSigmaMin = 0.11f;         // scale floor
+
+// Device error codes (the same numbers as fgmm_status).
+constexpr int32_t kErrBadParams = 2;
+constexpr int32_t kErrCapacity = 3;
+constexpr int32_t kErrCorrupt = 4;
+
+__device__ __forceinline__ void set_error(int32_t* err, int32_t code)
+{
+    if (*reinterpret_cast<volatile int32_t*>(err) == 0) atomicCAS(err, 0, code);
+}
+
+// exp(a), a in [-72, 0]: Cody-Waite reduction a = k ln2 + r (ln2 split into
+// a high part whose product with any |k| <= 127 is short, and the rounding
+// remainder), degree-7 Taylor polynomial of exp(r) with coefficients 1/i!,
+// and the factor 2^k added into the exponent field.
+__device__ __forceinline__ float exp_cw(float a)
+{
+    const float kLog2e = 0x1.715476p+0f;
+    const float kLn2Hi = 0x1.62e4p-1f;
+    const float kLn2Lo = 0x1.7f7d1cp-20f;
+    float k = rintf(__fmul_rn(a, kLog2e));
+    float r = __fmaf_rn(-k, kLn2Hi, a);
+    r = __fmaf_rn(-k, kLn2Lo, r);
+    float p = 0x1.a01a02p-13f;           // fp32(1/7!)
+    p = __fmaf_rn(p, r, 0x1.6c16c2p-10f);  // fp32(1/6!)
+    p = __fmaf_rn(p, r, 0x1.111112p-7f);   // fp32(1/5!)
+    p = __fmaf_rn(p, r, 0x1.555556p-5f);   // fp32(1/4!)
+    p = __fmaf_rn(p, r, 0x1.555556p-3f);   // fp32(1/3!)
+    p = __fmaf_rn(p, r, 0.5f);
+    p = __fmaf_rn(p, r, 1.0f);
+    p = __fmaf_rn(p, r, 1.0f);
+    uint32_t bits = __float_as_uint(p) + (static_cast<uint32_t>(static_cast<int32_t>(k)) << 23);
+    return __uint_as_float(bits);
+}
+
+// Phi-hat(z): A&S 26.2.17, Phi(x) ~ 1 - Z(x) sum_i b_i t^i, t = 1/(1+px),
+// x = |z|, mirrored for z < 0. p = 0.2316419 and b_1..b_5 are the handbook's;
+// the 1/sqrt(2 pi) of the density Z is pre-multiplied into the b_i
+// (c_i = fp32(b_i / sqrt(2 pi))). z is clamped to [-12, 12] and rounded to the
+// grid 2^-22 (half to even), where this FP32 evaluation is monotone.
+__device__ __forceinline__ float phi_hat(float z)
+{
+    const float kP = 0x1.da6712p-3f;
+    const float kC1 = 0x1.04f20cp-3f;
+    const float kC2 = -0x1.23531cp-3f;
+    const float kC3 = 0x1.6be1c6p-1f;
+    const float kC4 = -0x1.7401c6p-1f;
+    const float kC5 = 0x1.0fb844p-1f;
+    float zc = fminf(fmaxf(z, -12.0f), 12.0f);
+    float zs = __fmul_rn(rintf(__fmul_rn(zc, 0x1p22f)), 0x1p-22f);
+    float x = fabsf(zs);
+    float d = __fmaf_rn(kP, x, 1.0f);
+    float t = __frcp_rn(d);
+    float h = __fmaf_rn(kC5, t, kC4);
+    h = __fmaf_rn(h, t, kC3);
+    h = __fmaf_rn(h, t, kC2);
+    h = __fmaf_rn(h, t, kC1);
+    float g = __fmul_rn(h, t);
+    float a = __fmul_rn(-0.5f, __fmul_rn(x, x));
+    float q = __fmul_rn(exp_cw(a), g);
+    return zs >= 0.0f ? __fsub_rn(1.0f, q) : q;
+}
+
+// Parameter loads from the planar [3][K][N] layout.
+__device__ __forceinline__ float load_param(const float* p, int64_t i) { return __ldg(p + i); }
+__device__ __forceinline__ float load_param(const __nv_bfloat16* p, int64_t i)
+{
+    const unsigned short b = __ldg(reinterpret_cast<const unsigned short*>(p) + i);
+    return __uint_as_float(static_cast<uint32_t>(b) << 16);
+}
+
+// One symbol's mixture, ready for CDF probes: weights, means, reciprocal
+// floored scales, the window [lo, hi] and T' = 2^16 - W - 1.
+template <int K>
+struct Mix {
+    float w[K], mu[K], inv[K];
+    int lo, hi;
+    float tp;
+};
+
+// Loads symbol n's parameters and prepares its window. Returns false (and
+// neutralises the mixture: all weights 0) if a parameter is invalid
+// (weight negative or non-finite, mean non-finite, scale non-finite or <= 0).
+template <int K, typename T>
+__device__ __forceinline__ bool load_mix(const T* params, int64_t N, int64_t n, Mix<K>& m)
+{
+    float a = __int_as_float(0xff800000);   // -inf
+    float b = __int_as_float(0x7f800000);   // +inf
+    float lo_f = b, hi_f = a;
+    bool ok = true;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        float w = load_param(params, (int64_t)(0 * K + k) * N + n);
+        float mu = load_param(params, (int64_t)(1 * K + k) * N + n);
+        float s = load_param(params, (int64_t)(2 * K + k) * N + n);
+        ok = ok && isfinite(w) && w >= 0.0f && isfinite(mu) && isfinite(s) && s > 0.0f;
+        float sp = fmaxf(s, kSigmaMin);
+        m.w[k] = w;
+        m.mu[k] = mu;
+        m.inv[k] = __frcp_rn(sp);
+        lo_f = fminf(lo_f, __fmaf_rn(-kR, sp, mu));
+        hi_f = fmaxf(hi_f, __fmaf_rn(kR, sp, mu));
+    }
+    if (!ok) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) { m.w[k] = 0.0f; m.mu[k] = 0.0f; m.inv[k] = 1.0f; }
+        lo_f = -1.0f;
+        hi_f = 1.0f;
+    }
+    lo_f = fminf(fmaxf(floorf(lo_f), -(float)kYmax), (float)kYmax);
+    hi_f = fminf(fmaxf(ceilf(hi_f), -(float)kYmax), (float)kYmax);
+    int lo = (int)lo_f, hi = (int)hi_f;
+    if (lo > hi) { int t = lo; lo = hi; hi = t; }
+    m.lo = lo;
+    m.hi = hi;
+    m.tp = (float)(int)(kM - (uint32_t)(hi - lo + 1) - 1u);
+    return ok;
+}
+
+// F-hat(j - 1/2) = sum_k w_k Phi-hat((b - mu_k) / sigma'_k), k ascending.
+template <int K>
+__device__ __forceinline__ float mix_cdf(const Mix<K>& m, int j)
+{
+    const float b = __fsub_rn((float)j, 0.5f);
+    float acc = 0.0f;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        float z = __fmul_rn(__fsub_rn(b, m.mu[k]), m.inv[k]);
+        acc = __fmaf_rn(m.w[k], phi_hat(z), acc);
+    }
+    return acc;
+}
+
+// Quantised CDF Q(j) for lo < j <= hi+1: (j - lo) + floor(T' min(F-hat, 1)).
+// Q(lo) = 0 is not evaluated.
+template <int K>
+__device__ __forceinline__ uint32_t q_at(const Mix<K>& m, int j)
+{
+    const float v = fminf(mix_cdf<K>(m, j), 1.0f);
+    return (uint32_t)(j - m.lo) + (uint32_t)floorf(__fmul_rn(m.tp, v));
+}
+
+// The rANS interval of symbol s. Escape (s outside [lo, hi]) gets
+// [Q(hi+1), 2^16); an interval is an escape iff start + freq == 2^16.
+template <int K>
+__device__ __forceinline__ void interval_of(const Mix<K>& m, int32_t s, uint32_t& start, uint32_t& freq)
+{
+    if (s >= m.lo && s <= m.hi) {
+        const uint32_t a = (s == m.lo) ? 0u : q_at<K>(m, s);
+        const uint32_t b = q_at<K>(m, s + 1);
+        start = a;
+        freq = b - a;
+    } else {
+        const uint32_t e = q_at<K>(m, m.hi + 1);
+        start = e;
+        freq = kM - e;
+    }
+}
+
+// Decoder search: the symbol whose interval holds `slot`, by binary search
+// over Q on [lo, hi+1] after the escape test (Sec. III-A). Returns true for
+// the escape slot. `probes` counts CDF evaluations.
+template <int K>
+__device__ __forceinline__ bool search_slot(const Mix<K>& m, uint32_t slot, int32_t& s, uint32_t& start,
+                                            uint32_t& freq, int& probes)
+{
+    const uint32_t qe = q_at<K>(m, m.hi + 1);
+    ++probes;
+    if (slot >= qe) {
+        start = qe;
+        freq = kM - qe;
+        return true;
+    }
+    int a = m.lo, b = m.hi + 1;
+    uint32_t qa = 0, qb = qe;
+    while (b - a > 1) {
+        const int mid = a + ((b - a) >> 1);
+        const uint32_t qm = q_at<K>(m, mid);
+        ++probes;
+        if (qm <= slot) { a = mid; qa = qm; }
+        else { b = mid; qb = qm; }
+    }
+    s = a;
+    start = qa;
+    freq = qb - qa;
+    return false;
+}
+
+__device__ __forceinline__ uint32_t lanemask_lt()
+{
+    uint32_t m;
+    asm volatile("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+}  // namespace fgmm

@@ -1,0 +1,190 @@
+"""GPU encode/decode parity with the CPU oracle: frequencies, bitstreams,
+offsets and decoded symbols must be identical (bit-exact), on the seeded
+synthetic workloads, across tile edges and ragged tails, with escapes and
+extreme parameters; damage and bad input are reported through the status
+word, never by a fault."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2509_18815_gb300 import synth
+from tests.gpu_util import dev_i32, dev_params, host_u16, host_u32, need_gpu, oracle_params
+
+pytestmark = pytest.mark.gpu
+
+
+def _codec():
+    need_gpu()
+    from paper_2509_18815_gb300 import codec
+    return codec
+
+
+def _check_latent(params, syms, S, bf16=False, check_oracle_decode=True):
+    codec = _codec()
+    op = oracle_params(params, bf16)
+    dp = dev_params(params, bf16)
+    ds = dev_i32(syms)
+    # frequencies
+    sf_g = host_u32(codec.freqs(dp, ds))
+    sf_c = oracle.freqs(op, syms)
+    np.testing.assert_array_equal(sf_g, sf_c)
+    # bitstream
+    words_g, off_g = codec.encode(dp, ds, S)
+    words_c, off_c = oracle.encode(op, syms, S)
+    np.testing.assert_array_equal(off_g.cpu().numpy(), off_c)
+    np.testing.assert_array_equal(host_u16(words_g), words_c)
+    # decode
+    out = codec.decode(dp, words_g, off_g, S).cpu().numpy()
+    np.testing.assert_array_equal(out, syms)
+    if check_oracle_decode:
+        out_c, st = oracle.decode(op, words_c, off_c, S)
+        assert st == oracle.OK
+        np.testing.assert_array_equal(out_c, syms)
+
+
+def test_workload_latent_192x16x16_k3_s32():
+    lat = synth.make_latent(192, 16, 16, 3, seed=1001)
+    _check_latent(lat.params, lat.symbols, 32)
+
+
+def test_workload_latent_192x32x48_k3_s1024():
+    lat = synth.make_latent(192, 32, 48, 3, seed=1002)
+    _check_latent(lat.params, lat.symbols, 1024)
+
+
+@pytest.mark.parametrize("N", [0, 1, 31, 32, 33, 1000, 4097, 70001])
+@pytest.mark.parametrize("S", [32, 64, 1024])
+def test_sizes(N, S):
+    lat = synth.make_latent(1, 1, max(N, 1), 3, seed=N + 3 * S)
+    _check_latent(np.ascontiguousarray(lat.params[:, :, :N]), np.ascontiguousarray(lat.symbols[:N]), S)
+
+
+@pytest.mark.parametrize("K", [1, 2, 3, 4])
+@pytest.mark.parametrize("bf16", [False, True])
+def test_components_and_dtypes(K, bf16):
+    lat = synth.make_latent(16, 16, 16, K, seed=200 + K)
+    _check_latent(lat.params, lat.symbols, 256, bf16=bf16)
+
+
+def test_escapes():
+    lat = synth.make_latent(8, 32, 32, 3, seed=300, escape_stress=0.02)
+    s = lat.symbols.copy()
+    s[:6] = [np.iinfo(np.int32).min, np.iinfo(np.int32).max, -256, 256, -1, 65536]
+    _check_latent(lat.params, s, 128)
+
+
+def test_extreme_params():
+    lat = synth.make_latent(4, 32, 32, 4, seed=301, sigma_max=64.0)
+    p = lat.params.copy()
+    p[2, :, ::5] = 0.11
+    p[2, 1, 1::5] = 1e7
+    p[1, 2, 2::5] = -3e4
+    p[0, :, 3::5] = 0.0
+    p[0, 0, 4::5] = 3.0
+    p[1, 0, 6::11] = 3e38
+    _check_latent(p, lat.symbols, 64)
+
+
+def test_large_scales_workload_distribution():
+    lat = synth.make_latent(32, 32, 32, 3, seed=302, sigma_max=64.0)
+    _check_latent(lat.params, lat.symbols, 512)
+
+
+@pytest.mark.parametrize("K,bf16", [(3, False), (4, False), (3, True), (4, True)])
+def test_workload_latent_320x64x96(K, bf16):
+    """Full-size 1,966,080-symbol latent: GPU stream identical to the oracle's
+    (the oracle encodes it in about a second); GPU round trip exact."""
+    lat = synth.make_latent(320, 64, 96, K, seed=1003)
+    codec = _codec()
+    S = 4096
+    op = oracle_params(lat.params, bf16)
+    dp = dev_params(lat.params, bf16)
+    ds = dev_i32(lat.symbols)
+    words_g, off_g = codec.encode(dp, ds, S)
+    words_c, off_c = oracle.encode(op, lat.symbols, S)
+    np.testing.assert_array_equal(off_g.cpu().numpy(), off_c)
+    np.testing.assert_array_equal(host_u16(words_g), words_c)
+    out = codec.decode(dp, words_g, off_g, S).cpu().numpy()
+    np.testing.assert_array_equal(out, lat.symbols)
+
+
+# ---------------------------------------------------------------------------
+# Errors are reported, not faulted.
+# ---------------------------------------------------------------------------
+
+def test_corrupt_streams_report_corrupt():
+    codec = _codec()
+    from paper_2509_18815_gb300._abi import FGMM_ERR_CORRUPT, FgmmError
+    lat = synth.make_latent(4, 16, 16, 3, seed=400)
+    dp, ds = dev_params(lat.params), dev_i32(lat.symbols)
+    S = 64
+    words, off = codec.encode(dp, ds, S)
+    bad = words.clone()
+    bad[int(off[1].item()) - 64] ^= 0x1234
+    with pytest.raises(FgmmError) as e:
+        codec.decode(dp, bad, off, S)
+    assert e.value.status == FGMM_ERR_CORRUPT
+    # truncated: offsets beyond the words buffer
+    with pytest.raises(FgmmError) as e:
+        codec.decode(dp, words[:-5], off, S)
+    assert e.value.status == FGMM_ERR_CORRUPT
+    # segment shorter than its flush block
+    off2 = off.clone()
+    off2[1] = off2[0] + 10
+    with pytest.raises(FgmmError) as e:
+        codec.decode(dp, words, off2, S)
+    assert e.value.status == FGMM_ERR_CORRUPT
+    # garbage words: every read stays inside the segment
+    junk = torch.randint(-32768, 32767, words.shape, dtype=torch.int16, device="cuda")
+    with pytest.raises(FgmmError) as e:
+        codec.decode(dp, junk, off, S)
+    assert e.value.status == FGMM_ERR_CORRUPT
+    # the handle is still usable afterwards
+    out = codec.decode(dp, words, off, S).cpu().numpy()
+    np.testing.assert_array_equal(out, lat.symbols)
+
+
+def test_bad_params_and_capacity():
+    codec = _codec()
+    from paper_2509_18815_gb300._abi import FGMM_ERR_BAD_PARAMS, FGMM_ERR_CAPACITY, FGMM_ERR_INVALID_ARG, FgmmError
+    lat = synth.make_latent(2, 16, 16, 3, seed=401)
+    ds = dev_i32(lat.symbols)
+    for c, v in [(0, -1.0), (0, float("nan")), (1, float("inf")), (2, 0.0), (2, -2.0)]:
+        p = lat.params.copy()
+        p[c, 1, 17] = v
+        with pytest.raises(FgmmError) as e:
+            codec.encode(dev_params(p), ds, 32)
+        assert e.value.status == FGMM_ERR_BAD_PARAMS
+    dp = dev_params(lat.params)
+    with pytest.raises(FgmmError) as e:
+        codec.encode(dp, ds, 32, words_cap=100)
+    assert e.value.status == FGMM_ERR_CAPACITY
+    with pytest.raises(ValueError):
+        codec.encode(dp, ds, 48)
+    from paper_2509_18815_gb300 import _abi
+    import ctypes
+    h = codec.handle()
+    bad = codec.latent(dp)
+    bad.K = 5
+    st = _abi.fgmm_freqs(h.ptr, ctypes.byref(bad), ds.data_ptr(), ds.data_ptr(), None)
+    assert st == FGMM_ERR_INVALID_ARG
+    words, off = codec.encode(dp, ds, 32)
+    np.testing.assert_array_equal(codec.decode(dp, words, off, 32).cpu().numpy(), lat.symbols)
+
+
+def test_decode_counts_cdf_evaluations():
+    codec = _codec()
+    lat = synth.make_latent(8, 16, 16, 3, seed=402)
+    dp, ds = dev_params(lat.params), dev_i32(lat.symbols)
+    words, off = codec.encode(dp, ds, 64)
+    codec.stats_enable(True)
+    codec.stats_read()
+    codec.decode(dp, words, off, 64)
+    evals, nsym = codec.stats_read()
+    codec.stats_enable(False)
+    assert nsym == lat.N
+    lo, hi = oracle.window(lat.params)
+    W = (hi - lo + 1).astype(np.float64)
+    # one escape test plus floor/ceil(log2 W) bisection probes per symbol
+    assert np.sum(1 + np.floor(np.log2(W))) <= evals <= np.sum(1 + np.ceil(np.log2(W)))

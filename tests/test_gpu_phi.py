@@ -1,0 +1,45 @@
+"""GPU Phi-hat equals the oracle's bit for bit: on every point of the 2^-22
+grid in [-12, 12] (the whole input set the coder can produce after the
+grid rounding), and on arbitrary FP32 inputs off the grid."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from tests.gpu_util import need_gpu
+
+pytestmark = pytest.mark.gpu
+
+ZMAX_I = 12 << 22
+
+
+def test_phi_grid_bit_exact_whole_grid():
+    need_gpu()
+    from paper_2509_18815_gb300 import codec
+    chunk = 1 << 24
+    i = -ZMAX_I
+    prev_last = None
+    while i <= ZMAX_I:
+        n = min(chunk, ZMAX_I - i + 1)
+        g = codec.phi_grid(i, n).cpu().numpy()
+        c = oracle.phi_grid(i, n)
+        assert np.array_equal(g.view(np.uint32), c.view(np.uint32)), i
+        # monotone, including across chunk borders
+        assert np.all(np.diff(g) >= 0)
+        if prev_last is not None:
+            assert g[0] >= prev_last
+        prev_last = g[-1]
+        i += n
+
+
+def test_phi_off_grid_bit_exact():
+    need_gpu()
+    from paper_2509_18815_gb300 import codec
+    rng = np.random.default_rng(4)
+    z = np.concatenate([
+        rng.uniform(-13, 13, 1_000_000), rng.normal(0, 1e-4, 100_000),
+        np.array([0.0, -0.0, 12.0, -12.0, 1e30, -1e30, np.inf, -np.inf, 1e-45, -1e-45, 2 ** -23, -(2 ** -23)]),
+    ]).astype(np.float32)
+    g = codec.phi(torch.from_numpy(z).cuda()).cpu().numpy()
+    c = oracle.phi(z)
+    assert np.array_equal(g.view(np.uint32), c.view(np.uint32))
