@@ -54,7 +54,8 @@ typedef enum {
     FGMM_ERR_CORRUPT = 4,     /* stream fails the end-of-decode check or would read out of its segment */
     FGMM_ERR_TIMEOUT = 5,     /* a bounded wait gave up (reserved; no kernel here waits) */
     FGMM_ERR_CUDA = 6,        /* a CUDA runtime call or launch failed */
-    FGMM_ERR_NO_MEMORY = 7    /* workspace allocation failed */
+    FGMM_ERR_NO_MEMORY = 7,   /* workspace allocation failed */
+    FGMM_ERR_TOO_LARGE = 8    /* request exceeds the fixed scratch of fgmm_encode_noalloc */
 } fgmm_status;
 
 enum { FGMM_DTYPE_F32 = 0, FGMM_DTYPE_BF16 = 1 };
@@ -136,6 +137,47 @@ fgmm_status fgmm_decode(fgmm_handle *h, const fgmm_latent *lat, const uint16_t *
  * zeroes the counters. */
 fgmm_status fgmm_stats_enable(fgmm_handle *h, int32_t on);
 fgmm_status fgmm_stats_read(fgmm_handle *h, uint64_t *out, void *stream);
+
+/* Size of the fixed device scratch array used by fgmm_encode_noalloc. */
+#define FGMM_NOALLOC_SCRATCH_BYTES (16u << 20)
+
+/* Allocation-free variant of fgmm_encode. The paper has no counterpart: it
+ * exists for callers that cannot allocate device memory at the time they
+ * encode, for example code running inside a host callback or a real-time
+ * loop where cudaMalloc would block or is forbidden, or a plugin in a host
+ * application that owns all device allocations. It needs no handle and
+ * never calls cudaMalloc, cudaFree or any allocating routine; it produces
+ * exactly the words, offsets and total of fgmm_encode.
+ *
+ * Its scratch (per-symbol intervals, per-segment word buffers and lengths)
+ * lives in one static device array of FGMM_NOALLOC_SCRATCH_BYTES (16 MiB)
+ * that every GPU which loads this library holds until the process exits.
+ * A request fits when
+ *   align256(4 N) + align256(2 (S/32) align8(96 ceil(N/S) + 64)) + 8 (S/32)
+ * is at most that size (about 1.5 M symbols); larger requests return
+ * FGMM_ERR_TOO_LARGE without launching anything.
+ *
+ * All calls in the process share the one array, and it keeps whatever the
+ * last call left there (every scratch element is written before it is read,
+ * so nothing in it needs clearing). Calls whose work overlaps on the GPU
+ * (on different streams, or from different threads without ordering) race
+ * on the array and corrupt each other's output: serialise them.
+ *
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current) and caches it; make that
+ * first call before any stream capture on the device.
+ *
+ * Arguments are those of fgmm_encode (all device pointers, caller-owned),
+ * without the handle, plus
+ *   status_out  device int32[1]: set to 0 at the start of the call, then to
+ *               the first data-dependent error the kernels find
+ *               (FGMM_ERR_BAD_PARAMS, FGMM_ERR_CAPACITY); read it after the
+ *               stream has synchronised.
+ * The call is asynchronous on `stream`; the return value covers host-side
+ * checks and launch errors only. */
+fgmm_status fgmm_encode_noalloc(const fgmm_latent *lat, const int32_t *symbols, int32_t S, uint16_t *words,
+                                int64_t words_cap, int64_t *offsets, int64_t *n_words_out, int32_t *status_out,
+                                void *stream);
 
 #ifdef __cplusplus
 }

@@ -20,6 +20,8 @@ FGMM_ERR_CORRUPT = 4
 FGMM_ERR_TIMEOUT = 5
 FGMM_ERR_CUDA = 6
 FGMM_ERR_NO_MEMORY = 7
+FGMM_ERR_TOO_LARGE = 8
+FGMM_NOALLOC_SCRATCH_BYTES = 16 << 20
 FGMM_DTYPE_F32 = 0
 FGMM_DTYPE_BF16 = 1
 FGMM_MAX_K = 4
@@ -50,6 +52,7 @@ SIGNATURES = {
     "fgmm_decode": (I32, [P, LATP, P, I64, P, I32, P, P]),
     "fgmm_stats_enable": (I32, [P, I32]),
     "fgmm_stats_read": (I32, [P, P, P]),
+    "fgmm_encode_noalloc": (I32, [LATP, P, I32, P, I64, P, P, P, P]),
 }
 
 _lib = None

@@ -18,6 +18,7 @@
 
 #include <cstdint>
 #include <cstring>
+#include <mutex>
 
 #include "fgmm_device.cuh"
 #include "fgmm_internal.h"
@@ -430,6 +431,7 @@ const char* fgmm_status_string(int32_t status)
     case FGMM_ERR_TIMEOUT: return "bounded wait timed out";
     case FGMM_ERR_CUDA: return "CUDA error";
     case FGMM_ERR_NO_MEMORY: return "out of device memory";
+    case FGMM_ERR_TOO_LARGE: return "request exceeds the fixed scratch of the allocation-free encoder";
     default: return "unknown status";
     }
 }
@@ -568,3 +570,95 @@ fgmm_status fgmm_decode(fgmm_handle* h, const fgmm_latent* lat, const uint16_t* 
 }
 
 }  // extern "C"
+
+// ===========================================================================
+// Allocation-free encode: the same four kernels as fgmm_encode, with their
+// scratch in a fixed static device array instead of handle workspace.
+// ===========================================================================
+
+// Fixed scratch for fgmm_encode_noalloc, resident on every GPU that loads
+// this library until the process exits. Host code must not use this name as
+// an address: it is a host-side stand-in. The device address comes from
+// cudaGetSymbolAddress in noalloc_scratch_for_current_device().
+static __device__ __align__(256) unsigned char fgmm_noalloc_scratch[FGMM_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+
+constexpr int kNoAllocMaxDevices = 128;
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[kNoAllocMaxDevices];
+int g_noalloc_sms[kNoAllocMaxDevices];
+
+// One-time set-up per device, with that device current: look up and cache
+// the device address of the scratch array and the SM count.
+cudaError_t noalloc_scratch_for_current_device(void** ptr, int* sms)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, fgmm_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        int n = 0;
+        e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        g_noalloc_ptr[dev] = p;
+        g_noalloc_sms[dev] = n;
+    }
+    *ptr = g_noalloc_ptr[dev];
+    *sms = g_noalloc_sms[dev];
+    return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" fgmm_status fgmm_encode_noalloc(const fgmm_latent* lat, const int32_t* symbols, int32_t S,
+                                           uint16_t* words, int64_t words_cap, int64_t* offsets,
+                                           int64_t* n_words_out, int32_t* status_out, void* stream)
+{
+    if (!lat || lat->K < 1 || lat->K > FGMM_MAX_K || lat->N < 0 || lat->N > ((int64_t)1 << 40) ||
+        (lat->dtype != FGMM_DTYPE_F32 && lat->dtype != FGMM_DTYPE_BF16) || (lat->N > 0 && !lat->params))
+        return FGMM_ERR_INVALID_ARG;
+    if (S <= 0 || S % 32 != 0) return FGMM_ERR_INVALID_ARG;
+    if (!offsets || !n_words_out || !status_out || words_cap < 0 || (words_cap > 0 && !words) ||
+        (lat->N > 0 && !symbols))
+        return FGMM_ERR_INVALID_ARG;
+    const int64_t N = lat->N, nseg = S / 32, T = steps_of(N, S);
+    const int64_t cap = seg_cap_words(T);
+    const size_t o_sf = 0;
+    const size_t o_seg = align_up(o_sf + sizeof(uint32_t) * (size_t)N, 256);
+    const size_t o_len = align_up(o_seg + sizeof(uint16_t) * (size_t)(nseg * cap), 256);
+    const size_t bytes = o_len + sizeof(int64_t) * (size_t)nseg;
+    if (bytes > (size_t)FGMM_NOALLOC_SCRATCH_BYTES) return FGMM_ERR_TOO_LARGE;
+
+    void* base = nullptr;
+    int sms = 0;
+    cudaError_t e = noalloc_scratch_for_current_device(&base, &sms);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return FGMM_ERR_CUDA;
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    char* ws = static_cast<char*>(base);
+    uint32_t* sf = reinterpret_cast<uint32_t*>(ws + o_sf);
+    uint16_t* seg = reinterpret_cast<uint16_t*>(ws + o_seg);
+    int64_t* len = reinterpret_cast<int64_t*>(ws + o_len);
+
+    e = cudaMemsetAsync(status_out, 0, sizeof(int32_t), st);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return FGMM_ERR_CUDA;
+    }
+    launch_interval_any(lat, symbols, sf, status_out, sms, st);
+    const int thr = seg_threads(nseg, sms);
+    fgmm_rans_enc_kernel<<<(unsigned)((nseg * 32 + thr - 1) / thr), thr, 0, st>>>(sf, symbols, N, S, T, seg, cap,
+                                                                                  len, nseg);
+    fgmm_scan_kernel<<<1, 1024, 0, st>>>(len, nseg, offsets, n_words_out, words_cap, status_out);
+    fgmm_compact_kernel<<<grid_for(nseg * 32, 256, sms * 8), 256, 0, st>>>(seg, cap, len, offsets, nseg, words,
+                                                                            words_cap);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? FGMM_OK : FGMM_ERR_CUDA;
+}
