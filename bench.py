@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--impl", default="fgmm", choices=["fgmm", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=30)
+    ap.add_argument("--decode-lanes", type=int, default=0, help="0 = automatic")
     return ap.parse_args()
 
 
@@ -174,6 +175,7 @@ def run_fgmm(args):
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     from paper_2509_18815_gb300 import _abi, build, codec, synth
+    from paper_2509_18815_gb300.dist import max_over_ranks
     build.build()
     import ctypes
 
@@ -206,10 +208,16 @@ def run_fgmm(args):
     enc(); dec(); h.sync()
     assert torch.equal(out.cpu(), ds.cpu()), "round trip failed"
     n_words = int(total.item())
+    # algorithmic work: CDF evaluations of the plain binary search (one lane
+    # per stream); the timed decoder may evaluate more points per round
+    h.check(_abi.fgmm_set_option(h.ptr, _abi.FGMM_OPT_DECODE_LANES, 1))
     codec.stats_enable(True, h); codec.stats_read(h)
     dec(); h.sync()
     cdf_evals, nsym = codec.stats_read(h)
     codec.stats_enable(False, h)
+    h.check(_abi.fgmm_set_option(h.ptr, _abi.FGMM_OPT_DECODE_LANES, args.decode_lanes))
+    dec(); h.sync()
+    assert torch.equal(out.cpu(), ds.cpu()), "round trip failed"
 
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     for _ in range(max(args.warmup, 3)):
@@ -242,10 +250,46 @@ def run_fgmm(args):
     ms_enc = sum(t_enc) / len(t_enc)
     ms_dec = sum(t_dec) / len(t_dec)
     ms_step = ms_enc + ms_dec
-    if world > 1:
-        t = torch.tensor([ms_step, ms_enc, ms_dec], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step, ms_enc, ms_dec = [float(x) for x in t.tolist()]
+    ms_step, ms_enc, ms_dec = max_over_ranks([ms_step, ms_enc, ms_dec], device=dev)
+
+    # the table-based comparison coder on the same latent and GPU: builds the
+    # per-symbol CDF table (512 entries) and codes from it; same stream
+    table = torch.empty((N, 512), dtype=torch.int16, device=dev)
+    words_t = torch.empty(cap, dtype=torch.int16, device=dev)
+    offsets_t = torch.empty(S // 32 + 1, dtype=torch.int64, device=dev)
+    total_t = torch.empty(1, dtype=torch.int64, device=dev)
+    out_t = torch.empty(N, dtype=torch.int32, device=dev)
+
+    def tenc():
+        h.check(_abi.fgmm_table_encode(h.ptr, L, ds.data_ptr(), S, table.data_ptr(), words_t.data_ptr(), cap,
+                                       offsets_t.data_ptr(), total_t.data_ptr(), sptr))
+
+    def tdec():
+        h.check(_abi.fgmm_table_decode(h.ptr, L, table.data_ptr(), words.data_ptr(), cap, offsets.data_ptr(), S,
+                                       out_t.data_ptr(), sptr))
+
+    tenc(); tdec(); h.sync()
+    assert int(total_t.item()) == n_words and torch.equal(words_t[:n_words], words[:n_words]), \
+        "table coder stream differs"
+    assert torch.equal(out_t, ds), "table decode failed"
+    tsteps = max(3, min(args.steps, 20))
+    te, td = [], []
+    for i in range(tsteps + 2):
+        flush.fill_(i & 0xff)
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream); tenc(); e1.record(stream); tdec(); e2.record(stream)
+        torch.cuda.synchronize()
+        if i >= 2:
+            te.append(e0.elapsed_time(e1)); td.append(e1.elapsed_time(e2))
+    h.sync()
+    ms_tenc, ms_tdec = statistics.median(te), statistics.median(td)
+    del table
+
+    # rate: FP64 audit on the GPU
+    aud = torch.empty(4, dtype=torch.float64, device=dev)
+    h.check(_abi.fgmm_rate_audit(h.ptr, L, ds.data_ptr(), aud.data_ptr(), sptr))
+    h.sync()
+    ideal_bits, coded_bits, max_cdf_err, n_esc = aud.cpu().tolist()
 
     # end to end through the C ABI from pinned host buffers: H2D parameters
     # and symbols, encode, D2H stream; H2D stream, decode, D2H symbols
@@ -283,10 +327,7 @@ def run_fgmm(args):
     h.sync()
     assert torch.equal(hout, hs), "end-to-end round trip failed"
     e2e_ms = 1e3 * statistics.median(e2e_t)
-    if world > 1:
-        t = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    (e2e_ms,) = max_over_ranks([e2e_ms], device=dev)
 
     value = world * N / (ms_step * 1e-3) / 1e6
     props = torch.cuda.get_device_properties(dev)
@@ -316,11 +357,21 @@ def run_fgmm(args):
         "ms_decode": ms_dec,
         "bits_per_symbol": 16.0 * n_words / N,
         "cdf_evals_per_symbol": cdf_evals / max(nsym, 1),
+        "decode_lanes": args.decode_lanes or "auto",
+        "table_coder": {"encode_msym_s": N / (ms_tenc * 1e-3) / 1e6, "decode_msym_s": N / (ms_tdec * 1e-3) / 1e6,
+                        "ms_encode": ms_tenc, "ms_decode": ms_tdec, "table_mb": N * 512 * 2 / 1e6,
+                        "encode_speedup_table_free": ms_tenc / ms_enc, "decode_speedup_table_free": ms_tdec / ms_dec,
+                        "stream_identical": True},
+        "rate": {"ideal_bits_per_symbol": ideal_bits / N, "coded_bits_per_symbol": coded_bits / N,
+                 "overhead_pct": 100.0 * (coded_bits / ideal_bits - 1.0),
+                 "container_overhead_pct": 100.0 * (16.0 * n_words / coded_bits - 1.0),
+                 "max_cdf_err": max_cdf_err, "escapes": int(n_esc), "audit": "FP64 on the GPU (erfc)"},
         "gpu_launches": launches_per_step * args.steps,
         "wall_s_timed_region": t_wall,
         "e2e": {"value": world * N / (e2e_ms * 1e-3) / 1e6, "unit": "Msymbols/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
-        "roofline": {"kernel": "fgmm_rans_dec_kernel", "bound": "alu", "achieved": achieved, "peak": alu_peak,
+        "roofline": {"kernel": "fgmm_dec_coop_kernel" if args.decode_lanes != 1 else "fgmm_dec_kernel",
+                     "bound": "alu", "achieved": achieved, "peak": alu_peak,
                      "unit": "Tops/s (FP32 lane ops)", "frac": achieved / alu_peak, "traffic": None,
                      "peak_source": f"derived: {props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
                                     f"{sm_max:.0f} MHz"},

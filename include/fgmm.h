@@ -131,10 +131,162 @@ fgmm_status fgmm_encode(fgmm_handle *h, const fgmm_latent *lat, const int32_t *s
 fgmm_status fgmm_decode(fgmm_handle *h, const fgmm_latent *lat, const uint16_t *words, int64_t n_words,
                         const int64_t *offsets, int32_t S, int32_t *symbols_out, void *stream);
 
+/* ---- Table-based comparison coder (Sec. II-C, Eqs. 4-5) -----------------
+ * The conventional GMM coder the paper speeds up: the quantised CDF of every
+ * symbol is evaluated at every point of the alphabet j in [-255, 256] into a
+ * table (512 uint16 per symbol, O(K |Y|) work per symbol), and coding reads
+ * intervals from it; decoding binary-searches the table row. The table holds
+ * the same quantised CDF as the table-free coder, so the streams are
+ * byte-identical to fgmm_encode's.
+ * Table layout: device uint16 [N][512], 4-byte aligned, caller-owned;
+ * entry [n][j + 255] = Q_n(clamp(j, lo_n, hi_n + 1)). */
+
+/* Bytes of the table for N symbols (host-only). */
+int64_t fgmm_table_bytes(int64_t N);
+
+/* Builds the table of a latent. */
+fgmm_status fgmm_table_build(fgmm_handle *h, const fgmm_latent *lat, uint16_t *table, void *stream);
+
+/* Builds the table, then encodes from it; arguments as fgmm_encode plus the
+ * table buffer (fgmm_table_bytes(N) bytes). */
+fgmm_status fgmm_table_encode(fgmm_handle *h, const fgmm_latent *lat, const int32_t *symbols, int32_t S,
+                              uint16_t *table, uint16_t *words, int64_t words_cap, int64_t *offsets,
+                              int64_t *n_words_out, void *stream);
+
+/* Builds the table, then decodes by binary search over each table row;
+ * arguments as fgmm_decode plus the table buffer. */
+fgmm_status fgmm_table_decode(fgmm_handle *h, const fgmm_latent *lat, uint16_t *table, const uint16_t *words,
+                              int64_t n_words, const int64_t *offsets, int32_t S, int32_t *symbols_out,
+                              void *stream);
+
+/* ---- FP64 rate audit (Sec. V "no approximation" reference) --------------
+ * For a latent and its symbols, computes in FP64 on the GPU:
+ *   out[0] = sum over symbols of -log2 p64(s), p64 the exact mixture mass of
+ *            [s - 1/2, s + 1/2) with erfc (the ideal code length);
+ *   out[1] = sum of -log2(freq / 2^16) of the coder's intervals, plus 32 bits
+ *            for each escape (the coder's code length without container);
+ *   out[2] = max |F-hat32(b) - F64(b)| over the boundaries the encoder
+ *            evaluates;
+ *   out[3] = number of escapes.
+ * out is device double[4]. Rate overhead = out[1] / out[0] - 1. */
+fgmm_status fgmm_rate_audit(fgmm_handle *h, const fgmm_latent *lat, const int32_t *symbols, double *out,
+                            void *stream);
+
+/* ---- Batches: many latents in one persistent launch ---------------------
+ * A plan binds n latents and their buffers. All segments of all latents
+ * form one work list (longest latents first) that a persistent grid of warps
+ * drains through an atomic counter; encode is one such launch (the interval
+ * of each symbol evaluated inline, then rANS) followed by the offset scan and
+ * compaction over all segments, decode is one such launch. Latent i's stream
+ * is words[offsets[b_i] .. offsets[b_i + S_i/32]), b_i = sum_{j<i} S_j/32,
+ * byte-identical to fgmm_encode of that latent with S_i streams.
+ * fgmm_batch_capture records both launch sequences into CUDA graphs once;
+ * later fgmm_batch_encode/decode calls replay them. */
+typedef struct {
+    int32_t K;
+    int32_t dtype;
+    int64_t N;
+    const void *params;      /* device [3][K][N] */
+    const int32_t *symbols;  /* device int32[N]: encoder input */
+    int32_t *decoded;        /* device int32[N]: decoder output */
+} fgmm_batch_latent;
+
+typedef struct fgmm_batch fgmm_batch;
+
+/* Stream counts for a batch: the most parallel choice whose container cost
+ * (a 32-bit flushed state per stream) stays within max_overhead of the
+ * payload at bits_per_symbol, without more streams than the batch decoder
+ * runs concurrently on this GPU:
+ *   T* = max(ceil(32 / (max_overhead * bits_per_symbol)),
+ *            ceil(sum N / concurrent streams)),
+ *   S_i = clamp(roundup32(ceil(N_i / T*)), 32, roundup32(N_i)).
+ * N is host int64[n]; S_out host int32[n]. Host-only (queries occupancy). */
+fgmm_status fgmm_autotune(fgmm_handle *h, const int64_t *N, int32_t n, double max_overhead, double bits_per_symbol,
+                          int32_t *S_out);
+
+/* Creates a plan. lats: host array of n latents (device pointers inside).
+ * S_in: host int32[n] stream counts (multiples of 32), or NULL for
+ * fgmm_autotune with max_overhead 1% at 3.5 bits/symbol. words (device,
+ * words_cap entries), offsets (device int64[total segments + 1]) and
+ * n_words_out (device int64[1]) receive the encoded batch and are read by
+ * the decoder. The plan allocates its own device work list and encode
+ * scratch (about 6 bytes per symbol) here, never later. */
+fgmm_status fgmm_batch_create(fgmm_handle *h, const fgmm_batch_latent *lats, int32_t n, const int32_t *S_in,
+                              uint16_t *words, int64_t words_cap, int64_t *offsets, int64_t *n_words_out,
+                              fgmm_batch **out);
+void fgmm_batch_destroy(fgmm_batch *b);
+/* Total segments (offsets has this many + 1 entries). */
+int64_t fgmm_batch_segments(const fgmm_batch *b);
+/* Copies the stream count of every latent to host S_out[n]. */
+fgmm_status fgmm_batch_streams(const fgmm_batch *b, int32_t *S_out);
+/* Captures the encode and decode launch sequences into CUDA graphs. */
+fgmm_status fgmm_batch_capture(fgmm_batch *b);
+/* Encodes / decodes the whole batch on `stream` (graph replay if captured). */
+fgmm_status fgmm_batch_encode(fgmm_batch *b, void *stream);
+fgmm_status fgmm_batch_decode(fgmm_batch *b, void *stream);
+
+/* ---- Learned decode proposal (no counterpart in the paper) --------------
+ * A 10 -> 64 -> 64 -> 1 MLP guesses a symbol from its mixture (K = 3) and
+ * its rANS slot; fgmm_decode_proposal checks the guess against the exact
+ * quantised CDF and finishes with a galloping + binary search, so decoded
+ * symbols equal fgmm_decode's for any network weights. Features: weights,
+ * means and log-scales standardised by the mixture mean m0 and standard
+ * deviation s0 (components sorted by mean), and (slot + 1/2)/2^16 - 1/2;
+ * output y, guess round(m0 + s0 y). Activation z * sat(1/2 + (1.702/4) z).
+ * Parameter vector theta (device fp32[FGMM_MLP_PARAMS]): W1[10][64], b1[64],
+ * W2[64][64], b2[64], w3[64], b3. */
+#define FGMM_MLP_PARAMS 4929
+#define FGMM_MLP_PACKED_BYTES 11024
+
+/* Training triples: for each symbol (K = 3 latent), the slot drawn
+ * uniformly inside its interval, slot = start + min(freq - 1,
+ * floor(uniforms[n] * freq)), its features X (device fp32[N][10]), target
+ * (device fp32[N]: (s - m0)/s0 clipped to [-8, 8]) and, if slots is not
+ * NULL, the slot (device int32[N]). uniforms: device fp32[N] in [0, 1). */
+fgmm_status fgmm_mlp_data(fgmm_handle *h, const fgmm_latent *lat, const int32_t *symbols, const float *uniforms,
+                          float *X, float *target, int32_t *slots, void *stream);
+
+/* Mean squared error of the network on B samples and its gradient (FP32;
+ * per-block partial sums reduced in a fixed order, so the result is
+ * deterministic). grad: device fp32[FGMM_MLP_PARAMS]; loss: device fp32[1]. */
+fgmm_status fgmm_mlp_loss_grad(fgmm_handle *h, const float *X, const float *target, int64_t B, const float *theta,
+                               float *grad, float *loss, void *stream);
+
+/* `steps` Adam steps (beta 0.9 / 0.999, eps 1e-8, learning rate lr) over
+ * consecutive minibatches of `batch` samples from X/target (N samples,
+ * batch k = (step0 + i) mod (N / batch)); theta, adam_m, adam_v (device
+ * fp32[FGMM_MLP_PARAMS]) are updated in place; loss_trace (device
+ * fp32[steps]) receives each step's loss. Deterministic. */
+fgmm_status fgmm_mlp_train(fgmm_handle *h, const float *X, const float *target, int64_t N, float *theta,
+                           float *adam_m, float *adam_v, int64_t step0, int64_t steps, int64_t batch, float lr,
+                           float *loss_trace, void *stream);
+
+/* Converts theta to the BF16 fragment layout of the inference kernels
+ * (device, FGMM_MLP_PACKED_BYTES, 16-byte aligned). */
+fgmm_status fgmm_mlp_pack(fgmm_handle *h, const float *theta, void *packed, void *stream);
+
+/* Inference (BF16 mma.sync, FP32 accumulation) on B feature rows:
+ * y[b] = network(X[b]); X device fp32[B][10], y device fp32[B]. */
+fgmm_status fgmm_mlp_forward(fgmm_handle *h, const float *X, int64_t B, const void *packed, float *y, void *stream);
+
+/* fgmm_decode with the proposal (K = 3 latents); same arguments plus the
+ * packed network. */
+fgmm_status fgmm_decode_proposal(fgmm_handle *h, const fgmm_latent *lat, const void *packed, const uint16_t *words,
+                                 int64_t n_words, const int64_t *offsets, int32_t S, int32_t *symbols_out,
+                                 void *stream);
+
+/* Tuning options (fgmm_set_option). FGMM_OPT_DECODE_LANES: lanes that
+ * cooperate on one stream in fgmm_decode: 1 (binary search, one lane per
+ * stream), 2, 4, 8, 16 or 32 (G-ary search, G lanes per stream), or 0 to
+ * choose from the number of segments (default). The decoded symbols do not
+ * depend on it. */
+enum { FGMM_OPT_DECODE_LANES = 1 };
+fgmm_status fgmm_set_option(fgmm_handle *h, int32_t option, int64_t value);
+
 /* Optional counters. When enabled, decoders add the number of quantised-CDF
  * evaluations they make to a device counter; fgmm_stats_read synchronises
- * `stream` and copies {cdf_evals, symbols_decoded} to host out[2], then
- * zeroes the counters. */
+ * `stream` and copies {cdf_evals, symbols_decoded, proposal_hits} to host
+ * out[3], then zeroes the counters. */
 fgmm_status fgmm_stats_enable(fgmm_handle *h, int32_t on);
 fgmm_status fgmm_stats_read(fgmm_handle *h, uint64_t *out, void *stream);
 

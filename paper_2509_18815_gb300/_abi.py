@@ -25,6 +25,9 @@ FGMM_NOALLOC_SCRATCH_BYTES = 16 << 20
 FGMM_DTYPE_F32 = 0
 FGMM_DTYPE_BF16 = 1
 FGMM_MAX_K = 4
+FGMM_OPT_DECODE_LANES = 1
+FGMM_MLP_PARAMS = 4929
+FGMM_MLP_PACKED_BYTES = 11024
 
 
 class fgmm_latent(ctypes.Structure):
@@ -36,6 +39,11 @@ P = ctypes.c_void_p
 I32 = ctypes.c_int32
 I64 = ctypes.c_int64
 LATP = ctypes.POINTER(fgmm_latent)
+
+
+class fgmm_batch_latent(ctypes.Structure):
+    _fields_ = [("K", ctypes.c_int32), ("dtype", ctypes.c_int32), ("N", ctypes.c_int64),
+                ("params", ctypes.c_void_p), ("symbols", ctypes.c_void_p), ("decoded", ctypes.c_void_p)]
 
 # name -> (restype, argtypes); every function include/fgmm.h declares.
 SIGNATURES = {
@@ -52,6 +60,26 @@ SIGNATURES = {
     "fgmm_decode": (I32, [P, LATP, P, I64, P, I32, P, P]),
     "fgmm_stats_enable": (I32, [P, I32]),
     "fgmm_stats_read": (I32, [P, P, P]),
+    "fgmm_set_option": (I32, [P, I32, I64]),
+    "fgmm_table_bytes": (I64, [I64]),
+    "fgmm_table_build": (I32, [P, LATP, P, P]),
+    "fgmm_table_encode": (I32, [P, LATP, P, I32, P, P, I64, P, P, P]),
+    "fgmm_table_decode": (I32, [P, LATP, P, P, I64, P, I32, P, P]),
+    "fgmm_rate_audit": (I32, [P, LATP, P, P, P]),
+    "fgmm_autotune": (I32, [P, P, I32, ctypes.c_double, ctypes.c_double, P]),
+    "fgmm_batch_create": (I32, [P, P, I32, P, P, I64, P, P, ctypes.POINTER(P)]),
+    "fgmm_batch_destroy": (None, [P]),
+    "fgmm_batch_segments": (I64, [P]),
+    "fgmm_batch_streams": (I32, [P, P]),
+    "fgmm_batch_capture": (I32, [P]),
+    "fgmm_batch_encode": (I32, [P, P]),
+    "fgmm_batch_decode": (I32, [P, P]),
+    "fgmm_mlp_data": (I32, [P, LATP, P, P, P, P, P, P]),
+    "fgmm_mlp_loss_grad": (I32, [P, P, P, I64, P, P, P, P]),
+    "fgmm_mlp_train": (I32, [P, P, P, I64, P, P, P, I64, I64, I64, ctypes.c_float, P, P]),
+    "fgmm_mlp_pack": (I32, [P, P, P, P]),
+    "fgmm_mlp_forward": (I32, [P, P, I64, P, P, P]),
+    "fgmm_decode_proposal": (I32, [P, LATP, P, P, I64, P, I32, P, P]),
     "fgmm_encode_noalloc": (I32, [LATP, P, I32, P, I64, P, P, P, P]),
 }
 

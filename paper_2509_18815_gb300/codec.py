@@ -161,9 +161,253 @@ def stats_enable(on: bool = True, h: Handle | None = None):
     h.check(_abi.fgmm_stats_enable(h.ptr, 1 if on else 0))
 
 
-def stats_read(h: Handle | None = None):
-    """(cdf_evals, symbols_decoded) since the last read."""
+def stats_read(h: Handle | None = None, with_hits: bool = False):
+    """(cdf_evals, symbols_decoded[, proposal_hits]) since the last read."""
     h = h or handle()
-    out = (ctypes.c_uint64 * 2)()
+    out = (ctypes.c_uint64 * 3)()
     h.check(_abi.fgmm_stats_read(h.ptr, out, _stream()))
+    if with_hits:
+        return int(out[0]), int(out[1]), int(out[2])
     return int(out[0]), int(out[1])
+
+
+def table_build(params: torch.Tensor, h: Handle | None = None) -> torch.Tensor:
+    """Quantised-CDF table [N, 512] (uint16 bits in int16) of the comparison coder."""
+    h = h or handle(params.device)
+    lat = latent(params)
+    table = torch.empty((lat.N, 512), dtype=torch.int16, device=params.device)
+    h.check(_abi.fgmm_table_build(h.ptr, ctypes.byref(lat), _ptr(table), _stream()))
+    h.sync()
+    return table
+
+
+def table_encode(params, symbols, S, table=None, h: Handle | None = None, sync: bool = True):
+    """Table-based encode (same stream as encode()). Returns (words, offsets)."""
+    h = h or handle(params.device)
+    lat = latent(params)
+    sym = symbols.to(torch.int32).contiguous()
+    if table is None:
+        table = torch.empty((lat.N, 512), dtype=torch.int16, device=params.device)
+    cap = encode_bound_words(lat.N, S)
+    words = torch.empty(max(cap, 1), dtype=torch.int16, device=params.device)
+    offsets = torch.empty(S // 32 + 1, dtype=torch.int64, device=params.device)
+    total = torch.empty(1, dtype=torch.int64, device=params.device)
+    h.check(_abi.fgmm_table_encode(h.ptr, ctypes.byref(lat), _ptr(sym), S, _ptr(table), _ptr(words), cap,
+                                   _ptr(offsets), _ptr(total), _stream()))
+    if not sync:
+        return words, offsets, total
+    h.sync()
+    return words[: int(total.item())], offsets
+
+
+def table_decode(params, words, offsets, S, table=None, h: Handle | None = None, out=None, sync: bool = True):
+    """Table-based decode (builds the table, then searches it)."""
+    h = h or handle(params.device)
+    lat = latent(params)
+    if table is None:
+        table = torch.empty((lat.N, 512), dtype=torch.int16, device=params.device)
+    if out is None:
+        out = torch.empty(lat.N, dtype=torch.int32, device=params.device)
+    words = words.contiguous()
+    offsets = offsets.to(torch.int64).contiguous()
+    h.check(_abi.fgmm_table_decode(h.ptr, ctypes.byref(lat), _ptr(table), _ptr(words), words.numel(), _ptr(offsets),
+                                   S, _ptr(out), _stream()))
+    if sync:
+        h.sync()
+    return out
+
+
+def rate_audit(params, symbols, h: Handle | None = None):
+    """(ideal_bits, coded_bits, max_cdf_err, n_escape) computed in FP64 on the GPU."""
+    h = h or handle(params.device)
+    lat = latent(params)
+    sym = symbols.to(torch.int32).contiguous()
+    out = torch.empty(4, dtype=torch.float64, device=params.device)
+    h.check(_abi.fgmm_rate_audit(h.ptr, ctypes.byref(lat), _ptr(sym), _ptr(out), _stream()))
+    h.sync()
+    v = out.cpu().tolist()
+    return v[0], v[1], v[2], int(v[3])
+
+
+def autotune(Ns, max_overhead: float = 0.01, bits_per_symbol: float = 3.5, h: Handle | None = None):
+    """Stream counts for a batch of latents with N symbols each (see
+    fgmm_autotune in include/fgmm.h)."""
+    h = h or handle()
+    n = len(Ns)
+    arr = (ctypes.c_int64 * max(n, 1))(*[int(x) for x in Ns])
+    out = (ctypes.c_int32 * max(n, 1))()
+    h.check(_abi.fgmm_autotune(h.ptr, arr, n, max_overhead, bits_per_symbol, out))
+    return [int(out[i]) for i in range(n)]
+
+
+class Batch:
+    """A batch plan (fgmm_batch): n latents coded by one persistent launch per
+    direction, optionally replayed from captured CUDA graphs.
+
+    params: list of CUDA tensors [3, K, N]; symbols: list of int32 CUDA
+    tensors [N]. After encode(), `words`, `offsets`, `n_words` hold the batch
+    stream; decode() writes `decoded` (list of int32 tensors)."""
+
+    def __init__(self, params, symbols, S=None, h: Handle | None = None, words_cap: int | None = None):
+        self.h = h or handle(params[0].device if params else None)
+        dev = params[0].device
+        n = len(params)
+        self.params = [p.contiguous() for p in params]
+        self.symbols = [s.to(torch.int32).contiguous() for s in symbols]
+        self.decoded = [torch.empty(int(p.shape[2]), dtype=torch.int32, device=dev) for p in self.params]
+        lats = (_abi.fgmm_batch_latent * max(n, 1))()
+        for i, (p, s, d) in enumerate(zip(self.params, self.symbols, self.decoded)):
+            base = latent(p)
+            lats[i] = _abi.fgmm_batch_latent(base.K, base.dtype, base.N, base.params, s.data_ptr(), d.data_ptr())
+        s_arr = None
+        if S is not None:
+            s_arr = (ctypes.c_int32 * max(n, 1))(*[int(x) for x in S])
+        total_bound = 0
+        Ss = S if S is not None else autotune([int(p.shape[2]) for p in self.params], h=self.h)
+        for p, si in zip(self.params, Ss):
+            total_bound += encode_bound_words(int(p.shape[2]), si)
+        cap = total_bound if words_cap is None else words_cap
+        self.words = torch.empty(max(cap, 1), dtype=torch.int16, device=dev)
+        nseg = sum(si // 32 for si in Ss)
+        self.offsets = torch.empty(nseg + 1, dtype=torch.int64, device=dev)
+        self.total = torch.empty(1, dtype=torch.int64, device=dev)
+        ptr = ctypes.c_void_p()
+        self.h.check(_abi.fgmm_batch_create(self.h.ptr, lats, n, s_arr if s_arr is not None else None,
+                                            _ptr(self.words), cap, _ptr(self.offsets), _ptr(self.total),
+                                            ctypes.byref(ptr)))
+        self.ptr = ptr
+        out = (ctypes.c_int32 * max(n, 1))()
+        self.h.check(_abi.fgmm_batch_streams(self.ptr, out))
+        self.S = [int(out[i]) for i in range(n)]
+        assert self.S == list(Ss)
+        self.seg_base = [0]
+        for si in self.S:
+            self.seg_base.append(self.seg_base[-1] + si // 32)
+
+    def capture(self):
+        self.h.check(_abi.fgmm_batch_capture(self.ptr))
+
+    def encode(self, sync: bool = True):
+        self.h.check(_abi.fgmm_batch_encode(self.ptr, _stream()))
+        if sync:
+            self.h.sync()
+
+    def decode(self, sync: bool = True):
+        self.h.check(_abi.fgmm_batch_decode(self.ptr, _stream()))
+        if sync:
+            self.h.sync()
+
+    def latent_stream(self, i: int):
+        """(words, offsets) of latent i, in the single-latent format."""
+        off = self.offsets[self.seg_base[i]: self.seg_base[i + 1] + 1]
+        a, b = int(off[0].item()), int(off[-1].item())
+        return self.words[a:b], off - a
+
+    def close(self):
+        if self.ptr:
+            _abi.fgmm_batch_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------------------
+# Learned decode proposal
+# ---------------------------------------------------------------------------
+
+def mlp_data(params, symbols, uniforms, h: Handle | None = None, with_slots: bool = False):
+    """Training triples (features X [N, 10], target [N][, slots [N]])."""
+    h = h or handle(params.device)
+    lat = latent(params)
+    dev = params.device
+    X = torch.empty((lat.N, 10), dtype=torch.float32, device=dev)
+    t = torch.empty(lat.N, dtype=torch.float32, device=dev)
+    sl = torch.empty(lat.N, dtype=torch.int32, device=dev) if with_slots else None
+    u = uniforms.to(torch.float32).contiguous()
+    sym = symbols.to(torch.int32).contiguous()
+    h.check(_abi.fgmm_mlp_data(h.ptr, ctypes.byref(lat), _ptr(sym), _ptr(u), _ptr(X), _ptr(t),
+                               _ptr(sl) if sl is not None else None, _stream()))
+    h.sync()
+    return (X, t, sl) if with_slots else (X, t)
+
+
+def mlp_loss_grad(X, target, theta, h: Handle | None = None):
+    h = h or handle(X.device)
+    g = torch.empty(_abi.FGMM_MLP_PARAMS, dtype=torch.float32, device=X.device)
+    loss = torch.empty(1, dtype=torch.float32, device=X.device)
+    h.check(_abi.fgmm_mlp_loss_grad(h.ptr, _ptr(X.contiguous()), _ptr(target.contiguous()), X.shape[0],
+                                    _ptr(theta), _ptr(g), _ptr(loss), _stream()))
+    h.sync()
+    return float(loss.item()), g
+
+
+class MlpTrainer:
+    """FP32 master weights and Adam state of the proposal network on the GPU.
+    state_dict()/load_state_dict() checkpoint and resume training exactly."""
+
+    def __init__(self, theta0, device="cuda", h: Handle | None = None):
+        self.h = h or handle(device)
+        self.theta = torch.as_tensor(theta0, dtype=torch.float32).to(device).contiguous()
+        self.m = torch.zeros_like(self.theta)
+        self.v = torch.zeros_like(self.theta)
+        self.step = 0
+
+    def train(self, X, target, steps: int, batch: int, lr: float):
+        trace = torch.empty(max(steps, 1), dtype=torch.float32, device=self.theta.device)
+        self.h.check(_abi.fgmm_mlp_train(self.h.ptr, _ptr(X), _ptr(target), X.shape[0], _ptr(self.theta),
+                                         _ptr(self.m), _ptr(self.v), self.step, steps, batch, lr, _ptr(trace),
+                                         _stream()))
+        self.h.sync()
+        self.step += steps
+        return trace[:steps]
+
+    def state_dict(self):
+        return {"theta": self.theta.cpu().clone(), "m": self.m.cpu().clone(), "v": self.v.cpu().clone(),
+                "step": self.step}
+
+    def load_state_dict(self, st):
+        dev = self.theta.device
+        self.theta = st["theta"].to(dev).contiguous()
+        self.m = st["m"].to(dev).contiguous()
+        self.v = st["v"].to(dev).contiguous()
+        self.step = int(st["step"])
+
+    def packed(self):
+        P = torch.empty(_abi.FGMM_MLP_PACKED_BYTES // 4, dtype=torch.int32, device=self.theta.device)
+        self.h.check(_abi.fgmm_mlp_pack(self.h.ptr, _ptr(self.theta), _ptr(P), _stream()))
+        self.h.sync()
+        return P
+
+
+def mlp_pack(theta, h: Handle | None = None):
+    h = h or handle(theta.device)
+    P = torch.empty(_abi.FGMM_MLP_PACKED_BYTES // 4, dtype=torch.int32, device=theta.device)
+    h.check(_abi.fgmm_mlp_pack(h.ptr, _ptr(theta.contiguous()), _ptr(P), _stream()))
+    h.sync()
+    return P
+
+
+def mlp_forward(X, packed, h: Handle | None = None):
+    h = h or handle(X.device)
+    y = torch.empty(X.shape[0], dtype=torch.float32, device=X.device)
+    h.check(_abi.fgmm_mlp_forward(h.ptr, _ptr(X.contiguous()), X.shape[0], _ptr(packed), _ptr(y), _stream()))
+    h.sync()
+    return y
+
+
+def decode_proposal(params, words, offsets, S, packed, h: Handle | None = None, out=None, sync: bool = True):
+    h = h or handle(params.device)
+    lat = latent(params)
+    if out is None:
+        out = torch.empty(lat.N, dtype=torch.int32, device=params.device)
+    words = words.contiguous()
+    offsets = offsets.to(torch.int64).contiguous()
+    h.check(_abi.fgmm_decode_proposal(h.ptr, ctypes.byref(lat), _ptr(packed), _ptr(words), words.numel(),
+                                      _ptr(offsets), S, _ptr(out), _stream()))
+    if sync:
+        h.sync()
+    return out

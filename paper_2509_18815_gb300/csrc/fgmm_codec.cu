@@ -11,9 +11,7 @@
 //   3. fgmm_scan_kernel: exclusive prefix sum of the segment lengths.
 //   4. fgmm_compact_kernel: copies segments to their offsets.
 // Decode (Sec. III-A: binary search over the same on-the-fly CDF) is one
-// launch, fgmm_rans_dec_kernel: one warp per segment, one lane per stream,
-// steps 0 .. T-1, each step a binary search over the symbol's quantised CDF
-// followed by the inverse rANS step and a ballot-ranked backward refill.
+// launch of a kernel in fgmm_decode.cu.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -181,93 +179,6 @@ __global__ void __launch_bounds__(256) fgmm_compact_kernel(const uint16_t* __res
 }
 
 // ---------------------------------------------------------------------------
-// Decoder, one warp per segment.
-// ---------------------------------------------------------------------------
-
-// Refill after a decode sub-phase: the lanes (among `part`) whose state fell
-// below 2^16 take the last c unread words, the lane of rank r word ptr-c+r.
-// A read below the segment start is never performed; it marks the stream bad.
-__device__ __forceinline__ void dec_refill(uint32_t& x, bool part, const uint16_t* __restrict__ words,
-                                           int64_t& ptr, int64_t beg, bool& bad, uint32_t lt)
-{
-    const bool need = part && x < kL;
-    const uint32_t m = __ballot_sync(kFull, need);
-    if (m) {
-        const int c = __popc(m);
-        if (need) {
-            const int64_t idx = ptr - c + __popc(m & lt);
-            uint32_t w = 0;
-            if (idx >= beg) w = __ldg(words + idx);
-            else bad = true;
-            x = (x << 16) | w;
-        }
-        ptr -= c;
-    }
-}
-
-template <int K, typename T>
-__global__ void __launch_bounds__(64) fgmm_rans_dec_kernel(const T* __restrict__ params, int64_t N, int32_t S,
-                                                           int64_t T_steps, const uint16_t* __restrict__ words,
-                                                           int64_t n_words, const int64_t* __restrict__ offsets,
-                                                           int64_t nseg, int32_t* __restrict__ out, int32_t* err,
-                                                           unsigned long long* stats)
-{
-    const int64_t g = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (g >= nseg) return;
-    const int64_t beg = offsets[g], end = offsets[g + 1];
-    if (!(beg >= 0 && end <= n_words && end - beg >= 64)) {
-        if (lane == 0) set_error(err, kErrCorrupt);
-        return;
-    }
-    const uint32_t lt = lanemask_lt();
-    uint32_t x = (uint32_t)__ldg(words + end - 64 + 2 * lane) | ((uint32_t)__ldg(words + end - 63 + 2 * lane) << 16);
-    int64_t ptr = end - 64;
-    bool bad = false, badp = false;
-    int probes = 0, decoded = 0;
-    int64_t n = g * 32 + lane;
-    for (int64_t t = 0; t < T_steps; ++t, n += S) {
-        const bool act = n < N;
-        int32_t s = 0;
-        bool esc = false;
-        if (act) {
-            ++decoded;
-            Mix<K> m;
-            badp |= !load_mix<K>(params, N, n, m);
-            const uint32_t slot = x & 0xffffu;
-            uint32_t st, fr;
-            esc = search_slot<K>(m, slot, s, st, fr, probes);
-            x = fr * (x >> 16) + slot - st;
-        }
-        dec_refill(x, act, words, ptr, beg, bad, lt);
-        if (__ballot_sync(kFull, esc)) {
-            uint32_t hi16 = 0, lo16 = 0;
-            if (esc) { hi16 = x & 0xffffu; x >>= 16; }
-            dec_refill(x, esc, words, ptr, beg, bad, lt);
-            if (esc) { lo16 = x & 0xffffu; x >>= 16; }
-            dec_refill(x, esc, words, ptr, beg, bad, lt);
-            if (esc) s = (int32_t)((hi16 << 16) | lo16);
-        }
-        if (act) out[n] = s;
-    }
-    const bool fail = bad || x != kL || ptr != beg;
-    if (__ballot_sync(kFull, fail) && lane == 0) set_error(err, kErrCorrupt);
-    if (__ballot_sync(kFull, badp) && lane == 0) set_error(err, kErrBadParams);
-    if (stats) {
-        int p = probes, d = decoded;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            p += __shfl_xor_sync(kFull, p, o);
-            d += __shfl_xor_sync(kFull, d, o);
-        }
-        if (lane == 0) {
-            atomicAdd(stats, (unsigned long long)p);
-            atomicAdd(stats + 1, (unsigned long long)d);
-        }
-    }
-}
-
-// ---------------------------------------------------------------------------
 // Host-side dispatch helpers.
 // ---------------------------------------------------------------------------
 inline int grid_for(int64_t n, int threads, int max_blocks)
@@ -311,32 +222,6 @@ void launch_interval_any(const fgmm_latent* lat, const int32_t* sym, uint32_t* s
 // segments do not fill the SMs, so that each warp has an SM to itself.
 inline int seg_threads(int64_t nseg, int sms) { return nseg <= 2 * (int64_t)sms ? 32 : 64; }
 
-template <int K, typename T>
-void launch_dec(const fgmm_latent* lat, int32_t S, const uint16_t* words, int64_t n_words, const int64_t* offsets,
-                int32_t* out, int32_t* err, unsigned long long* stats, int sms, cudaStream_t st)
-{
-    const int64_t nseg = S / 32;
-    const int64_t steps = (lat->N + S - 1) / S;
-    const int threads = seg_threads(nseg, sms);
-    const int64_t blocks = (nseg * 32 + threads - 1) / threads;
-    fgmm_rans_dec_kernel<K, T><<<(unsigned)blocks, threads, 0, st>>>(static_cast<const T*>(lat->params), lat->N, S,
-                                                                      steps, words, n_words, offsets, nseg, out, err,
-                                                                      stats);
-}
-
-template <typename T>
-void dispatch_dec(const fgmm_latent* lat, int32_t S, const uint16_t* words, int64_t n_words, const int64_t* offsets,
-                  int32_t* out, int32_t* err, unsigned long long* stats, int sms, cudaStream_t st)
-{
-    switch (lat->K) {
-    case 1: launch_dec<1, T>(lat, S, words, n_words, offsets, out, err, stats, sms, st); break;
-    case 2: launch_dec<2, T>(lat, S, words, n_words, offsets, out, err, stats, sms, st); break;
-    case 3: launch_dec<3, T>(lat, S, words, n_words, offsets, out, err, stats, sms, st); break;
-    default: launch_dec<4, T>(lat, S, words, n_words, offsets, out, err, stats, sms, st); break;
-    }
-}
-
-inline int64_t steps_of(int64_t N, int32_t S) { return N > 0 ? (N + S - 1) / S : 0; }
 
 // Per-segment scratch capacity: at most three words per lane and step (an
 // escape emits for two chunks and the main symbol) plus the flush block;
@@ -367,6 +252,44 @@ fgmm_status ws_reserve(fgmm_handle* h, size_t bytes, cudaStream_t stream)
     }
     h->ws_bytes = want;
     return FGMM_OK;
+}
+
+fgmm_status encode_reserve(fgmm_handle* h, int64_t N, int32_t S, cudaStream_t st, EncodeWs* ws)
+{
+    const int64_t nseg = S / 32, T = steps_of(N, S);
+    const int64_t cap = seg_cap_words(T);
+    // workspace: intervals [N] u32 | segment scratch [nseg][cap] u16 | lengths [nseg] i64
+    const size_t o_sf = 0;
+    const size_t o_seg = align_up(o_sf + sizeof(uint32_t) * (size_t)N, 256);
+    const size_t o_len = align_up(o_seg + sizeof(uint16_t) * (size_t)(nseg * cap), 256);
+    const size_t bytes = o_len + sizeof(int64_t) * (size_t)nseg;
+    fgmm_status s = ws_reserve(h, bytes, st);
+    if (s != FGMM_OK) return s;
+    char* base = static_cast<char*>(h->ws);
+    ws->sf = reinterpret_cast<uint32_t*>(base + o_sf);
+    ws->seg = reinterpret_cast<uint16_t*>(base + o_seg);
+    ws->len = reinterpret_cast<int64_t*>(base + o_len);
+    ws->cap = cap;
+    return FGMM_OK;
+}
+
+void encode_from_intervals(const EncodeWs& ws, const int32_t* symbols, int64_t N, int32_t S, uint16_t* words,
+                           int64_t words_cap, int64_t* offsets, int64_t* n_words_out, int32_t* err, int sms,
+                           cudaStream_t st)
+{
+    const int64_t nseg = S / 32, T = steps_of(N, S);
+    const int thr = seg_threads(nseg, sms);
+    fgmm_rans_enc_kernel<<<(unsigned)((nseg * 32 + thr - 1) / thr), thr, 0, st>>>(ws.sf, symbols, N, S, T, ws.seg,
+                                                                                  ws.cap, ws.len, nseg);
+    fgmm_scan_kernel<<<1, 1024, 0, st>>>(ws.len, nseg, offsets, n_words_out, words_cap, err);
+    fgmm_compact_kernel<<<grid_for(nseg * 32, 256, sms * 8), 256, 0, st>>>(ws.seg, ws.cap, ws.len, offsets, nseg,
+                                                                            words, words_cap);
+}
+
+void launch_scan(const int64_t* len, int64_t nseg, int64_t* offsets, int64_t* total_out, int64_t cap, int32_t* err,
+                 cudaStream_t st)
+{
+    fgmm_scan_kernel<<<1, 1024, 0, st>>>(len, nseg, offsets, total_out, cap, err);
 }
 
 fgmm_status check_latent(fgmm_handle* h, const fgmm_latent* lat)
@@ -467,12 +390,13 @@ fgmm_status fgmm_stats_read(fgmm_handle* h, uint64_t* out, void* stream)
     if (!h || !out) return FGMM_ERR_INVALID_ARG;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaError_t e = cudaStreamSynchronize(st);
-    unsigned long long v[2] = {0, 0};
+    unsigned long long v[3] = {0, 0, 0};
     if (e == cudaSuccess) e = cudaMemcpy(v, h->d_stats, sizeof v, cudaMemcpyDeviceToHost);
-    if (e == cudaSuccess) e = cudaMemset(h->d_stats, 0, 2 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(h->d_stats, 0, 3 * sizeof(unsigned long long));
     if (e != cudaSuccess) return cuda_fail(h, e, "fgmm_stats_read");
     out[0] = v[0];
     out[1] = v[1];
+    out[2] = v[2];
     return FGMM_OK;
 }
 
@@ -526,27 +450,11 @@ fgmm_status fgmm_encode(fgmm_handle* h, const fgmm_latent* lat, const int32_t* s
     if (!offsets || !n_words_out || words_cap < 0 || (words_cap > 0 && !words) || (lat->N > 0 && !symbols))
         return fail(h, FGMM_ERR_INVALID_ARG, "fgmm_encode: NULL buffer");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const int64_t N = lat->N, nseg = S / 32, T = steps_of(N, S);
-    const int64_t cap = seg_cap_words(T);
-    // workspace: intervals [N] u32 | segment scratch [nseg][cap] u16 | lengths [nseg] i64
-    const size_t o_sf = 0;
-    const size_t o_seg = align_up(o_sf + sizeof(uint32_t) * (size_t)N, 256);
-    const size_t o_len = align_up(o_seg + sizeof(uint16_t) * (size_t)(nseg * cap), 256);
-    const size_t bytes = o_len + sizeof(int64_t) * (size_t)nseg;
-    s = ws_reserve(h, bytes, st);
+    EncodeWs ws;
+    s = encode_reserve(h, lat->N, S, st, &ws);
     if (s != FGMM_OK) return s;
-    char* ws = static_cast<char*>(h->ws);
-    uint32_t* sf = reinterpret_cast<uint32_t*>(ws + o_sf);
-    uint16_t* seg = reinterpret_cast<uint16_t*>(ws + o_seg);
-    int64_t* len = reinterpret_cast<int64_t*>(ws + o_len);
-
-    launch_interval_any(lat, symbols, sf, h->d_err, h->num_sms, st);
-    const int thr = seg_threads(nseg, h->num_sms);
-    fgmm_rans_enc_kernel<<<(unsigned)((nseg * 32 + thr - 1) / thr), thr, 0, st>>>(sf, symbols, N, S, T, seg, cap,
-                                                                                  len, nseg);
-    fgmm_scan_kernel<<<1, 1024, 0, st>>>(len, nseg, offsets, n_words_out, words_cap, h->d_err);
-    fgmm_compact_kernel<<<grid_for(nseg * 32, 256, h->num_sms * 8), 256, 0, st>>>(seg, cap, len, offsets, nseg,
-                                                                                  words, words_cap);
+    launch_interval_any(lat, symbols, ws.sf, h->d_err, h->num_sms, st);
+    encode_from_intervals(ws, symbols, lat->N, S, words, words_cap, offsets, n_words_out, h->d_err, h->num_sms, st);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? FGMM_OK : cuda_fail(h, e, "fgmm_encode launch");
 }
@@ -560,13 +468,35 @@ fgmm_status fgmm_decode(fgmm_handle* h, const fgmm_latent* lat, const uint16_t* 
     if (!offsets || n_words < 0 || (n_words > 0 && !words) || (lat->N > 0 && !symbols_out))
         return fail(h, FGMM_ERR_INVALID_ARG, "fgmm_decode: NULL buffer");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    unsigned long long* stats = h->stats_on ? h->d_stats : nullptr;
-    if (lat->dtype == FGMM_DTYPE_BF16)
-        dispatch_dec<__nv_bfloat16>(lat, S, words, n_words, offsets, symbols_out, h->d_err, stats, h->num_sms, st);
-    else
-        dispatch_dec<float>(lat, S, words, n_words, offsets, symbols_out, h->d_err, stats, h->num_sms, st);
-    cudaError_t e = cudaGetLastError();
+    DecodeArgs a;
+    a.params = lat->params;
+    a.N = lat->N;
+    a.S = S;
+    a.T = steps_of(lat->N, S);
+    a.words = words;
+    a.n_words = n_words;
+    a.offsets = offsets;
+    a.nseg = S / 32;
+    a.out = symbols_out;
+    a.err = h->d_err;
+    a.stats = h->stats_on ? h->d_stats : nullptr;
+    const int lanes = h->decode_lanes > 0 ? h->decode_lanes : decode_lanes_auto(a.nseg, h->num_sms);
+    cudaError_t e = launch_decode(a, lat->K, lat->dtype, lanes, st);
     return e == cudaSuccess ? FGMM_OK : cuda_fail(h, e, "fgmm_decode launch");
+}
+
+fgmm_status fgmm_set_option(fgmm_handle* h, int32_t option, int64_t value)
+{
+    if (!h) return FGMM_ERR_INVALID_ARG;
+    switch (option) {
+    case FGMM_OPT_DECODE_LANES:
+        if (!(value == 0 || value == 1 || value == 2 || value == 4 || value == 8 || value == 16 || value == 32))
+            return fail(h, FGMM_ERR_INVALID_ARG, "decode lanes must be 0 (auto), 1, 2, 4, 8, 16 or 32");
+        h->decode_lanes = (int)value;
+        return FGMM_OK;
+    default:
+        return fail(h, FGMM_ERR_INVALID_ARG, "unknown option");
+    }
 }
 
 }  // extern "C"

@@ -217,4 +217,26 @@ __device__ __forceinline__ uint32_t lanemask_lt()
     return m;
 }
 
+// Warp-level refill after a decode sub-phase (one lane per stream, 32
+// streams per warp): the lanes (among `part`) whose state fell below 2^16
+// take the last c unread words, the lane of rank r word ptr - c + r. A read
+// below the segment start is never performed; it marks the stream bad.
+__device__ __forceinline__ void refill_warp(uint32_t& x, bool part, const uint16_t* __restrict__ words,
+                                            int64_t& ptr, int64_t beg, bool& bad, uint32_t lt)
+{
+    const bool need = part && x < kL;
+    const uint32_t m = __ballot_sync(0xffffffffu, need);
+    if (m) {
+        const int c = __popc(m);
+        if (need) {
+            const int64_t idx = ptr - c + __popc(m & lt);
+            uint32_t w = 0;
+            if (idx >= beg) w = __ldg(words + idx);
+            else bad = true;
+            x = (x << 16) | w;
+        }
+        ptr -= c;
+    }
+}
+
 }  // namespace fgmm

@@ -17,6 +17,7 @@ struct fgmm_handle {
     void* ws = nullptr;                // reusable workspace
     size_t ws_bytes = 0;
     int num_sms = 0;
+    int decode_lanes = 0;              // 0 = automatic; else lanes per stream (1, 2, 4, 8, 16, 32)
     std::string last_error;
 };
 
@@ -47,5 +48,41 @@ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 // Checks the latent descriptor on the host.
 fgmm_status check_latent(fgmm_handle* h, const fgmm_latent* lat);
+
+// Encode stages shared by fgmm_encode and the table coder (fgmm_codec.cu):
+// workspace for per-symbol intervals, per-segment word buffers and lengths;
+// then rANS encode of the intervals, offset scan and compaction.
+struct EncodeWs {
+    uint32_t* sf;
+    uint16_t* seg;
+    int64_t* len;
+    int64_t cap;
+};
+fgmm_status encode_reserve(fgmm_handle* h, int64_t N, int32_t S, cudaStream_t st, EncodeWs* ws);
+void encode_from_intervals(const EncodeWs& ws, const int32_t* symbols, int64_t N, int32_t S, uint16_t* words,
+                           int64_t words_cap, int64_t* offsets, int64_t* n_words_out, int32_t* err, int sms,
+                           cudaStream_t st);
+// Exclusive scan of nseg segment lengths into offsets[0..nseg], total into
+// *total_out; records FGMM_ERR_CAPACITY if the total exceeds cap.
+void launch_scan(const int64_t* len, int64_t nseg, int64_t* offsets, int64_t* total_out, int64_t cap, int32_t* err,
+                 cudaStream_t st);
+inline int64_t steps_of(int64_t N, int32_t S) { return N > 0 ? (N + S - 1) / S : 0; }
+
+// Decoder launch (fgmm_decode.cu).
+struct DecodeArgs {
+    const void* params;
+    int64_t N;
+    int32_t S;
+    int64_t T;
+    const uint16_t* words;
+    int64_t n_words;
+    const int64_t* offsets;
+    int64_t nseg;
+    int32_t* out;
+    int32_t* err;
+    unsigned long long* stats;
+};
+int decode_lanes_auto(int64_t nseg, int num_sms);
+cudaError_t launch_decode(const DecodeArgs& a, int K, int dtype, int lanes, cudaStream_t st);
 
 }  // namespace fgmm

@@ -173,6 +173,64 @@ def test_bad_params_and_capacity():
     np.testing.assert_array_equal(codec.decode(dp, words, off, 32).cpu().numpy(), lat.symbols)
 
 
+def _set_lanes(G):
+    from paper_2509_18815_gb300 import _abi
+    codec = _codec()
+    h = codec.handle()
+    h.check(_abi.fgmm_set_option(h.ptr, _abi.FGMM_OPT_DECODE_LANES, G))
+
+
+DECODE_CASES = [
+    # (C, H, W, K, seed, escape_stress, sigma_max, S, bf16, N_cut)
+    (8, 32, 32, 3, 500, 0.02, 16.0, 128, False, None),    # escapes, 16-byte staging
+    (1, 1, 70001, 4, 501, 0.001, 64.0, 64, True, None),   # bf16, odd N: plain staging
+    (1, 1, 4097, 2, 502, 0.0, 16.0, 1024, False, None),   # N % 4 = 1: 4-byte staging, mostly idle lanes
+    (192, 32, 48, 3, 1002, 0.0, 16.0, 1024, False, None),  # the bench latent
+    (4, 16, 16, 1, 503, 0.01, 16.0, 32, True, 1002),      # K = 1, bf16, 2N % 16 = 4: 4-byte staging
+]
+
+
+@pytest.mark.parametrize("case", range(len(DECODE_CASES)))
+@pytest.mark.parametrize("G", [1, 2, 4, 8, 16, 32])
+def test_decode_lanes_give_identical_symbols(case, G):
+    codec = _codec()
+    C, H, W, K, seed, esc, smax, S, bf16, cut = DECODE_CASES[case]
+    lat = synth.make_latent(C, H, W, K, seed=seed, escape_stress=esc, sigma_max=smax)
+    p, s = lat.params, lat.symbols
+    if cut is not None:
+        p, s = np.ascontiguousarray(p[:, :, :cut]), np.ascontiguousarray(s[:cut])
+    dp, ds = dev_params(p, bf16), dev_i32(s)
+    words, off = codec.encode(dp, ds, S)
+    try:
+        _set_lanes(G)
+        out = codec.decode(dp, words, off, S).cpu().numpy()
+    finally:
+        _set_lanes(0)
+    np.testing.assert_array_equal(out, s)
+
+
+@pytest.mark.parametrize("G", [1, 8, 32])
+def test_decode_lanes_report_corruption(G):
+    codec = _codec()
+    from paper_2509_18815_gb300._abi import FGMM_ERR_CORRUPT, FgmmError
+    lat = synth.make_latent(4, 16, 16, 3, seed=504)
+    dp, ds = dev_params(lat.params), dev_i32(lat.symbols)
+    words, off = codec.encode(dp, ds, 64)
+    junk = torch.randint(-32768, 32767, words.shape, dtype=torch.int16, device="cuda")
+    try:
+        _set_lanes(G)
+        with pytest.raises(FgmmError) as e:
+            codec.decode(dp, junk, off, 64)
+        assert e.value.status == FGMM_ERR_CORRUPT
+        with pytest.raises(FgmmError) as e:
+            codec.decode(dp, words[:-3], off, 64)
+        assert e.value.status == FGMM_ERR_CORRUPT
+        out = codec.decode(dp, words, off, 64).cpu().numpy()
+    finally:
+        _set_lanes(0)
+    np.testing.assert_array_equal(out, lat.symbols)
+
+
 def test_decode_counts_cdf_evaluations():
     codec = _codec()
     lat = synth.make_latent(8, 16, 16, 3, seed=402)
@@ -180,7 +238,11 @@ def test_decode_counts_cdf_evaluations():
     words, off = codec.encode(dp, ds, 64)
     codec.stats_enable(True)
     codec.stats_read()
-    codec.decode(dp, words, off, 64)
+    _set_lanes(1)
+    try:
+        codec.decode(dp, words, off, 64)
+    finally:
+        _set_lanes(0)
     evals, nsym = codec.stats_read()
     codec.stats_enable(False)
     assert nsym == lat.N
