@@ -145,6 +145,9 @@ __device__ __forceinline__ void dec_segment(const T* __restrict__ params, int64_
         const bool act = n < N;
         RawParams<K> nxt;
         if (t + 1 < T_steps && n + S < N) load_raw_params<K, T>(params, N, n + S, nxt);
+        // the refill words of the next steps lie just below ptr (a segment
+        // consumes a few words per step): pull their line into L1 ahead
+        if (lane == 0 && ptr - 96 >= beg) asm volatile("prefetch.global.L1 [%0];" ::"l"(words + ptr - 96));
         int32_t s = 0;
         bool esc = false;
         if (act) {
