@@ -370,7 +370,8 @@ def run_fgmm(args):
         "wall_s_timed_region": t_wall,
         "e2e": {"value": world * N / (e2e_ms * 1e-3) / 1e6, "unit": "Msymbols/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
-        "roofline": {"kernel": "fgmm_dec_coop_kernel" if args.decode_lanes != 1 else "fgmm_dec_kernel",
+        "roofline": {"kernel": {0: "fgmm_dec_wide_kernel", 1: "fgmm_dec_kernel", 32: "fgmm_dec_wide_kernel"}.get(
+                         args.decode_lanes, "fgmm_dec_coop_kernel"),
                      "bound": "alu", "achieved": achieved, "peak": alu_peak,
                      "unit": "Tops/s (FP32 lane ops)", "frac": achieved / alu_peak, "traffic": None,
                      "peak_source": f"derived: {props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x "

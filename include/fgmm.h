@@ -89,6 +89,14 @@ const char *fgmm_last_error(const fgmm_handle *h);
  * recorded since the last call (FGMM_OK if none), or FGMM_ERR_CUDA. */
 fgmm_status fgmm_sync_status(fgmm_handle *h, void *stream);
 
+/* Exhaustive check, on the current GPU, of the fast exact arithmetic the
+ * kernels rely on: out[0] = number of floats d in [2^-125, 2^125] whose
+ * Newton-refined reciprocal differs from the correctly rounded 1/d;
+ * out[1] = number of failures of the encoder's division x / f (f in
+ * [1, 2^16), quotient below 2^16) at the remainders 0, 1 and f - 1.
+ * Both must be 0. Synchronous; takes about a second. */
+fgmm_status fgmm_self_check(fgmm_handle *h, uint64_t *out);
+
 /* Phi-hat (Sec. III-B, Eq. 8, A&S 26.2.17) at n points: out[i] =
  * Phi-hat(z[i]). z and out are device float arrays of length n. */
 fgmm_status fgmm_phi(fgmm_handle *h, const float *z, float *out, int64_t n, void *stream);
@@ -278,9 +286,11 @@ fgmm_status fgmm_decode_proposal(fgmm_handle *h, const fgmm_latent *lat, const v
 /* Tuning options (fgmm_set_option). FGMM_OPT_DECODE_LANES: lanes that
  * cooperate on one stream in fgmm_decode: 1 (binary search, one lane per
  * stream), 2, 4, 8, 16 or 32 (G-ary search, G lanes per stream), or 0 to
- * choose from the number of segments (default). The decoded symbols do not
- * depend on it. */
-enum { FGMM_OPT_DECODE_LANES = 1 };
+ * choose from the number of segments (default). FGMM_OPT_DECODE_CLUSTER:
+ * CTAs (a thread-block cluster, one SM each) sharing one segment when G > 1:
+ * 1, 2 or 4 (at most G), 8 for G = 32, or 0 for automatic. The decoded symbols do not
+ * depend on either. */
+enum { FGMM_OPT_DECODE_LANES = 1, FGMM_OPT_DECODE_CLUSTER = 2 };
 fgmm_status fgmm_set_option(fgmm_handle *h, int32_t option, int64_t value);
 
 /* Optional counters. When enabled, decoders add the number of quantised-CDF

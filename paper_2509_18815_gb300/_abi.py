@@ -26,6 +26,7 @@ FGMM_DTYPE_F32 = 0
 FGMM_DTYPE_BF16 = 1
 FGMM_MAX_K = 4
 FGMM_OPT_DECODE_LANES = 1
+FGMM_OPT_DECODE_CLUSTER = 2
 FGMM_MLP_PARAMS = 4929
 FGMM_MLP_PACKED_BYTES = 11024
 
@@ -52,6 +53,7 @@ SIGNATURES = {
     "fgmm_status_string": (ctypes.c_char_p, [I32]),
     "fgmm_last_error": (ctypes.c_char_p, [P]),
     "fgmm_sync_status": (I32, [P, P]),
+    "fgmm_self_check": (I32, [P, P]),
     "fgmm_phi": (I32, [P, P, P, I64, P]),
     "fgmm_phi_grid": (I32, [P, I64, P, I64, P]),
     "fgmm_freqs": (I32, [P, LATP, P, P, P]),

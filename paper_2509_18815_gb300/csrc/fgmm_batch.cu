@@ -46,7 +46,8 @@ struct WorkItem {
     int32_t g;          // segment within the latent
 };
 
-constexpr int kBatchThreads = 128;
+constexpr int kBatchThreads = 32;        // one warp per block: warps spread over all SMs
+constexpr int kTargetWarpsPerSM = 16;    // enough resident warps to keep the issue slots busy
 
 template <int K, typename T>
 __device__ __forceinline__ void enc_item(const BatchLatentDev& L, int32_t g, uint16_t* scratch, int64_t* len,
@@ -133,6 +134,76 @@ __global__ void __launch_bounds__(kBatchThreads) fgmm_batch_dec_kernel(const Bat
     }
 }
 
+// Specialised persistent kernels for batches whose latents share K and the
+// parameter type (fewer registers than the mixed kernels above).
+template <int K, typename T>
+__global__ void __launch_bounds__(kBatchThreads) fgmm_batch_enc_kt_kernel(const BatchLatentDev* __restrict__ lats,
+                                                                          const WorkItem* __restrict__ work,
+                                                                          int64_t nwork, unsigned long long* counter,
+                                                                          uint16_t* __restrict__ scratch,
+                                                                          int64_t* __restrict__ len, int32_t* err)
+{
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        unsigned long long i = 0;
+        if (lane == 0) i = atomicAdd(counter, 1ull);
+        i = __shfl_sync(0xffffffffu, i, 0);
+        if (i >= (unsigned long long)nwork) break;
+        const WorkItem w = work[i];
+        enc_item<K, T>(lats[w.latent], w.g, scratch, len, err);
+    }
+}
+
+template <int K, typename T>
+__global__ void __launch_bounds__(kBatchThreads) fgmm_batch_dec_kt_kernel(const BatchLatentDev* __restrict__ lats,
+                                                                          const WorkItem* __restrict__ work,
+                                                                          int64_t nwork, unsigned long long* counter,
+                                                                          const uint16_t* __restrict__ words,
+                                                                          int64_t n_words,
+                                                                          const int64_t* __restrict__ offsets,
+                                                                          int32_t* err, unsigned long long* stats)
+{
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        unsigned long long i = 0;
+        if (lane == 0) i = atomicAdd(counter, 1ull);
+        i = __shfl_sync(0xffffffffu, i, 0);
+        if (i >= (unsigned long long)nwork) break;
+        const WorkItem w = work[i];
+        dec_item<K, T>(lats[w.latent], w.g, words, n_words, offsets, err, stats);
+    }
+}
+
+using EncKernel = void (*)(const BatchLatentDev*, const WorkItem*, int64_t, unsigned long long*, uint16_t*, int64_t*,
+                           int32_t*);
+using DecKernel = void (*)(const BatchLatentDev*, const WorkItem*, int64_t, unsigned long long*, const uint16_t*,
+                           int64_t, const int64_t*, int32_t*, unsigned long long*);
+
+template <typename T>
+void pick_kt(int K, EncKernel* e, DecKernel* d)
+{
+    switch (K) {
+    case 1: *e = fgmm_batch_enc_kt_kernel<1, T>; *d = fgmm_batch_dec_kt_kernel<1, T>; break;
+    case 2: *e = fgmm_batch_enc_kt_kernel<2, T>; *d = fgmm_batch_dec_kt_kernel<2, T>; break;
+    case 3: *e = fgmm_batch_enc_kt_kernel<3, T>; *d = fgmm_batch_dec_kt_kernel<3, T>; break;
+    default: *e = fgmm_batch_enc_kt_kernel<4, T>; *d = fgmm_batch_dec_kt_kernel<4, T>; break;
+    }
+}
+
+// Kernels for a batch: specialised when all latents share K and dtype.
+void pick_kernels(const std::vector<int>& Ks, const std::vector<int>& dts, EncKernel* e, DecKernel* d)
+{
+    bool same = true;
+    for (size_t i = 1; i < Ks.size(); ++i) same = same && Ks[i] == Ks[0] && dts[i] == dts[0];
+    if (Ks.empty() || !same) {
+        *e = fgmm_batch_enc_kernel;
+        *d = fgmm_batch_dec_kernel;
+        return;
+    }
+    if (dts[0] == FGMM_DTYPE_BF16) pick_kt<__nv_bfloat16>(Ks[0], e, d);
+    else pick_kt<float>(Ks[0], e, d);
+}
+
 // Compaction of all segments: warp per segment, 16-bit copies.
 __global__ void __launch_bounds__(256) fgmm_batch_compact_kernel(const uint16_t* __restrict__ scratch,
                                                                  const int64_t* __restrict__ scr_off,
@@ -167,6 +238,8 @@ struct fgmm_batch {
     int64_t* offsets = nullptr;
     int64_t* n_words_out = nullptr;
     int grid_enc = 0, grid_dec = 0;
+    EncKernel enc_kernel = nullptr;
+    DecKernel dec_kernel = nullptr;
     cudaGraphExec_t g_enc = nullptr, g_dec = nullptr;
     fgmm_handle* h = nullptr;
 };
@@ -177,8 +250,8 @@ void enqueue_encode(fgmm_batch* b, cudaStream_t st)
 {
     fgmm_handle* h = b->h;
     cudaMemsetAsync(b->d_counters, 0, sizeof(unsigned long long), st);
-    fgmm_batch_enc_kernel<<<b->grid_enc, kBatchThreads, 0, st>>>(b->d_lats, b->d_work, b->nseg, b->d_counters,
-                                                                  b->d_scratch, b->d_len, h->d_err);
+    b->enc_kernel<<<b->grid_enc, kBatchThreads, 0, st>>>(b->d_lats, b->d_work, b->nseg, b->d_counters, b->d_scratch,
+                                                          b->d_len, h->d_err);
     // offsets over all segments, then compaction into the output
     launch_scan(b->d_len, b->nseg, b->offsets, b->n_words_out, b->words_cap, h->d_err, st);
     const int64_t cblocks = std::min<int64_t>((int64_t)h->num_sms * 8, (b->nseg * 32 + 255) / 256);
@@ -191,9 +264,9 @@ void enqueue_decode(fgmm_batch* b, cudaStream_t st)
 {
     fgmm_handle* h = b->h;
     cudaMemsetAsync(b->d_counters + 1, 0, sizeof(unsigned long long), st);
-    fgmm_batch_dec_kernel<<<b->grid_dec, kBatchThreads, 0, st>>>(b->d_lats, b->d_work, b->nseg, b->d_counters + 1,
-                                                                  b->words, b->words_cap, b->offsets, h->d_err,
-                                                                  h->stats_on ? h->d_stats : nullptr);
+    b->dec_kernel<<<b->grid_dec, kBatchThreads, 0, st>>>(b->d_lats, b->d_work, b->nseg, b->d_counters + 1, b->words,
+                                                          b->words_cap, b->offsets, h->d_err,
+                                                          h->stats_on ? h->d_stats : nullptr);
 }
 
 void free_plan(fgmm_batch* b)
@@ -223,27 +296,35 @@ fgmm_status fgmm_autotune(fgmm_handle* h, const int64_t* N, int32_t n, double ma
         if (N[i] < 0) return fail(h, FGMM_ERR_INVALID_ARG, "fgmm_autotune: negative N");
         total += N[i];
     }
-    // Streams the batch decoder runs concurrently: resident warps x 32.
+    // Warps the batch decoder keeps resident: occupancy of the K = 3 fp32
+    // decoder, capped at kTargetWarpsPerSM per SM (beyond that the SM's
+    // issue slots are full and more streams only add container bits).
     int blocks_per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, fgmm_batch_dec_kernel,
-                                                                  kBatchThreads, 0);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm,
+                                                                  fgmm_batch_dec_kt_kernel<3, float>, kBatchThreads, 0);
     if (e != cudaSuccess) return cuda_fail(h, e, "fgmm_autotune occupancy");
-    const double concurrent_streams = (double)h->num_sms * blocks_per_sm * (kBatchThreads / 32) * 32;
+    const int64_t warps_per_sm = std::max(1, std::min(blocks_per_sm * (kBatchThreads / 32), kTargetWarpsPerSM));
+    const int64_t max_segments = std::max<int64_t>(1, (int64_t)h->num_sms * warps_per_sm);
     // Each stream ends with a 32-bit flushed state: keeping that below
-    // max_overhead of the payload needs T >= 32 / (max_overhead * bps)
-    // symbols per stream. More streams than run concurrently add overhead
-    // without adding parallelism.
+    // max_overhead of the payload needs T >= 32 / (max_overhead * bps).
     const double t_min = std::ceil(32.0 / (max_overhead * bits_per_symbol));
-    const double t_par = std::ceil((double)total / concurrent_streams);
-    const double t_star = std::max(t_min, t_par);
-    for (int i = 0; i < n; ++i) {
-        int64_t s = (int64_t)std::ceil((double)N[i] / t_star);
-        s = (s + 31) / 32 * 32;
-        if (s < 32) s = 32;
-        const int64_t smax = std::max<int64_t>(32, (N[i] + 31) / 32 * 32);
-        if (s > smax) s = smax;
-        if (s > (int64_t)1 << 30) s = (int64_t)1 << 30;
-        S_out[i] = (int32_t)s;
+    double t_star = std::max(t_min, std::ceil((double)total / (32.0 * (double)max_segments)));
+    for (int iter = 0; iter < 200; ++iter) {
+        int64_t segs = 0;
+        for (int i = 0; i < n; ++i) {
+            int64_t s = (int64_t)std::ceil((double)N[i] / t_star);
+            s = (s + 31) / 32 * 32;
+            if (s < 32) s = 32;
+            const int64_t smax = std::max<int64_t>(32, (N[i] + 31) / 32 * 32);
+            if (s > smax) s = smax;
+            if (s > (int64_t)1 << 30) s = (int64_t)1 << 30;
+            S_out[i] = (int32_t)s;
+            segs += s / 32;
+        }
+        // one wave: every segment resident at once (a second wave of a few
+        // segments would double the time)
+        if (segs <= max_segments || t_star >= (double)total) break;
+        t_star = std::ceil(t_star * 1.03) + 1.0;
     }
     return FGMM_OK;
 }
@@ -320,11 +401,16 @@ fgmm_status fgmm_batch_create(fgmm_handle* h, const fgmm_batch_latent* lats, int
         e = cudaMemcpy(b->d_lats, L.data(), sizeof(BatchLatentDev) * n, cudaMemcpyHostToDevice);
     if (e == cudaSuccess && seg > 0)
         e = cudaMemcpy(b->d_work, work.data(), sizeof(WorkItem) * seg, cudaMemcpyHostToDevice);
+    {
+        std::vector<int> Ks(n), dts(n);
+        for (int i = 0; i < n; ++i) { Ks[i] = lats[i].K; dts[i] = lats[i].dtype; }
+        pick_kernels(Ks, dts, &b->enc_kernel, &b->dec_kernel);
+    }
     int bpm_e = 0, bpm_d = 0;
     if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bpm_e, fgmm_batch_enc_kernel, kBatchThreads, 0);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bpm_e, b->enc_kernel, kBatchThreads, 0);
     if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bpm_d, fgmm_batch_dec_kernel, kBatchThreads, 0);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bpm_d, b->dec_kernel, kBatchThreads, 0);
     if (e != cudaSuccess) {
         cudaGetLastError();
         free_plan(b);

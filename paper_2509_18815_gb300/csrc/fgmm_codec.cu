@@ -20,6 +20,7 @@
 
 #include "fgmm_device.cuh"
 #include "fgmm_internal.h"
+#include "fgmm_segment.cuh"
 
 using namespace fgmm;
 
@@ -34,6 +35,43 @@ __global__ void phi_kernel(const float* __restrict__ z, float* __restrict__ out,
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         out[i] = phi_hat(z[i]);
+}
+
+// Exhaustive check of recip() against __frcp_rn over [2^-125, 2^125]
+// (every float), and a check of the encoder's exact division for every
+// divisor f in [1, 2^16) at x = q f + r, r in {0, 1, f - 1}, for the 64
+// smallest and 64 largest quotients and every 67th one in between.
+__global__ void self_check_recip_kernel(unsigned long long* bad)
+{
+    unsigned long long nb = 0;
+    const uint32_t lo = 0x01000000u, hi = 0x7e000000u;   // 2^-125 .. 2^125
+    for (uint32_t u = lo + blockIdx.x * blockDim.x + threadIdx.x; u <= hi; u += gridDim.x * blockDim.x) {
+        const float d = __uint_as_float(u);
+        if (__float_as_uint(recip(d)) != __float_as_uint(__frcp_rn(d))) ++nb;
+    }
+    atomicAdd(bad, nb);
+}
+
+__global__ void self_check_div_kernel(unsigned long long* bad)
+{
+    unsigned long long nb = 0;
+    constexpr uint32_t kQ = 128 + (65536 - 128) / 67;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < 65536ull * kQ;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t f = (uint32_t)(i / kQ), qi = (uint32_t)(i % kQ);
+        const uint32_t q = qi < 64 ? qi : (qi < 128 ? 65535u - (qi - 64) : 64u + (qi - 128) * 67u);
+        if (f == 0 || q > 65535u) continue;
+        const uint32_t rs[3] = {0u, 1u % f, f - 1};
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const uint64_t x64 = (uint64_t)q * f + rs[k];
+            if (x64 >= ((uint64_t)f << 16)) continue;
+            uint32_t r;
+            const uint32_t qq = divmod_small((uint32_t)x64, f, r);
+            if (qq != q || r != rs[k]) ++nb;
+        }
+    }
+    atomicAdd(bad, nb);
 }
 
 __global__ void phi_grid_kernel(int64_t i0, float* __restrict__ out, int64_t n)
@@ -63,26 +101,7 @@ __global__ void __launch_bounds__(256) fgmm_interval_kernel(const T* __restrict_
 // 2. Interleaved rANS encoder, one warp per segment.
 // ---------------------------------------------------------------------------
 
-// Codes (start, freq) on the lanes where `part` holds. Lanes whose state
-// would overflow first emit their low 16 bits; the words of the sub-phase
-// land in ascending lane order at out[base ...].
-__device__ __forceinline__ void enc_put(uint32_t& x, uint32_t start, uint32_t freq, bool part,
-                                        uint16_t* __restrict__ out, int64_t& base, uint32_t lt)
-{
-    const bool need = part && x >= (freq << 16);
-    const uint32_t m = __ballot_sync(kFull, need);
-    if (need) {
-        out[base + __popc(m & lt)] = (uint16_t)(x & 0xffffu);
-        x >>= 16;
-    }
-    base += __popc(m);
-    if (part) {
-        const uint32_t q = x / freq;
-        x = (q << 16) + (x - q * freq) + start;
-    }
-}
-
-__global__ void __launch_bounds__(64) fgmm_rans_enc_kernel(const uint32_t* __restrict__ sf,
+__global__ void __launch_bounds__(32) fgmm_rans_enc_kernel(const uint32_t* __restrict__ sf,
                                                            const int32_t* __restrict__ sym, int64_t N, int32_t S,
                                                            int64_t T, uint16_t* __restrict__ seg_words,
                                                            int64_t seg_cap, int64_t* __restrict__ seg_len,
@@ -96,17 +115,20 @@ __global__ void __launch_bounds__(64) fgmm_rans_enc_kernel(const uint32_t* __res
     uint32_t x = kL;
     int64_t base = 0;
     int64_t n = (T - 1) * (int64_t)S + g * 32 + lane;
+    uint32_t v = (T > 0 && n < N) ? __ldg(sf + n) : 0u;
     for (int64_t t = T - 1; t >= 0; --t, n -= S) {
         const bool act = n < N;
-        const uint32_t v = act ? __ldg(sf + n) : 0u;
+        // next (lower) step's interval, loaded ahead of this step's work
+        const uint32_t vn = (t > 0 && n - S < N) ? __ldg(sf + n - S) : 0u;
         const uint32_t start = v & 0xffffu, freq = v >> 16;
         const bool esc = act && (start + freq == kM);
         if (__ballot_sync(kFull, esc)) {
             const uint32_t raw = esc ? (uint32_t)__ldg(sym + n) : 0u;
-            enc_put(x, raw & 0xffffu, 1u, esc, out, base, lt);
-            enc_put(x, raw >> 16, 1u, esc, out, base, lt);
+            enc_put_warp(x, raw & 0xffffu, 1u, esc, out, base, lt);
+            enc_put_warp(x, raw >> 16, 1u, esc, out, base, lt);
         }
-        enc_put(x, start, freq, act, out, base, lt);
+        enc_put_warp(x, start, freq, act, out, base, lt);
+        v = vn;
     }
     out[base + 2 * lane] = (uint16_t)(x & 0xffffu);
     out[base + 2 * lane + 1] = (uint16_t)(x >> 16);
@@ -220,7 +242,7 @@ void launch_interval_any(const fgmm_latent* lat, const int32_t* sym, uint32_t* s
 
 // Warps per block for the per-segment kernels: one warp per block while the
 // segments do not fill the SMs, so that each warp has an SM to itself.
-inline int seg_threads(int64_t nseg, int sms) { return nseg <= 2 * (int64_t)sms ? 32 : 64; }
+inline int seg_threads(int64_t, int) { return 32; }
 
 
 // Per-segment scratch capacity: at most three words per lane and step (an
@@ -320,8 +342,8 @@ fgmm_status fgmm_create(fgmm_handle** out)
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
     if (e == cudaSuccess) e = cudaMalloc(&h->d_err, sizeof(int32_t));
     if (e == cudaSuccess) e = cudaMemset(h->d_err, 0, sizeof(int32_t));
-    if (e == cudaSuccess) e = cudaMalloc(&h->d_stats, 4 * sizeof(unsigned long long));
-    if (e == cudaSuccess) e = cudaMemset(h->d_stats, 0, 4 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_stats, 8 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(h->d_stats, 0, 8 * sizeof(unsigned long long));
     if (e != cudaSuccess) {
         cudaGetLastError();
         if (h->d_err) cudaFree(h->d_err);
@@ -423,6 +445,24 @@ fgmm_status fgmm_phi_grid(fgmm_handle* h, int64_t i0, float* out, int64_t n, voi
     return e == cudaSuccess ? FGMM_OK : cuda_fail(h, e, "fgmm_phi_grid launch");
 }
 
+fgmm_status fgmm_self_check(fgmm_handle* h, uint64_t* out)
+{
+    if (!h || !out) return FGMM_ERR_INVALID_ARG;
+    unsigned long long* d = h->d_stats + 4;   // spare counters
+    cudaError_t e = cudaMemset(d, 0, 2 * sizeof(unsigned long long));
+    if (e == cudaSuccess) {
+        self_check_recip_kernel<<<h->num_sms * 8, 256>>>(d);
+        self_check_div_kernel<<<h->num_sms * 8, 256>>>(d + 1);
+        e = cudaDeviceSynchronize();
+    }
+    unsigned long long v[2] = {0, 0};
+    if (e == cudaSuccess) e = cudaMemcpy(v, d, sizeof v, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(h, e, "fgmm_self_check");
+    out[0] = v[0];
+    out[1] = v[1];
+    return FGMM_OK;
+}
+
 fgmm_status fgmm_freqs(fgmm_handle* h, const fgmm_latent* lat, const int32_t* symbols, uint32_t* sf, void* stream)
 {
     fgmm_status s = check_latent(h, lat);
@@ -480,8 +520,14 @@ fgmm_status fgmm_decode(fgmm_handle* h, const fgmm_latent* lat, const uint16_t* 
     a.out = symbols_out;
     a.err = h->d_err;
     a.stats = h->stats_on ? h->d_stats : nullptr;
-    const int lanes = h->decode_lanes > 0 ? h->decode_lanes : decode_lanes_auto(a.nseg, h->num_sms);
-    cudaError_t e = launch_decode(a, lat->K, lat->dtype, lanes, st);
+    int lanes = 1, cluster = 1;
+    decode_config_auto(a.nseg, h->num_sms, &lanes, &cluster);
+    if (h->decode_lanes > 0) {
+        lanes = h->decode_lanes;
+        cluster = 1;
+    }
+    if (h->decode_cluster > 0) cluster = h->decode_cluster;
+    cudaError_t e = launch_decode(a, lat->K, lat->dtype, lanes, cluster, st);
     return e == cudaSuccess ? FGMM_OK : cuda_fail(h, e, "fgmm_decode launch");
 }
 
@@ -493,6 +539,11 @@ fgmm_status fgmm_set_option(fgmm_handle* h, int32_t option, int64_t value)
         if (!(value == 0 || value == 1 || value == 2 || value == 4 || value == 8 || value == 16 || value == 32))
             return fail(h, FGMM_ERR_INVALID_ARG, "decode lanes must be 0 (auto), 1, 2, 4, 8, 16 or 32");
         h->decode_lanes = (int)value;
+        return FGMM_OK;
+    case FGMM_OPT_DECODE_CLUSTER:
+        if (!(value == 0 || value == 1 || value == 2 || value == 4 || value == 8))
+            return fail(h, FGMM_ERR_INVALID_ARG, "decode cluster must be 0 (auto), 1, 2, 4 or 8");
+        h->decode_cluster = (int)value;
         return FGMM_OK;
     default:
         return fail(h, FGMM_ERR_INVALID_ARG, "unknown option");

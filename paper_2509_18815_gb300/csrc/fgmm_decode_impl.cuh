@@ -1,0 +1,733 @@
+// fgmm_decode_impl.cuh -- decoder kernels (included by the fp32 and bf16
+// instantiation units fgmm_decode.cu and fgmm_decode_bf16.cu).
+//
+// Decoders: binary search over the on-the-fly quantised
+// CDF (Sec. III-A), inverse rANS step (Eq. 3), ballot-ranked refill.
+//
+// Two kernels produce identical symbols (the search result is unique
+// because Q is strictly increasing); they differ in how the search is
+// spread over lanes:
+//
+// * fgmm_dec_kernel (G = 1): one lane per stream, 32 streams (a segment) per
+//   warp, plain binary search (one CDF evaluation per round). Least work per
+//   symbol; the choice when there are enough segments to fill the GPU. The
+//   next step's parameters are loaded one step ahead into registers.
+//
+// * fgmm_dec_coop_kernel (G = 2 .. 32): G lanes cooperate on one stream and
+//   evaluate G points of the quantised CDF per round (G-ary search), so a
+//   step needs ~log_{G+1}(W) dependent rounds instead of ~log_2(W). A CTA of
+//   G warps holds one segment; parameters are staged through a cp.async ring
+//   in shared memory PF steps ahead, the segment's words are copied to
+//   shared memory when they fit, and the refill ranks of the 32 streams are
+//   combined through shared memory with one CTA barrier per step. The choice
+//   when the streams alone cannot fill the GPU (few streams, long streams).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "fgmm_device.cuh"
+#include "fgmm_internal.h"
+#include "fgmm_segment.cuh"
+
+using namespace fgmm;
+
+namespace {
+
+constexpr uint32_t kFull = 0xffffffffu;
+
+// ---------------------------------------------------------------------------
+// G = 1: binary search, one lane per stream.
+// ---------------------------------------------------------------------------
+template <int K, typename T>
+__global__ void __launch_bounds__(32) fgmm_dec_kernel(const T* __restrict__ params, int64_t N, int32_t S,
+                                                       int64_t T_steps, const uint16_t* __restrict__ words,
+                                                       int64_t n_words, const int64_t* __restrict__ offsets,
+                                                       int64_t nseg, int32_t* __restrict__ out, int32_t* err,
+                                                       unsigned long long* stats)
+{
+    const int64_t g = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (g >= nseg) return;
+    const int64_t beg = offsets[g], end = offsets[g + 1];
+    if (!(beg >= 0 && end <= n_words && end - beg >= 64)) {
+        if ((threadIdx.x & 31) == 0) set_error(err, kErrCorrupt);
+        return;
+    }
+    dec_segment<K, T>(params, N, S, T_steps, g, words, beg, end, out, err, stats);
+}
+
+// ---------------------------------------------------------------------------
+// G = 2 .. 32: cooperative G-ary search, one CTA of G warps per segment.
+// ---------------------------------------------------------------------------
+constexpr int kPF = 4;            // parameter prefetch distance (steps)
+constexpr int kRing = 8;          // ring slots (>= kPF + 2, power of two)
+constexpr int kWordCap = 16384;   // segment words staged in shared memory if they fit
+
+__device__ __forceinline__ void cp_async_16(void* smem, const void* gmem, int src_bytes)
+{
+    const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(src_bytes));
+}
+__device__ __forceinline__ void cp_async_4(void* smem, const void* gmem, int src_bytes)
+{
+    const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(s), "l"(gmem), "r"(src_bytes));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int n>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(n)); }
+
+// Copies step t's parameters of COLS consecutive streams (3K rows x COLS
+// symbols) into ring slot `dst` ([3K][COLS] of T). Elements at n >= N are zero-filled and
+// never read from global memory. mode 2: 16-byte cp.async (rows 16-byte
+// aligned); mode 1: 4-byte cp.async (rows 4-byte aligned); mode 0: plain
+// loads and shared stores (any alignment), visible after the next barrier.
+template <int K, typename T, int COLS>
+__device__ __forceinline__ void stage_params(T* dst, const T* __restrict__ params, int64_t N, int64_t n0, int tid,
+                                             int nthreads, int mode)
+{
+    if (mode == 2) {
+        constexpr int per_chunk = 16 / (int)sizeof(T);
+        constexpr int chunks_per_row = COLS / per_chunk > 0 ? COLS / per_chunk : 1;
+        constexpr int total = 3 * K * chunks_per_row;
+        for (int c = tid; c < total; c += nthreads) {
+            const int row = c / chunks_per_row, col = (c % chunks_per_row) * per_chunk;
+            const int64_t n = n0 + col;
+            int64_t valid = N - n;
+            valid = valid < 0 ? 0 : (valid > per_chunk ? per_chunk : valid);
+            const T* src = valid > 0 ? params + (int64_t)row * N + n : params;
+            cp_async_16(dst + row * COLS + col, src, (int)(valid * sizeof(T)));
+        }
+    } else if (mode == 1) {
+        constexpr int per_chunk = 4 / (int)sizeof(T);
+        constexpr int chunks_per_row = COLS / per_chunk;
+        constexpr int total = 3 * K * chunks_per_row;
+        for (int c = tid; c < total; c += nthreads) {
+            const int row = c / chunks_per_row, col = (c % chunks_per_row) * per_chunk;
+            const int64_t n = n0 + col;
+            int64_t valid = N - n;
+            valid = valid < 0 ? 0 : (valid > per_chunk ? per_chunk : valid);
+            const T* src = valid > 0 ? params + (int64_t)row * N + n : params;
+            cp_async_4(dst + row * COLS + col, src, (int)(valid * sizeof(T)));
+        }
+    } else {
+        constexpr int total = 3 * K * COLS;
+        for (int c = tid; c < total; c += nthreads) {
+            const int row = c / COLS, col = c % COLS;
+            const int64_t n = n0 + col;
+            dst[row * COLS + col] = n < N ? params[(int64_t)row * N + n] : T(0.0f);
+        }
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ float smem_param(const T* p);
+template <>
+__device__ __forceinline__ float smem_param<float>(const float* p) { return *p; }
+template <>
+__device__ __forceinline__ float smem_param<__nv_bfloat16>(const __nv_bfloat16* p)
+{
+    return __uint_as_float((uint32_t)(*reinterpret_cast<const unsigned short*>(p)) << 16);
+}
+
+// Barrier over the CTAs that share a segment: the CTA itself (CL = 1) or
+// the thread-block cluster (CL > 1, release/acquire at cluster scope).
+template <int CL>
+__device__ __forceinline__ void seg_sync()
+{
+    if constexpr (CL == 1) {
+        __syncthreads();
+    } else {
+        asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+    }
+}
+
+__device__ __forceinline__ uint32_t cluster_rank()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+// Stores v at `local` in the shared memory of every CTA of the cluster.
+template <int CL>
+__device__ __forceinline__ void publish(uint32_t* local, uint32_t v)
+{
+    if constexpr (CL == 1) {
+        *local = v;
+    } else {
+        const uint32_t a = (uint32_t)__cvta_generic_to_shared(local);
+#pragma unroll
+        for (uint32_t r = 0; r < (uint32_t)CL; ++r) {
+            uint32_t ra;
+            asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(a), "r"(r));
+            asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(ra), "r"(v) : "memory");
+        }
+    }
+}
+
+// Segment-wide refill for one sub-phase. need: this stream needs a word.
+// Each of the segment's G warps publishes the need bits of its 32/G streams;
+// after the barrier every thread forms the segment's 32-bit mask and the
+// stream's rank.
+template <int G, int CL>
+__device__ __forceinline__ void refill_coop(uint32_t& x, bool need, uint32_t* pub, int wseg, int grp, int sub,
+                                            const uint16_t* wsrc, int64_t wbase, int64_t& ptr, int64_t beg,
+                                            bool& bad)
+{
+    constexpr int SPW = 32 / G;    // streams per warp
+    const uint32_t b = __ballot_sync(kFull, need && sub == 0);
+    uint32_t part = 0;
+#pragma unroll
+    for (int i = 0; i < SPW; ++i) part |= ((b >> (i * G)) & 1u) << i;
+    if ((threadIdx.x & 31) == 0) publish<CL>(pub + wseg, part);
+    seg_sync<CL>();
+    uint32_t M = 0;
+#pragma unroll
+    for (int i = 0; i < G; ++i) M |= pub[i] << (i * SPW);
+    if (M) {
+        const int w = wseg * SPW + grp;   // stream index within the segment
+        const int c = __popc(M);
+        if (need) {
+            const int64_t idx = ptr - c + __popc(M & ((1u << w) - 1u));
+            uint32_t v = 0;
+            if (idx >= beg) v = wsrc[idx - wbase];
+            else bad = true;
+            x = (x << 16) | v;
+        }
+        ptr -= c;
+    }
+}
+
+// One segment per CL CTAs (a cluster when CL > 1); each CTA holds 32/CL
+// streams, G lanes per stream, G/CL warps.
+template <int K, typename T, int G, int CL>
+__global__ void __launch_bounds__(32 * G / CL) fgmm_dec_coop_kernel(const T* __restrict__ params, int64_t N,
+                                                                    int32_t S, int64_t T_steps,
+                                                                    const uint16_t* __restrict__ words,
+                                                                    int64_t n_words,
+                                                                    const int64_t* __restrict__ offsets,
+                                                                    int32_t* __restrict__ out, int32_t* err,
+                                                                    unsigned long long* stats, int mode)
+{
+    constexpr int SPW = 32 / G;        // streams per warp
+    constexpr int SPC = 32 / CL;       // streams per CTA
+    constexpr int WPC = G / CL;        // warps per CTA
+    constexpr int NT = 32 * WPC;
+    extern __shared__ __align__(16) unsigned char smem[];
+    T* ring = reinterpret_cast<T*>(smem);                                              // [kRing][3K][SPC]
+    uint32_t* pubs = reinterpret_cast<uint32_t*>(smem + sizeof(T) * kRing * 3 * K * SPC);   // [6][G]
+    uint16_t* wsm = reinterpret_cast<uint16_t*>(pubs + 6 * G);                         // [kWordCap]
+
+    const int rank = CL > 1 ? (int)cluster_rank() : 0;
+    const int tid = threadIdx.x, lane = tid & 31, grp = lane / G, sub = lane % G;
+    const int wseg = rank * WPC + (tid >> 5);          // warp index within the segment
+    const int wstream = wseg * SPW + grp;              // stream index within the segment
+    const int wcol = wstream - rank * SPC;             // column in this CTA's parameter slots
+    const int64_t g = blockIdx.x / CL;
+    const int64_t beg = offsets[g], end = offsets[g + 1];
+    if (!(beg >= 0 && end <= n_words && end - beg >= 64)) {
+        if (tid == 0 && rank == 0) set_error(err, kErrCorrupt);
+        return;   // uniform over the segment's CTAs, before any barrier
+    }
+    const int64_t seg_len = end - beg;
+    const bool staged = seg_len <= kWordCap;
+    const uint16_t* wsrc = staged ? wsm : words;
+    const int64_t wbase = staged ? beg : 0;
+
+    // prologue: parameters of steps 0 .. PF-1, then the segment's words
+    const int64_t nbase = g * 32 + rank * SPC;
+#pragma unroll
+    for (int p = 0; p < kPF; ++p) {
+        if (p < T_steps)
+            stage_params<K, T, SPC>(ring + (p % kRing) * 3 * K * SPC, params, N, p * (int64_t)S + nbase, tid, NT, mode);
+        cp_async_commit();
+    }
+    if (staged)
+        for (int64_t i = tid; i < seg_len; i += NT) wsm[i] = __ldg(words + beg + i);
+    cp_async_wait<kPF - 1>();
+    seg_sync<CL>();   // all CTAs of the cluster are running before any remote store
+
+    uint32_t x = (uint32_t)wsrc[end - 64 + 2 * wstream - wbase] | ((uint32_t)wsrc[end - 63 + 2 * wstream - wbase] << 16);
+    int64_t ptr = end - 64;
+    bool bad = false, badp = false;
+    int probes = 0, decoded = 0;
+    const unsigned gshift = grp * G;
+
+    for (int64_t t = 0; t < T_steps; ++t) {
+        // prefetch step t + PF into its ring slot (the slot of step t + PF - kRing,
+        // read before the previous barrier)
+        if (t + kPF < T_steps)
+            stage_params<K, T, SPC>(ring + ((t + kPF) % kRing) * 3 * K * SPC, params, N,
+                                    (t + kPF) * (int64_t)S + nbase, tid, NT, mode);
+        cp_async_commit();
+
+        const int64_t n = t * (int64_t)S + g * 32 + wstream;
+        const bool act = n < N;
+        int32_t s = 0;
+        bool esc = false;
+        uint32_t start = 0, freq = 1;
+        Mix<K> m;
+        {
+            const T* slot_p = ring + (t % kRing) * 3 * K * SPC;
+            RawParams<K> r;
+#pragma unroll
+            for (int i = 0; i < 3 * K; ++i) r.v[i] = smem_param<T>(slot_p + i * SPC + wcol);
+            const bool ok = mix_from_params<K>(r, m);
+            badp |= act && !ok;
+        }
+        const uint32_t slot = x & 0xffffu;
+        // round 0: G points p_i = lo + ceil((i+1) W / G); p_{G-1} = hi + 1
+        const int W = m.hi - m.lo + 1;
+        int a = m.lo, b = m.hi + 1;
+        uint32_t qa = 0, qb = 0;
+        {
+            const int p = m.lo + ((sub + 1) * W + G - 1) / G;
+            const uint32_t q = act ? q_at<K>(m, p) : 0u;
+            probes += act;
+            const uint32_t bal = (__ballot_sync(kFull, act && q <= slot) >> gshift) & ((G == 32) ? kFull : ((1u << G) - 1u));
+            const int c = __popc(bal);
+            const uint32_t q_c = __shfl_sync(kFull, q, grp * G + (c < G ? c : G - 1));
+            const uint32_t q_c1 = __shfl_sync(kFull, q, grp * G + (c > 0 ? c - 1 : 0));
+            const int p_c = m.lo + ((min(c, G - 1) + 1) * W + G - 1) / G;
+            const int p_c1 = m.lo + (c * W + G - 1) / G;   // p_{c-1}
+            if (c == G) {
+                esc = true;
+                start = q_c;   // Q(hi + 1)
+                freq = kM - q_c;
+                a = b;         // nothing left to search
+            } else {
+                b = p_c;
+                qb = q_c;
+                if (c > 0) { a = p_c1; qa = q_c1; }
+            }
+        }
+        // further rounds: G points strictly inside (a, b)
+        while (__any_sync(kFull, act && !esc && b - a > 1)) {
+            const bool live = act && !esc && b - a > 1;
+            const int L = b - a;
+            const bool fine = L - 1 <= G;
+            const int p = fine ? a + 1 + sub : a + ((sub + 1) * L) / (G + 1);
+            const bool valid = live && (fine ? sub < L - 1 : true);
+            const uint32_t q = valid ? q_at<K>(m, p) : 0u;
+            probes += valid;
+            const uint32_t bal = (__ballot_sync(kFull, valid && q <= slot) >> gshift) & ((G == 32) ? kFull : ((1u << G) - 1u));
+            const int nvalid = fine ? min(L - 1, G) : G;
+            const int c = __popc(bal);
+            const uint32_t q_c = __shfl_sync(kFull, q, grp * G + (c < G ? c : G - 1));
+            const uint32_t q_c1 = __shfl_sync(kFull, q, grp * G + (c > 0 ? c - 1 : 0));
+            const int p_c = fine ? a + 1 + c : a + ((c + 1) * L) / (G + 1);
+            const int p_c1 = fine ? a + c : a + (c * L) / (G + 1);
+            if (live) {
+                const int na = c > 0 ? p_c1 : a;
+                const uint32_t nqa = c > 0 ? q_c1 : qa;
+                if (c < nvalid) { b = p_c; qb = q_c; }
+                a = na;
+                qa = nqa;
+            }
+        }
+        if (act && !esc) {
+            s = a;
+            start = qa;
+            freq = qb - qa;
+        }
+        if (act) {
+            x = freq * (x >> 16) + slot - start;
+            decoded += (sub == 0);
+        }
+        // wait for step t+1's parameters before the barrier that publishes them
+        cp_async_wait<kPF - 1>();
+        const int par = (int)(t & 1);
+        // publish the escape bits with the refill bits
+        const uint32_t be = __ballot_sync(kFull, act && esc && sub == 0);
+        uint32_t epart = 0;
+#pragma unroll
+        for (int i = 0; i < SPW; ++i) epart |= ((be >> (i * G)) & 1u) << i;
+        if (lane == 0) publish<CL>(pubs + (2 + par) * G + wseg, epart);
+        refill_coop<G, CL>(x, act && x < kL, pubs + par * G, wseg, grp, sub, wsrc, wbase, ptr, beg, bad);
+        uint32_t E = 0;
+#pragma unroll
+        for (int i = 0; i < G; ++i) E |= pubs[(2 + par) * G + i] << (i * SPW);
+        if (E) {   // uniform over the segment's CTAs
+            uint32_t hi16 = 0, lo16 = 0;
+            if (esc) { hi16 = x & 0xffffu; x >>= 16; }
+            refill_coop<G, CL>(x, esc && x < kL, pubs + 4 * G, wseg, grp, sub, wsrc, wbase, ptr, beg, bad);
+            if (esc) { lo16 = x & 0xffffu; x >>= 16; }
+            refill_coop<G, CL>(x, esc && x < kL, pubs + 5 * G, wseg, grp, sub, wsrc, wbase, ptr, beg, bad);
+            if (esc) s = (int32_t)((hi16 << 16) | lo16);
+            seg_sync<CL>();   // escape buffers are reused by the next escape step
+        }
+        if (act && sub == 0) out[n] = s;
+    }
+    cp_async_wait<0>();
+    const bool fail = bad || x != kL || ptr != beg;
+    if (__syncthreads_or(fail) && tid == 0) set_error(err, kErrCorrupt);
+    if (__syncthreads_or(badp) && tid == 0) set_error(err, kErrBadParams);
+    if (stats) {
+        int p = probes, d = decoded;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            p += __shfl_xor_sync(kFull, p, o);
+            d += __shfl_xor_sync(kFull, d, o);
+        }
+        if (lane == 0) {
+            atomicAdd(stats, (unsigned long long)p);
+            atomicAdd(stats + 1, (unsigned long long)d);
+        }
+    }
+    seg_sync<CL>();   // no CTA leaves while another may still address its shared memory
+}
+
+// ---------------------------------------------------------------------------
+// Wide decoder: one warp (32 lanes) per stream, CL CTAs per segment.
+// Round 0 evaluates Q at 32 points of the window (the last is hi + 1, the
+// escape test); it depends only on the parameters, so the round 0 of step
+// t + 1 is computed while step t runs and leaves the dependent chain. With
+// 32 points the bracket it leaves holds at most 16 symbols, so one more
+// round over its interior always finishes the search: each step costs one
+// dependent CDF evaluation. The segment's refill mask is combined with one
+// shared-memory OR per warp (remote for CL > 1) into triple-buffered words.
+// ---------------------------------------------------------------------------
+template <int CL>
+__device__ __forceinline__ void or_all(uint32_t* local, uint32_t v)
+{
+    if constexpr (CL == 1) {
+        atomicOr(local, v);
+    } else {
+        const uint32_t a = (uint32_t)__cvta_generic_to_shared(local);
+#pragma unroll
+        for (uint32_t r = 0; r < (uint32_t)CL; ++r) {
+            uint32_t ra;
+            asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(a), "r"(r));
+            asm volatile("red.shared::cluster.or.b32 [%0], %1;" ::"r"(ra), "r"(v) : "memory");
+        }
+    }
+}
+
+template <int K>
+__device__ __forceinline__ int wide_point(const Mix<K>& m, int lane)
+{
+    const int W = m.hi - m.lo + 1;
+    return m.lo + ((lane + 1) * W + 31) / 32;
+}
+
+template <int K, typename T, int CL>
+__global__ void __launch_bounds__(32 * 32 / CL) fgmm_dec_wide_kernel(const T* __restrict__ params, int64_t N,
+                                                                     int32_t S, int64_t T_steps,
+                                                                     const uint16_t* __restrict__ words,
+                                                                     int64_t n_words,
+                                                                     const int64_t* __restrict__ offsets,
+                                                                     int32_t* __restrict__ out, int32_t* err,
+                                                                     unsigned long long* stats, int mode)
+{
+    constexpr int SPC = 32 / CL;       // streams (warps) per CTA
+    constexpr int NT = 32 * SPC;
+    extern __shared__ __align__(16) unsigned char smem[];
+    T* ring = reinterpret_cast<T*>(smem);                                                  // [kRing][3K][SPC]
+    uint32_t* masks = reinterpret_cast<uint32_t*>(smem + sizeof(T) * kRing * 3 * K * SPC); // [3][4]
+    uint16_t* wsm = reinterpret_cast<uint16_t*>(masks + 12);                               // [kWordCap]
+
+    const int rank = CL > 1 ? (int)cluster_rank() : 0;
+    const int tid = threadIdx.x, lane = tid & 31, wl = tid >> 5;
+    const int ws = rank * SPC + wl;                    // stream within the segment
+    const uint32_t bit = 1u << ws;
+    const int64_t g = blockIdx.x / CL;
+    const int64_t beg = offsets[g], end = offsets[g + 1];
+    if (!(beg >= 0 && end <= n_words && end - beg >= 64)) {
+        if (tid == 0 && rank == 0) set_error(err, kErrCorrupt);
+        return;
+    }
+    const int64_t seg_len = end - beg;
+    const bool staged = seg_len <= kWordCap;
+    const uint16_t* wsrc = staged ? wsm : words;
+    const int64_t wbase = staged ? beg : 0;
+    const int64_t nbase = g * 32 + rank * SPC;
+#pragma unroll
+    for (int p = 0; p < kPF; ++p) {
+        if (p < T_steps)
+            stage_params<K, T, SPC>(ring + (p % kRing) * 3 * K * SPC, params, N, p * (int64_t)S + nbase, tid, NT, mode);
+        cp_async_commit();
+    }
+    if (staged)
+        for (int64_t i = tid; i < seg_len; i += NT) wsm[i] = __ldg(words + beg + i);
+    if (tid < 12) masks[tid] = 0u;
+    cp_async_wait<kPF - 2>();   // steps 0 and 1 resident
+    seg_sync<CL>();
+
+    uint32_t x = (uint32_t)wsrc[end - 64 + 2 * ws - wbase] | ((uint32_t)wsrc[end - 63 + 2 * ws - wbase] << 16);
+    int64_t ptr = end - 64;
+    bool bad = false, badp = false;
+    int probes = 0, decoded = 0;
+
+    // step 0's mixture and round-0 probe
+    Mix<K> m;
+    uint32_t q0 = 0;
+    {
+        RawParams<K> r;
+#pragma unroll
+        for (int i = 0; i < 3 * K; ++i) r.v[i] = smem_param<T>(ring + i * SPC + wl);
+        const bool ok = mix_from_params<K>(r, m);
+        const bool act0 = T_steps > 0 && g * 32 + ws < N;
+        badp |= act0 && !ok;
+        if (act0) { q0 = q_at<K>(m, wide_point<K>(m, lane)); ++probes; }
+    }
+
+    for (int64_t t = 0; t < T_steps; ++t) {
+        if (t + kPF < T_steps)
+            stage_params<K, T, SPC>(ring + ((t + kPF) % kRing) * 3 * K * SPC, params, N,
+                                    (t + kPF) * (int64_t)S + nbase, tid, NT, mode);
+        cp_async_commit();
+        const int64_t n = t * (int64_t)S + g * 32 + ws;
+        const bool act = n < N;   // uniform over the warp
+        const uint32_t slot = x & 0xffffu;
+        int32_t s = 0;
+        bool esc = false;
+        uint32_t start = 0, freq = 1;
+        // round 0 (precomputed): the symbol lies between points c-1 and c
+        const int c = __popc(__ballot_sync(kFull, act && q0 <= slot));
+        const uint32_t q_last = __shfl_sync(kFull, q0, 31);   // Q(hi + 1)
+        if (act && c == 32) {
+            esc = true;
+            start = q_last;
+            freq = kM - start;
+        }
+        const int W = m.hi - m.lo + 1;
+        const int a = c > 0 ? m.lo + (c * W + 31) / 32 : m.lo;
+        const int b = m.lo + ((min(c, 31) + 1) * W + 31) / 32;
+        const uint32_t qc1 = __shfl_sync(kFull, q0, c > 0 ? c - 1 : 0);
+        const uint32_t qa0 = c > 0 ? qc1 : 0u;                 // Q(lo) = 0
+        const uint32_t qb0 = __shfl_sync(kFull, q0, c < 32 ? c : 31);
+        // round 1: every point strictly inside (a, b) (at most 15)
+        const int L = b - a;
+        const bool valid = act && !esc && lane < L - 1;
+        const uint32_t q1 = valid ? q_at<K>(m, a + 1 + lane) : 0u;
+        probes += valid;
+        const int c1 = __popc(__ballot_sync(kFull, valid && q1 <= slot));
+        const uint32_t q1a = __shfl_sync(kFull, q1, c1 > 0 ? c1 - 1 : 0);
+        const uint32_t q1b = __shfl_sync(kFull, q1, c1 < 31 ? c1 : 31);
+        // next step's mixture and round-0 probe: independent of the state,
+        // so they overlap with this step's dependent chain
+        Mix<K> mn;
+        uint32_t q0n = 0;
+        if (t + 1 < T_steps) {
+            const T* slot_p = ring + ((t + 1) % kRing) * 3 * K * SPC;
+            RawParams<K> r;
+#pragma unroll
+            for (int i = 0; i < 3 * K; ++i) r.v[i] = smem_param<T>(slot_p + i * SPC + wl);
+            const bool ok = mix_from_params<K>(r, mn);
+            const bool actn = n + S < N;
+            badp |= actn && !ok;
+            if (actn) { q0n = q_at<K>(mn, wide_point<K>(mn, lane)); ++probes; }
+        }
+        if (act && !esc) {
+            s = a + c1;
+            start = c1 > 0 ? q1a : qa0;
+            freq = (c1 < L - 1 ? q1b : qb0) - start;
+        }
+        if (act) {
+            x = freq * (x >> 16) + slot - start;
+            decoded += (lane == 0);
+        }
+        // parameters of step t + 2 resident before the barrier publishes them
+        cp_async_wait<kPF - 2>();
+        uint32_t* mk = masks + (int)(t % 3) * 4;
+        const bool need = act && x < kL;
+        if (lane == 0) {
+            if (need) or_all<CL>(mk, bit);
+            if (esc) or_all<CL>(mk + 1, bit);
+        }
+        seg_sync<CL>();
+        const uint32_t M = mk[0], E = mk[1];
+        if (tid < 4) masks[(int)((t + 2) % 3) * 4 + tid] = 0u;   // buffer of step t + 2 (last read at t - 1)
+        const uint32_t below = bit - 1u;
+        if (M) {
+            const int cnt = __popc(M);
+            if (need) {
+                const int64_t idx = ptr - cnt + __popc(M & below);
+                uint32_t v = 0;
+                if (idx >= beg) v = wsrc[idx - wbase];
+                else bad = true;
+                x = (x << 16) | v;
+            }
+            ptr -= cnt;
+        }
+        if (E) {   // uniform over the segment
+            uint32_t hi16 = 0, lo16 = 0;
+            if (esc) { hi16 = x & 0xffffu; x >>= 16; }
+            const bool n2 = esc && x < kL;
+            if (lane == 0 && n2) or_all<CL>(mk + 2, bit);
+            seg_sync<CL>();
+            const uint32_t M2 = mk[2];
+            if (M2) {
+                const int cnt = __popc(M2);
+                if (n2) {
+                    const int64_t idx = ptr - cnt + __popc(M2 & below);
+                    uint32_t v = 0;
+                    if (idx >= beg) v = wsrc[idx - wbase];
+                    else bad = true;
+                    x = (x << 16) | v;
+                }
+                ptr -= cnt;
+            }
+            if (esc) { lo16 = x & 0xffffu; x >>= 16; }
+            const bool n3 = esc && x < kL;
+            if (lane == 0 && n3) or_all<CL>(mk + 3, bit);
+            seg_sync<CL>();
+            const uint32_t M3 = mk[3];
+            if (M3) {
+                const int cnt = __popc(M3);
+                if (n3) {
+                    const int64_t idx = ptr - cnt + __popc(M3 & below);
+                    uint32_t v = 0;
+                    if (idx >= beg) v = wsrc[idx - wbase];
+                    else bad = true;
+                    x = (x << 16) | v;
+                }
+                ptr -= cnt;
+            }
+            if (esc) s = (int32_t)((hi16 << 16) | lo16);
+        }
+        if (act && lane == 0) out[n] = s;
+        m = mn;
+        q0 = q0n;
+    }
+    cp_async_wait<0>();
+    const bool fail = bad || x != kL || ptr != beg;
+    if (__syncthreads_or(fail) && tid == 0) set_error(err, kErrCorrupt);
+    if (__syncthreads_or(badp) && tid == 0) set_error(err, kErrBadParams);
+    if (stats) {
+        int p = probes, d = decoded;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            p += __shfl_xor_sync(kFull, p, o);
+            d += __shfl_xor_sync(kFull, d, o);
+        }
+        if (lane == 0) {
+            atomicAdd(stats, (unsigned long long)p);
+            atomicAdd(stats + 1, (unsigned long long)d);
+        }
+    }
+    seg_sync<CL>();
+}
+
+template <int K, typename T, int CL>
+cudaError_t launch_wide(const DecodeArgs& a, cudaStream_t st)
+{
+    constexpr int SPC = 32 / CL;
+    const size_t smem = sizeof(T) * kRing * 3 * K * SPC + sizeof(uint32_t) * 12 + sizeof(uint16_t) * kWordCap;
+    auto kern = fgmm_dec_wide_kernel<K, T, CL>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const uintptr_t base = reinterpret_cast<uintptr_t>(a.params);
+    int mode = 0;
+    if (base % 16 == 0 && (a.N * (int64_t)sizeof(T)) % 16 == 0 && SPC * sizeof(T) >= 16) mode = 2;
+    else if (base % 4 == 0 && (a.N * (int64_t)sizeof(T)) % 4 == 0 && SPC * sizeof(T) >= 4) mode = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(a.nseg * CL));
+    cfg.blockDim = dim3(32 * SPC);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CL;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = CL > 1 ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kern, static_cast<const T*>(a.params), a.N, a.S, a.T, a.words, a.n_words,
+                              a.offsets, a.out, a.err, a.stats, mode);
+}
+
+template <int K, typename T>
+cudaError_t launch_wide_cl(const DecodeArgs& a, int CL, cudaStream_t st)
+{
+    switch (CL) {
+    case 8: return launch_wide<K, T, 8>(a, st);
+    case 4: return launch_wide<K, T, 4>(a, st);
+    case 2: return launch_wide<K, T, 2>(a, st);
+    default: return launch_wide<K, T, 1>(a, st);
+    }
+}
+
+template <int K, typename T, int G, int CL>
+cudaError_t launch_coop(const DecodeArgs& a, cudaStream_t st)
+{
+    constexpr int SPC = 32 / CL;
+    const size_t smem = sizeof(T) * kRing * 3 * K * SPC + sizeof(uint32_t) * 6 * G + sizeof(uint16_t) * kWordCap;
+    auto kern = fgmm_dec_coop_kernel<K, T, G, CL>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    // copy mode: rows start at params + r * N (elements), so the row
+    // alignment follows from the base pointer and N
+    const uintptr_t base = reinterpret_cast<uintptr_t>(a.params);
+    int mode = 0;
+    if (base % 16 == 0 && (a.N * (int64_t)sizeof(T)) % 16 == 0 && SPC * sizeof(T) >= 16) mode = 2;
+    else if (base % 4 == 0 && (a.N * (int64_t)sizeof(T)) % 4 == 0) mode = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(a.nseg * CL));
+    cfg.blockDim = dim3(32 * G / CL);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CL;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = CL > 1 ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kern, static_cast<const T*>(a.params), a.N, a.S, a.T, a.words, a.n_words,
+                              a.offsets, a.out, a.err, a.stats, mode);
+}
+
+template <int K, typename T, int G>
+cudaError_t launch_coop_cl(const DecodeArgs& a, int CL, cudaStream_t st)
+{
+    if constexpr (G >= 4) {
+        if (CL == 4) return launch_coop<K, T, G, 4>(a, st);
+    }
+    if constexpr (G >= 2) {
+        if (CL == 2) return launch_coop<K, T, G, 2>(a, st);
+    }
+    return launch_coop<K, T, G, 1>(a, st);
+}
+
+template <int K, typename T>
+cudaError_t launch_k(const DecodeArgs& a, int G, int CL, cudaStream_t st)
+{
+    switch (G) {
+    case 2: return launch_coop_cl<K, T, 2>(a, CL, st);
+    case 4: return launch_coop_cl<K, T, 4>(a, CL, st);
+    case 8: return launch_coop_cl<K, T, 8>(a, CL, st);
+    case 16: return launch_coop_cl<K, T, 16>(a, CL, st);
+    case 32: return launch_wide_cl<K, T>(a, CL, st);
+    default: {
+        const int threads = 32;   // one warp (segment) per block: segments spread over all SMs
+        const int64_t blocks = (a.nseg * 32 + threads - 1) / threads;
+        fgmm_dec_kernel<K, T><<<(unsigned)blocks, threads, 0, st>>>(static_cast<const T*>(a.params), a.N, a.S, a.T,
+                                                                    a.words, a.n_words, a.offsets, a.nseg, a.out,
+                                                                    a.err, a.stats);
+        return cudaGetLastError();
+    }
+    }
+}
+
+template <typename T>
+cudaError_t launch_t(const DecodeArgs& a, int K, int G, int CL, cudaStream_t st)
+{
+    switch (K) {
+    case 1: return launch_k<1, T>(a, G, CL, st);
+    case 2: return launch_k<2, T>(a, G, CL, st);
+    case 3: return launch_k<3, T>(a, G, CL, st);
+    default: return launch_k<4, T>(a, G, CL, st);
+    }
+}
+
+}  // namespace
+
+// Launch entry for one parameter type (defined in the instantiation units).
+template <typename T>
+cudaError_t launch_decode_t(const DecodeArgs& a, int K, int G, int CL, cudaStream_t st)
+{
+    return launch_t<T>(a, K, G, CL, st);
+}

@@ -57,6 +57,23 @@ __device__ __forceinline__ float exp_cw(float a)
     return __uint_as_float(bits);
 }
 
+// 1/d, correctly rounded, for normal d with a normal reciprocal
+// (2^-125 <= d <= 2^125): the hardware reciprocal approximation refined by
+// one Newton-Raphson step, y1 = y0 + y0 (1 - d y0), with the residual and the
+// update each a single fused multiply-add. fgmm_self_check compares it with
+// __frcp_rn on every float of that range. Being inline, it lets the K
+// component evaluations of a CDF probe overlap.
+__device__ __forceinline__ float recip(float d)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(d));
+    const float e = __fmaf_rn(-d, y, 1.0f);
+    return __fmaf_rn(y, e, y);
+}
+
+// 1/s for a floored scale s >= 0.11 (any finite value above).
+__device__ __forceinline__ float recip_scale(float s) { return s < 0x1p125f ? recip(s) : __frcp_rn(s); }
+
 // Phi-hat(z): A&S 26.2.17, Phi(x) ~ 1 - Z(x) sum_i b_i t^i, t = 1/(1+px),
 // x = |z|, mirrored for z < 0. p = 0.2316419 and b_1..b_5 are the handbook's;
 // the 1/sqrt(2 pi) of the density Z is pre-multiplied into the b_i
@@ -73,8 +90,8 @@ __device__ __forceinline__ float phi_hat(float z)
     float zc = fminf(fmaxf(z, -12.0f), 12.0f);
     float zs = __fmul_rn(rintf(__fmul_rn(zc, 0x1p22f)), 0x1p-22f);
     float x = fabsf(zs);
-    float d = __fmaf_rn(kP, x, 1.0f);
-    float t = __frcp_rn(d);
+    float d = __fmaf_rn(kP, x, 1.0f);   // d in [1, 3.78]
+    float t = recip(d);
     float h = __fmaf_rn(kC5, t, kC4);
     h = __fmaf_rn(h, t, kC3);
     h = __fmaf_rn(h, t, kC2);
@@ -121,7 +138,7 @@ __device__ __forceinline__ bool load_mix(const T* params, int64_t N, int64_t n, 
         float sp = fmaxf(s, kSigmaMin);
         m.w[k] = w;
         m.mu[k] = mu;
-        m.inv[k] = __frcp_rn(sp);
+        m.inv[k] = recip_scale(sp);
         lo_f = fminf(lo_f, __fmaf_rn(-kR, sp, mu));
         hi_f = fmaxf(hi_f, __fmaf_rn(kR, sp, mu));
     }

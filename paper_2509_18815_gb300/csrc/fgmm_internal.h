@@ -18,6 +18,7 @@ struct fgmm_handle {
     size_t ws_bytes = 0;
     int num_sms = 0;
     int decode_lanes = 0;              // 0 = automatic; else lanes per stream (1, 2, 4, 8, 16, 32)
+    int decode_cluster = 0;            // 0 = automatic; else CTAs per segment (1, 2, 4)
     std::string last_error;
 };
 
@@ -82,7 +83,7 @@ struct DecodeArgs {
     int32_t* err;
     unsigned long long* stats;
 };
-int decode_lanes_auto(int64_t nseg, int num_sms);
-cudaError_t launch_decode(const DecodeArgs& a, int K, int dtype, int lanes, cudaStream_t st);
+void decode_config_auto(int64_t nseg, int num_sms, int* lanes, int* cluster);
+cudaError_t launch_decode(const DecodeArgs& a, int K, int dtype, int lanes, int cluster, cudaStream_t st);
 
 }  // namespace fgmm

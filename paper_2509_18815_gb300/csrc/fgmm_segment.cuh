@@ -39,7 +39,7 @@ __device__ __forceinline__ bool mix_from_params(const RawParams<K>& r, Mix<K>& m
         const float sp = fmaxf(s, kSigmaMin);
         m.w[k] = w;
         m.mu[k] = mu;
-        m.inv[k] = __frcp_rn(sp);
+        m.inv[k] = recip_scale(sp);
         lo_f = fminf(lo_f, __fmaf_rn(-kR, sp, mu));
         hi_f = fmaxf(hi_f, __fmaf_rn(kR, sp, mu));
     }
@@ -59,6 +59,22 @@ __device__ __forceinline__ bool mix_from_params(const RawParams<K>& r, Mix<K>& m
     return ok;
 }
 
+// Exact x / f and x mod f for x < f * 2^16 (the state after
+// renormalisation), f in [1, 2^16). The FP32 estimate x * (1/f) has relative
+// error below 3 * 2^-24, so with the quotient below 2^16 it is off by less
+// than 0.02 and its truncation by at most one; one correction step each way
+// makes it exact.
+__device__ __forceinline__ uint32_t divmod_small(uint32_t x, uint32_t f, uint32_t& r)
+{
+    const float rf = __frcp_rn((float)f);
+    uint32_t q = __float2uint_rz(__fmul_rn(__uint2float_rn(x), rf));
+    int32_t rem = (int32_t)(x - q * f);
+    if (rem < 0) { --q; rem += (int32_t)f; }
+    else if (rem >= (int32_t)f) { ++q; rem -= (int32_t)f; }
+    r = (uint32_t)rem;
+    return q;
+}
+
 // rANS encode of (start, freq) on the lanes where `part` holds, with the
 // sub-phase's renormalisation words appended in ascending lane order.
 __device__ __forceinline__ void enc_put_warp(uint32_t& x, uint32_t start, uint32_t freq, bool part,
@@ -72,8 +88,9 @@ __device__ __forceinline__ void enc_put_warp(uint32_t& x, uint32_t start, uint32
     }
     base += __popc(m);
     if (part) {
-        const uint32_t q = x / freq;
-        x = (q << 16) + (x - q * freq) + start;
+        uint32_t r;
+        const uint32_t q = divmod_small(x, freq, r);
+        x = (q << 16) + r + start;
     }
 }
 

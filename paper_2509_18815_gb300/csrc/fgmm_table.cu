@@ -68,7 +68,7 @@ __global__ void __launch_bounds__(256) fgmm_table_interval_kernel(const uint16_t
 }
 
 // Decoder: binary search over the table row, one lane per stream.
-__global__ void __launch_bounds__(128) fgmm_table_dec_kernel(const uint16_t* __restrict__ table, int64_t N,
+__global__ void __launch_bounds__(32) fgmm_table_dec_kernel(const uint16_t* __restrict__ table, int64_t N,
                                                              int32_t S, int64_t T_steps,
                                                              const uint16_t* __restrict__ words, int64_t n_words,
                                                              const int64_t* __restrict__ offsets, int64_t nseg,
@@ -213,8 +213,8 @@ fgmm_status fgmm_table_decode(fgmm_handle* h, const fgmm_latent* lat, uint16_t* 
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     launch_build(lat, table, h->d_err, h->num_sms, st);
     const int64_t nseg = S / 32;
-    const int64_t blocks = (nseg * 32 + 127) / 128;
-    fgmm_table_dec_kernel<<<(unsigned)blocks, 128, 0, st>>>(table, lat->N, S, steps_of(lat->N, S), words, n_words,
+    const int64_t blocks = nseg;
+    fgmm_table_dec_kernel<<<(unsigned)blocks, 32, 0, st>>>(table, lat->N, S, steps_of(lat->N, S), words, n_words,
                                                             offsets, nseg, symbols_out, h->d_err);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? FGMM_OK : cuda_fail(h, e, "fgmm_table_decode launch");

@@ -209,8 +209,38 @@ def test_decode_lanes_give_identical_symbols(case, G):
     np.testing.assert_array_equal(out, s)
 
 
-@pytest.mark.parametrize("G", [1, 8, 32])
-def test_decode_lanes_report_corruption(G):
+def _set_cluster(CL):
+    from paper_2509_18815_gb300 import _abi
+    codec = _codec()
+    h = codec.handle()
+    h.check(_abi.fgmm_set_option(h.ptr, _abi.FGMM_OPT_DECODE_CLUSTER, CL))
+
+
+@pytest.mark.parametrize("case", range(len(DECODE_CASES)))
+@pytest.mark.parametrize("G,CL", [(2, 2), (4, 4), (8, 2), (8, 4), (16, 4), (32, 1), (32, 2), (32, 4), (32, 8)])
+def test_decode_clusters_give_identical_symbols(case, G, CL):
+    """A segment spread over a cluster of CL CTAs (refill ranks exchanged
+    through distributed shared memory) decodes the same symbols."""
+    codec = _codec()
+    C, H, W, K, seed, esc, smax, S, bf16, cut = DECODE_CASES[case]
+    lat = synth.make_latent(C, H, W, K, seed=seed, escape_stress=esc, sigma_max=smax)
+    p, s = lat.params, lat.symbols
+    if cut is not None:
+        p, s = np.ascontiguousarray(p[:, :, :cut]), np.ascontiguousarray(s[:cut])
+    dp, ds = dev_params(p, bf16), dev_i32(s)
+    words, off = codec.encode(dp, ds, S)
+    try:
+        _set_lanes(G)
+        _set_cluster(CL)
+        out = codec.decode(dp, words, off, S).cpu().numpy()
+    finally:
+        _set_lanes(0)
+        _set_cluster(0)
+    np.testing.assert_array_equal(out, s)
+
+
+@pytest.mark.parametrize("G,CL", [(1, 1), (8, 1), (32, 1), (8, 4), (32, 8)])
+def test_decode_lanes_report_corruption(G, CL):
     codec = _codec()
     from paper_2509_18815_gb300._abi import FGMM_ERR_CORRUPT, FgmmError
     lat = synth.make_latent(4, 16, 16, 3, seed=504)
@@ -219,6 +249,7 @@ def test_decode_lanes_report_corruption(G):
     junk = torch.randint(-32768, 32767, words.shape, dtype=torch.int16, device="cuda")
     try:
         _set_lanes(G)
+        _set_cluster(CL)
         with pytest.raises(FgmmError) as e:
             codec.decode(dp, junk, off, 64)
         assert e.value.status == FGMM_ERR_CORRUPT
@@ -228,6 +259,7 @@ def test_decode_lanes_report_corruption(G):
         out = codec.decode(dp, words, off, 64).cpu().numpy()
     finally:
         _set_lanes(0)
+        _set_cluster(0)
     np.testing.assert_array_equal(out, lat.symbols)
 
 

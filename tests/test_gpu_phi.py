@@ -43,3 +43,17 @@ def test_phi_off_grid_bit_exact():
     g = codec.phi(torch.from_numpy(z).cuda()).cpu().numpy()
     c = oracle.phi(z)
     assert np.array_equal(g.view(np.uint32), c.view(np.uint32))
+
+
+def test_self_check_fast_reciprocal_and_division():
+    """The Newton-refined reciprocal equals the correctly rounded one on every
+    float of [2^-125, 2^125] (which contains every divisor the coder uses), and
+    the encoder's float-based exact division is exact at the remainder
+    boundaries of every (divisor, quotient) pair."""
+    need_gpu()
+    import ctypes
+    from paper_2509_18815_gb300 import _abi, codec
+    out = (ctypes.c_uint64 * 2)()
+    h = codec.handle()
+    h.check(_abi.fgmm_self_check(h.ptr, out))
+    assert out[0] == 0 and out[1] == 0
