@@ -35,6 +35,11 @@ WORKLOAD = dict(name="latent_192x32x48_k3_s1024", C=192, H=32, W=48, K=3, S=1024
 OPS_PER_COMPONENT = 32
 OPS_PER_EVAL = 7
 FP32_LANES_PER_SM = 128
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from
+# the ncu capture summarised in
+# profiles/fgmm_dec_wide_kernel_latent_192x32x48_k3_s1024.md; valid for the
+# kernel as captured there.
+DECODE_TRAFFIC_BYTES = {"fgmm_dec_wide_kernel": 10777856}
 
 
 def parse():
@@ -46,6 +51,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=30)
     ap.add_argument("--decode-lanes", type=int, default=0, help="0 = automatic")
+    ap.add_argument("--no-throughput", action="store_true", help="skip the large-workload section")
     return ap.parse_args()
 
 
@@ -131,6 +137,139 @@ def cpu_baseline(lat, S, budget_s=8.0):
     dt = time.perf_counter() - t0
     return {"value": reps * lat.N / dt / 1e6, "unit": "Msymbols/s", "cores": 1, "kind": "oracle",
             "sample": f"{reps} encode+decode round trip(s) of the full {lat.N}-symbol latent, single thread"}
+
+
+def _events_ms(fn, reps, flush=None):
+    import torch
+    ts = []
+    for i in range(reps):
+        if flush is not None:
+            flush.fill_(i & 0xff)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    return statistics.median(ts)
+
+
+def throughput_workloads(dev, alu_peak_tops, hbm_gbs, reps=5):
+    """Large workloads where the GPU can be filled: one 320x64x96 latent and a
+    batch of 64 uneven latents (both K = 3, autotuned stream counts, one
+    persistent launch per direction replayed from a CUDA graph), and the
+    learned proposal on 16 latents with scales up to 64. Inputs exceed L2."""
+    import numpy as np
+    import torch
+    from paper_2509_18815_gb300 import _abi, codec, synth
+    h = codec.handle(dev)
+    out = {}
+
+    def batch_case(name, lats):
+        params = [torch.from_numpy(l.params).to(dev) for l in lats]
+        syms = [torch.from_numpy(l.symbols).to(dev) for l in lats]
+        N = sum(l.N for l in lats)
+        b = codec.Batch(params, syms)
+        b.capture()
+        b.encode()
+        b.decode()
+        assert all(torch.equal(b.decoded[i], syms[i]) for i in range(len(lats))), name
+        nw = int(b.total.item())
+        codec.stats_enable(True, h); codec.stats_read(h)
+        b.decode()
+        evals, _ = codec.stats_read(h)
+        codec.stats_enable(False, h)
+        te = _events_ms(lambda: b.encode(sync=False), reps)
+        td = _events_ms(lambda: b.decode(sync=False), reps)
+        coded = 0.0
+        for p_, s_ in zip(params, syms):
+            coded += codec.rate_audit(p_, s_, h)[1]
+        b.close()
+        bytes_sym = 36.0 + 4.0 + 16.0 * nw / N / 8.0
+        enc_ops = 2 * N * (32 * 3 + 7)
+        dec_ops = evals * (32 * 3 + 7)
+        out[name] = {
+            "symbols": N, "latents": len(lats), "segments": sum(s // 32 for s in b.S),
+            "encode_msym_s": N / te / 1e3, "decode_msym_s": N / td / 1e3, "ms_encode": te, "ms_decode": td,
+            "container_overhead_pct": 100.0 * (16.0 * nw / coded - 1.0),
+            "encode_roofline": {"hbm_frac": N * bytes_sym / (te * 1e-3) / 1e9 / hbm_gbs,
+                                "alu_frac": enc_ops / (te * 1e-3) / 1e12 / alu_peak_tops},
+            "decode_roofline": {"alu_frac": dec_ops / (td * 1e-3) / 1e12 / alu_peak_tops,
+                                "hbm_frac": N * bytes_sym / (td * 1e-3) / 1e9 / hbm_gbs},
+        }
+        del params, syms
+
+    # one latent: autotuned S, single-latent encode / decode (automatic
+    # decoder configuration)
+    lat3 = synth.make_latent(320, 64, 96, 3, 1003)
+    dp3 = torch.from_numpy(lat3.params).to(dev)
+    ds3 = torch.from_numpy(lat3.symbols).to(dev)
+    S3 = codec.autotune([lat3.N], h=h)[0]
+    w3, o3 = codec.encode(dp3, ds3, S3, h=h)
+    out3 = torch.empty(lat3.N, dtype=torch.int32, device=dev)
+    codec.decode(dp3, w3, o3, S3, h=h, out=out3)
+    assert torch.equal(out3, ds3)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    te3 = _events_ms(lambda: codec.encode(dp3, ds3, S3, h=h, sync=False), reps, flush)
+    td3 = _events_ms(lambda: codec.decode(dp3, w3, o3, S3, h=h, out=out3, sync=False), reps, flush)
+    coded3 = codec.rate_audit(dp3, ds3, h)[1]
+    out["latent_320x64x96_k3"] = {"symbols": lat3.N, "S": S3, "segments": S3 // 32,
+                                  "encode_msym_s": lat3.N / te3 / 1e3, "decode_msym_s": lat3.N / td3 / 1e3,
+                                  "ms_encode": te3, "ms_decode": td3,
+                                  "container_overhead_pct": 100.0 * (16.0 * w3.numel() / coded3 - 1.0)}
+    del dp3, ds3, w3, o3, out3, flush
+    shapes = synth.batch_shapes(64, seed=1004)
+    batch_case("batch64_uneven_k3", [synth.make_latent(C, H, W, 3, 1004 + i) for i, (C, H, W) in enumerate(shapes)])
+
+    # learned proposal: trained on 2^21 triples, decoding 16 latents of
+    # 320x64x96 with scales up to 64
+    from paper_2509_18815_gb300.proposal import init_theta
+    train = synth.make_latent(32, 256, 256, 3, seed=1005, sigma_max=64.0)
+    rng = np.random.default_rng(11)
+    X, t = codec.mlp_data(torch.from_numpy(train.params).to(dev), torch.from_numpy(train.symbols).to(dev),
+                          torch.from_numpy(rng.random(train.N).astype(np.float32)).to(dev), h)
+    tr = codec.MlpTrainer(init_theta(12), device=dev, h=h)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for steps, lr in [(2000, 3e-3), (1000, 1e-3), (1000, 3e-4)]:
+        tr.train(X, t, steps=steps, batch=8192, lr=lr)
+    train_s = time.perf_counter() - t0
+    P = tr.packed()
+    del X, t
+    lats = [synth.make_latent(320, 64, 96, 3, seed=1105 + i, sigma_max=64.0) for i in range(16)]
+    S_all = codec.autotune([l.N for l in lats], h=h)
+    res = {"plain": [0.0, 0, 0, 0], "proposal": [0.0, 0, 0, 0]}
+    for l, S in zip(lats, S_all):
+        dp = torch.from_numpy(l.params).to(dev)
+        ds = torch.from_numpy(l.symbols).to(dev)
+        words, off = codec.encode(dp, ds, S, h=h)
+        o = torch.empty(l.N, dtype=torch.int32, device=dev)
+        for kind in ("plain", "proposal"):
+            if kind == "plain":
+                h.check(_abi.fgmm_set_option(h.ptr, _abi.FGMM_OPT_DECODE_LANES, 1))
+                fn = lambda: codec.decode(dp, words, off, S, h=h, out=o, sync=False)
+            else:
+                fn = lambda: codec.decode_proposal(dp, words, off, S, P, h=h, out=o, sync=False)
+            codec.stats_enable(True, h); codec.stats_read(h)
+            fn(); h.sync()
+            ev, nd, hits = codec.stats_read(h, with_hits=True)
+            codec.stats_enable(False, h)
+            assert torch.equal(o, ds), kind
+            ms = _events_ms(fn, 3)
+            r = res[kind]
+            r[0] += ms; r[1] += ev; r[2] += nd; r[3] += hits
+            h.check(_abi.fgmm_set_option(h.ptr, _abi.FGMM_OPT_DECODE_LANES, 0))
+    out["proposal_16x320x64x96_sigma64"] = {
+        "symbols": res["plain"][2], "train_s": train_s, "train_samples": 4000 * 8192,
+        "plain_decode_msym_s": res["plain"][2] / res["plain"][0] / 1e3,
+        "proposal_decode_msym_s": res["proposal"][2] / res["proposal"][0] / 1e3,
+        "plain_cdf_evals_per_symbol": res["plain"][1] / res["plain"][2],
+        "proposal_cdf_evals_per_symbol": res["proposal"][1] / res["proposal"][2],
+        "proposal_hit_rate": res["proposal"][3] / res["proposal"][2],
+        "streams_per_latent": S_all[0],
+    }
+    return out
 
 
 def run_reference(args):
@@ -373,13 +512,18 @@ def run_fgmm(args):
         "roofline": {"kernel": {0: "fgmm_dec_wide_kernel", 1: "fgmm_dec_kernel", 32: "fgmm_dec_wide_kernel"}.get(
                          args.decode_lanes, "fgmm_dec_coop_kernel"),
                      "bound": "alu", "achieved": achieved, "peak": alu_peak,
-                     "unit": "Tops/s (FP32 lane ops)", "frac": achieved / alu_peak, "traffic": None,
+                     "unit": "Tops/s (FP32 lane ops)", "frac": achieved / alu_peak,
+                     "traffic": DECODE_TRAFFIC_BYTES.get(
+                         {0: "fgmm_dec_wide_kernel", 1: "fgmm_dec_kernel", 32: "fgmm_dec_wide_kernel"}.get(
+                             args.decode_lanes, "fgmm_dec_coop_kernel")),
                      "peak_source": f"derived: {props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
                                     f"{sm_max:.0f} MHz"},
         "clocks": clk,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(lat, S)
+    if not args.no_throughput:
+        result["throughput"] = throughput_workloads(dev, alu_peak, float(peaks.get("hbm_gbs", 6800.0)))
     if rank == 0:
         print(json.dumps(result))
     if world > 1:

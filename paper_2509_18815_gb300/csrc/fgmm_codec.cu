@@ -101,25 +101,47 @@ __global__ void __launch_bounds__(256) fgmm_interval_kernel(const T* __restrict_
 // 2. Interleaved rANS encoder, one warp per segment.
 // ---------------------------------------------------------------------------
 
+// Intervals reach the warp through a shared-memory ring filled by cp.async
+// kEncPF steps ahead (4 bytes per lane; zero past N), so the dependent rANS
+// chain never waits on a global load.
+constexpr int kEncRing = 8, kEncPF = 6;
+
+__device__ __forceinline__ void enc_stage(uint32_t* dst, const uint32_t* __restrict__ sf, int64_t n, int64_t N)
+{
+    const uint32_t s = (uint32_t)__cvta_generic_to_shared(dst);
+    const uint32_t* src = n < N ? sf + n : sf;
+    const int bytes = n < N ? 4 : 0;
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(s), "l"(src), "r"(bytes));
+}
+
 __global__ void __launch_bounds__(32) fgmm_rans_enc_kernel(const uint32_t* __restrict__ sf,
                                                            const int32_t* __restrict__ sym, int64_t N, int32_t S,
                                                            int64_t T, uint16_t* __restrict__ seg_words,
                                                            int64_t seg_cap, int64_t* __restrict__ seg_len,
                                                            int64_t nseg)
 {
-    const int64_t g = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    __shared__ uint32_t ring[kEncRing][32];
+    const int64_t g = blockIdx.x;   // one warp (segment) per block
     const int lane = threadIdx.x & 31;
     if (g >= nseg) return;
     uint16_t* out = seg_words + g * seg_cap;
     const uint32_t lt = lanemask_lt();
     uint32_t x = kL;
     int64_t base = 0;
-    int64_t n = (T - 1) * (int64_t)S + g * 32 + lane;
-    uint32_t v = (T > 0 && n < N) ? __ldg(sf + n) : 0u;
-    for (int64_t t = T - 1; t >= 0; --t, n -= S) {
+    const int64_t n_top = (T - 1) * (int64_t)S + g * 32 + lane;   // step T-1; step T-1-k is n_top - k S
+#pragma unroll
+    for (int k = 0; k < kEncPF; ++k) {
+        if (k < T) enc_stage(&ring[k % kEncRing][lane], sf, n_top - (int64_t)k * S, N);
+        asm volatile("cp.async.commit_group;\n" ::);
+    }
+    for (int64_t k = 0; k < T; ++k) {
+        const int64_t n = n_top - k * S;
+        if (k + kEncPF < T) enc_stage(&ring[(k + kEncPF) % kEncRing][lane], sf, n - (int64_t)kEncPF * S, N);
+        asm volatile("cp.async.commit_group;\n" ::);
+        asm volatile("cp.async.wait_group %0;\n" ::"n"(kEncPF));
+        __syncwarp();
         const bool act = n < N;
-        // next (lower) step's interval, loaded ahead of this step's work
-        const uint32_t vn = (t > 0 && n - S < N) ? __ldg(sf + n - S) : 0u;
+        const uint32_t v = ring[k % kEncRing][lane];
         const uint32_t start = v & 0xffffu, freq = v >> 16;
         const bool esc = act && (start + freq == kM);
         if (__ballot_sync(kFull, esc)) {
@@ -128,8 +150,9 @@ __global__ void __launch_bounds__(32) fgmm_rans_enc_kernel(const uint32_t* __res
             enc_put_warp(x, raw >> 16, 1u, esc, out, base, lt);
         }
         enc_put_warp(x, start, freq, act, out, base, lt);
-        v = vn;
+        __syncwarp();   // slot k is refilled kEncRing - kEncPF steps later
     }
+    asm volatile("cp.async.wait_group 0;\n" ::);
     out[base + 2 * lane] = (uint16_t)(x & 0xffffu);
     out[base + 2 * lane + 1] = (uint16_t)(x >> 16);
     if (lane == 0) seg_len[g] = base + 64;

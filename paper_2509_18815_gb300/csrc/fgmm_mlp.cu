@@ -51,7 +51,10 @@ __device__ __forceinline__ float act_grad(float z)
     return r + kActC * z;
 }
 
-// Standardised features of one query (see the file comment).
+// Standardised features of one query (see the file comment). FAST selects
+// the hardware approximations of sqrt, reciprocal and log (the decoder's
+// guess needs no exactness; training data uses the accurate forms).
+template <bool FAST = false>
 __device__ __forceinline__ void features(const float* w_in, const float* mu_in, const float* sg_in, uint32_t slot,
                                          float* x, float& m0, float& s0)
 {
@@ -73,13 +76,19 @@ __device__ __forceinline__ void features(const float* w_in, const float* mu_in, 
     float v = 0.0f;
 #pragma unroll
     for (int k = 0; k < 3; ++k) v += w[k] * (sp[k] * sp[k] + (mu[k] - m0) * (mu[k] - m0));
-    s0 = sqrtf(fmaxf(v, 1e-4f));
-    const float inv = 1.0f / s0;
+    float inv;
+    if (FAST) {
+        inv = rsqrtf(fmaxf(v, 1e-4f));
+        s0 = fmaxf(v, 1e-4f) * inv;
+    } else {
+        s0 = sqrtf(fmaxf(v, 1e-4f));
+        inv = 1.0f / s0;
+    }
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         x[k] = w[k];
         x[3 + k] = (mu[k] - m0) * inv;
-        x[6 + k] = logf(sp[k] * inv);
+        x[6 + k] = FAST ? __logf(sp[k] * inv) : logf(sp[k] * inv);
     }
     x[9] = ((float)slot + 0.5f) * (1.0f / 65536.0f) - 0.5f;
 }
@@ -380,7 +389,7 @@ __global__ void __launch_bounds__(128) mlp_forward_kernel(const float* __restric
 // Proposal-bracketed decoder (K = 3), one warp per segment.
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(128) fgmm_dec_prop_kernel(const T* __restrict__ params, int64_t N, int32_t S,
+__global__ void __launch_bounds__(32) fgmm_dec_prop_kernel(const T* __restrict__ params, int64_t N, int32_t S,
                                                             int64_t T_steps, const uint16_t* __restrict__ words,
                                                             int64_t n_words, const int64_t* __restrict__ offsets,
                                                             int64_t nseg, const MlpPacked* __restrict__ Pg,
@@ -388,12 +397,12 @@ __global__ void __launch_bounds__(128) fgmm_dec_prop_kernel(const T* __restrict_
                                                             unsigned long long* stats)
 {
     __shared__ MlpPacked P;
-    __shared__ uint32_t xs[4][32 * 12];
+    __shared__ uint32_t xs[1][32 * 12];
     for (int i = threadIdx.x; i < (int)(sizeof(MlpPacked) / 4); i += blockDim.x)
         reinterpret_cast<uint32_t*>(&P)[i] = reinterpret_cast<const uint32_t*>(Pg)[i];
     __syncthreads();
-    const int wib = threadIdx.x >> 5;
-    const int64_t g = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int wib = 0;
+    const int64_t g = blockIdx.x;   // one warp (segment) per block: segments spread over all SMs
     const int lane = threadIdx.x & 31;
     if (g >= nseg) return;   // after the block-wide load; no block barrier follows
     const int64_t beg = offsets[g], end = offsets[g + 1];
@@ -422,7 +431,7 @@ __global__ void __launch_bounds__(128) fgmm_dec_prop_kernel(const T* __restrict_
         }
         const uint32_t slot = x & 0xffffu;
         float f[kIn], m0, s0;
-        features(&cur.v[0], &cur.v[3], &cur.v[6], slot, f, m0, s0);
+        features<true>(&cur.v[0], &cur.v[3], &cur.v[6], slot, f, m0, s0);
         const float yv = mlp_warp_forward(&P, f, xs[wib]);   // all lanes take part
         int32_t s = 0;
         bool esc = false;
@@ -643,15 +652,15 @@ fgmm_status fgmm_decode_proposal(fgmm_handle* h, const fgmm_latent* lat, const v
         return fail(h, FGMM_ERR_INVALID_ARG, "fgmm_decode_proposal: NULL buffer");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int64_t nseg = S / 32, T = steps_of(lat->N, S);
-    const int64_t blocks = (nseg * 32 + 127) / 128;
+    const int64_t blocks = nseg;
     unsigned long long* stats = h->stats_on ? h->d_stats : nullptr;
     const MlpPacked* P = static_cast<const MlpPacked*>(packed);
     if (lat->dtype == FGMM_DTYPE_BF16)
-        fgmm_dec_prop_kernel<__nv_bfloat16><<<(unsigned)blocks, 128, 0, st>>>(
+        fgmm_dec_prop_kernel<__nv_bfloat16><<<(unsigned)blocks, 32, 0, st>>>(
             static_cast<const __nv_bfloat16*>(lat->params), lat->N, S, T, words, n_words, offsets, nseg, P,
             symbols_out, h->d_err, stats);
     else
-        fgmm_dec_prop_kernel<float><<<(unsigned)blocks, 128, 0, st>>>(static_cast<const float*>(lat->params), lat->N,
+        fgmm_dec_prop_kernel<float><<<(unsigned)blocks, 32, 0, st>>>(static_cast<const float*>(lat->params), lat->N,
                                                                        S, T, words, n_words, offsets, nseg, P,
                                                                        symbols_out, h->d_err, stats);
     cudaError_t e = cudaGetLastError();
