@@ -13,6 +13,10 @@
 //   symbol; the choice when there are enough segments to fill the GPU. The
 //   next step's parameters are loaded one step ahead into registers.
 //
+// * fgmm_dec_ws_kernel (G = 32, clusters of 2-8 CTAs): one consumer warp per
+//   stream runs the state-dependent chain; a producer warp per stream
+//   prepares the mixture and the 32-point round 0 two steps ahead.
+//
 // * fgmm_dec_coop_kernel (G = 2 .. 32): G lanes cooperate on one stream and
 //   evaluate G points of the quantised CDF per round (G-ary search), so a
 //   step needs ~log_{G+1}(W) dependent rounds instead of ~log_2(W). A CTA of
@@ -498,28 +502,31 @@ __global__ void __launch_bounds__(32 * 32 / CL) fgmm_dec_wide_kernel(const T* __
         const uint32_t qc1 = __shfl_sync(kFull, q0, c > 0 ? c - 1 : 0);
         const uint32_t qa0 = c > 0 ? qc1 : 0u;                 // Q(lo) = 0
         const uint32_t qb0 = __shfl_sync(kFull, q0, c < 32 ? c : 31);
-        // round 1: every point strictly inside (a, b) (at most 15)
+        // Round 1 over the points strictly inside (a, b) (at most 15) and the
+        // next step's mixture and round-0 probe (independent of the state)
+        // are evaluated unconditionally -- pure arithmetic on values already
+        // in registers and shared memory -- so the two dependent chains sit
+        // in one basic block and overlap; unused results are discarded.
         const int L = b - a;
         const bool valid = act && !esc && lane < L - 1;
-        const uint32_t q1 = valid ? q_at<K>(m, a + 1 + lane) : 0u;
+        const uint32_t q1 = q_at<K>(m, min(a + 1 + lane, m.hi + 1));
         probes += valid;
-        const int c1 = __popc(__ballot_sync(kFull, valid && q1 <= slot));
-        const uint32_t q1a = __shfl_sync(kFull, q1, c1 > 0 ? c1 - 1 : 0);
-        const uint32_t q1b = __shfl_sync(kFull, q1, c1 < 31 ? c1 : 31);
-        // next step's mixture and round-0 probe: independent of the state,
-        // so they overlap with this step's dependent chain
         Mix<K> mn;
-        uint32_t q0n = 0;
-        if (t + 1 < T_steps) {
+        uint32_t q0n;
+        const bool actn = (t + 1 < T_steps) && (n + S < N);
+        {
             const T* slot_p = ring + ((t + 1) % kRing) * 3 * K * SPC;
             RawParams<K> r;
 #pragma unroll
             for (int i = 0; i < 3 * K; ++i) r.v[i] = smem_param<T>(slot_p + i * SPC + wl);
             const bool ok = mix_from_params<K>(r, mn);
-            const bool actn = n + S < N;
             badp |= actn && !ok;
-            if (actn) { q0n = q_at<K>(mn, wide_point<K>(mn, lane)); ++probes; }
+            q0n = q_at<K>(mn, wide_point<K>(mn, lane));
+            probes += actn;
         }
+        const int c1 = __popc(__ballot_sync(kFull, valid && q1 <= slot));
+        const uint32_t q1a = __shfl_sync(kFull, q1, c1 > 0 ? c1 - 1 : 0);
+        const uint32_t q1b = __shfl_sync(kFull, q1, c1 < 31 ? c1 : 31);
         if (act && !esc) {
             s = a + c1;
             start = c1 > 0 ? q1a : qa0;
@@ -611,6 +618,272 @@ __global__ void __launch_bounds__(32 * 32 / CL) fgmm_dec_wide_kernel(const T* __
     seg_sync<CL>();
 }
 
+// ---------------------------------------------------------------------------
+// Warp-specialised wide decoder. Per stream two warps: a producer that,
+// kLead steps ahead, prepares the stream's mixture (reciprocal scales,
+// window) and evaluates its 32-point round 0 into shared memory, and a
+// consumer that runs only the state-dependent chain of each step: one
+// ballot over the precomputed round 0, one round of CDF evaluations inside
+// the bracket, the inverse rANS step and the segment's refill exchange.
+// Producers and consumers meet at the per-step segment barrier.
+// ---------------------------------------------------------------------------
+constexpr int kLead = 2;          // producer lead (steps)
+constexpr int kPre = 4;           // precomputed-step slots (>= kLead + 2)
+
+template <int K>
+struct PreStep {
+    uint32_t q0[32];              // Q at the 32 round-0 points
+    float w[K], mu[K], inv[K];
+    int lo, hi;
+    float tp;
+    int ok;
+};
+
+template <int K, typename T, int CL>
+__global__ void __launch_bounds__(64 * 32 / CL) fgmm_dec_ws_kernel(const T* __restrict__ params, int64_t N, int32_t S,
+                                                                   int64_t T_steps,
+                                                                   const uint16_t* __restrict__ words,
+                                                                   int64_t n_words,
+                                                                   const int64_t* __restrict__ offsets,
+                                                                   int32_t* __restrict__ out, int32_t* err,
+                                                                   unsigned long long* stats, int mode)
+{
+    constexpr int SPC = 32 / CL;              // streams per CTA
+    constexpr int NT = 64 * SPC;              // SPC consumer warps + SPC producer warps
+    constexpr int PNT = 32 * SPC;             // producer threads
+    extern __shared__ __align__(16) unsigned char smem[];
+    PreStep<K>* pre = reinterpret_cast<PreStep<K>*>(smem);                                  // [kPre][SPC]
+    T* ring = reinterpret_cast<T*>(smem + sizeof(PreStep<K>) * kPre * SPC);               // [kRing][3K][SPC]
+    uint32_t* masks = reinterpret_cast<uint32_t*>(reinterpret_cast<unsigned char*>(ring) +
+                                                  sizeof(T) * kRing * 3 * K * SPC);     // [3][4]
+    uint16_t* wsm = reinterpret_cast<uint16_t*>(masks + 12);                                // [kWordCap]
+
+    const int rank = CL > 1 ? (int)cluster_rank() : 0;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const bool producer = warp >= SPC;
+    const int wl = producer ? warp - SPC : warp;      // stream slot in this CTA
+    const int ws = rank * SPC + wl;                   // stream within the segment
+    const uint32_t bit = 1u << ws;
+    const int ptid = tid - PNT;                       // producer thread index
+    const int64_t g = blockIdx.x / CL;
+    const int64_t beg = offsets[g], end = offsets[g + 1];
+    if (!(beg >= 0 && end <= n_words && end - beg >= 64)) {
+        if (tid == 0 && rank == 0) set_error(err, kErrCorrupt);
+        return;
+    }
+    const int64_t seg_len = end - beg;
+    const bool staged = seg_len <= kWordCap;
+    const uint16_t* wsrc = staged ? wsm : words;
+    const int64_t wbase = staged ? beg : 0;
+    const int64_t nbase = g * 32 + rank * SPC;
+
+    // producer side: prepare step u of this warp's stream into pre[u % kPre]
+    bool badp = false;
+    int probes = 0;
+    auto produce = [&](int64_t u) {
+        const T* slot_p = ring + (u % kRing) * 3 * K * SPC;
+        RawParams<K> r;
+#pragma unroll
+        for (int i = 0; i < 3 * K; ++i) r.v[i] = smem_param<T>(slot_p + i * SPC + wl);
+        Mix<K> m;
+        const bool ok = mix_from_params<K>(r, m);
+        const bool act = u * (int64_t)S + g * 32 + ws < N;
+        badp |= act && !ok;
+        PreStep<K>& P = pre[(u % kPre) * SPC + wl];
+        P.q0[lane] = q_at<K>(m, wide_point<K>(m, lane));
+        probes += act;
+        if (lane == 0) {
+#pragma unroll
+            for (int k = 0; k < K; ++k) { P.w[k] = m.w[k]; P.mu[k] = m.mu[k]; P.inv[k] = m.inv[k]; }
+            P.lo = m.lo;
+            P.hi = m.hi;
+            P.tp = m.tp;
+        }
+    };
+
+    // prologue: parameters of steps 0 .. kLead+1, words, round 0 of steps
+    // 0 .. kLead-1
+    for (int p = 0; p < kLead + 2; ++p) {
+        if (producer && p < T_steps)
+            stage_params<K, T, SPC>(ring + (p % kRing) * 3 * K * SPC, params, N, p * (int64_t)S + nbase, ptid, PNT,
+                                    mode);
+        cp_async_commit();
+    }
+    if (staged)
+        for (int64_t i = tid; i < seg_len; i += NT) wsm[i] = __ldg(words + beg + i);
+    if (tid < 12) masks[tid] = 0u;
+    cp_async_wait<1>();   // steps 0 .. kLead resident
+    __syncthreads();
+    if (producer)
+        for (int64_t u = 0; u < kLead && u < T_steps; ++u) produce(u);
+    seg_sync<CL>();
+
+    uint32_t x = (uint32_t)wsrc[end - 64 + 2 * ws - wbase] | ((uint32_t)wsrc[end - 63 + 2 * ws - wbase] << 16);
+    int64_t ptr = end - 64;
+    bool bad = false;
+    int decoded = 0;
+
+    for (int64_t t = 0; t < T_steps; ++t) {
+        if (producer) {
+            if (t + kLead + 2 < T_steps)
+                stage_params<K, T, SPC>(ring + ((t + kLead + 2) % kRing) * 3 * K * SPC, params, N,
+                                        (t + kLead + 2) * (int64_t)S + nbase, ptid, PNT, mode);
+            cp_async_commit();
+            if (t + kLead < T_steps) produce(t + kLead);
+            cp_async_wait<1>();   // step t + kLead + 1 resident for the next iteration
+        }
+        const int64_t n = t * (int64_t)S + g * 32 + ws;
+        const bool act = !producer && n < N;
+        int32_t s = 0;
+        bool esc = false;
+        uint32_t start = 0, freq = 1;
+        if (!producer) {
+            const PreStep<K>& P = pre[(t % kPre) * SPC + wl];
+            Mix<K> m;
+#pragma unroll
+            for (int k = 0; k < K; ++k) { m.w[k] = P.w[k]; m.mu[k] = P.mu[k]; m.inv[k] = P.inv[k]; }
+            m.lo = P.lo;
+            m.hi = P.hi;
+            m.tp = P.tp;
+            const uint32_t q0 = P.q0[lane];
+            const uint32_t slot = x & 0xffffu;
+            const int c = __popc(__ballot_sync(kFull, act && q0 <= slot));
+            const uint32_t q_last = __shfl_sync(kFull, q0, 31);
+            if (act && c == 32) {
+                esc = true;
+                start = q_last;
+                freq = kM - start;
+            }
+            const int W = m.hi - m.lo + 1;
+            const int a = c > 0 ? m.lo + (c * W + 31) / 32 : m.lo;
+            const int b = m.lo + ((min(c, 31) + 1) * W + 31) / 32;
+            const uint32_t qc1 = __shfl_sync(kFull, q0, c > 0 ? c - 1 : 0);
+            const uint32_t qa0 = c > 0 ? qc1 : 0u;
+            const uint32_t qb0 = __shfl_sync(kFull, q0, c < 32 ? c : 31);
+            const int L = b - a;
+            const bool valid = act && !esc && lane < L - 1;
+            const uint32_t q1 = q_at<K>(m, min(a + 1 + lane, m.hi + 1));
+            probes += valid;
+            const int c1 = __popc(__ballot_sync(kFull, valid && q1 <= slot));
+            const uint32_t q1a = __shfl_sync(kFull, q1, c1 > 0 ? c1 - 1 : 0);
+            const uint32_t q1b = __shfl_sync(kFull, q1, c1 < 31 ? c1 : 31);
+            if (act && !esc) {
+                s = a + c1;
+                start = c1 > 0 ? q1a : qa0;
+                freq = (c1 < L - 1 ? q1b : qb0) - start;
+            }
+            if (act) {
+                x = freq * (x >> 16) + slot - start;
+                decoded += (lane == 0);
+            }
+        }
+        uint32_t* mk = masks + (int)(t % 3) * 4;
+        const bool need = act && x < kL;
+        if (lane == 0 && !producer) {
+            if (need) or_all<CL>(mk, bit);
+            if (esc) or_all<CL>(mk + 1, bit);
+        }
+        seg_sync<CL>();
+        const uint32_t M = mk[0], E = mk[1];
+        if (tid < 4) masks[(int)((t + 2) % 3) * 4 + tid] = 0u;
+        const uint32_t below = bit - 1u;
+        if (M) {
+            const int cnt = __popc(M);
+            if (need) {
+                const int64_t idx = ptr - cnt + __popc(M & below);
+                uint32_t v = 0;
+                if (idx >= beg) v = wsrc[idx - wbase];
+                else bad = true;
+                x = (x << 16) | v;
+            }
+            ptr -= cnt;
+        }
+        if (E) {   // uniform over the segment's CTAs (producers take part in the barriers)
+            uint32_t hi16 = 0, lo16 = 0;
+            if (esc) { hi16 = x & 0xffffu; x >>= 16; }
+            const bool n2 = esc && x < kL;
+            if (lane == 0 && n2) or_all<CL>(mk + 2, bit);
+            seg_sync<CL>();
+            const uint32_t M2 = mk[2];
+            if (M2) {
+                const int cnt = __popc(M2);
+                if (n2) {
+                    const int64_t idx = ptr - cnt + __popc(M2 & below);
+                    uint32_t v = 0;
+                    if (idx >= beg) v = wsrc[idx - wbase];
+                    else bad = true;
+                    x = (x << 16) | v;
+                }
+                ptr -= cnt;
+            }
+            if (esc) { lo16 = x & 0xffffu; x >>= 16; }
+            const bool n3 = esc && x < kL;
+            if (lane == 0 && n3) or_all<CL>(mk + 3, bit);
+            seg_sync<CL>();
+            const uint32_t M3 = mk[3];
+            if (M3) {
+                const int cnt = __popc(M3);
+                if (n3) {
+                    const int64_t idx = ptr - cnt + __popc(M3 & below);
+                    uint32_t v = 0;
+                    if (idx >= beg) v = wsrc[idx - wbase];
+                    else bad = true;
+                    x = (x << 16) | v;
+                }
+                ptr -= cnt;
+            }
+            if (esc) s = (int32_t)((hi16 << 16) | lo16);
+        }
+        if (act && lane == 0) out[n] = s;
+    }
+    cp_async_wait<0>();
+    const bool fail = !producer && (bad || x != kL || ptr != beg);
+    if (__syncthreads_or(fail) && tid == 0) set_error(err, kErrCorrupt);
+    if (__syncthreads_or(badp) && tid == 0) set_error(err, kErrBadParams);
+    if (stats) {
+        int p = probes, d = decoded;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            p += __shfl_xor_sync(kFull, p, o);
+            d += __shfl_xor_sync(kFull, d, o);
+        }
+        if (lane == 0) {
+            atomicAdd(stats, (unsigned long long)p);
+            atomicAdd(stats + 1, (unsigned long long)d);
+        }
+    }
+    seg_sync<CL>();
+}
+
+template <int K, typename T, int CL>
+cudaError_t launch_ws(const DecodeArgs& a, cudaStream_t st)
+{
+    constexpr int SPC = 32 / CL;
+    const size_t smem = sizeof(PreStep<K>) * kPre * SPC + sizeof(T) * kRing * 3 * K * SPC + sizeof(uint32_t) * 12 +
+                        sizeof(uint16_t) * kWordCap;
+    auto kern = fgmm_dec_ws_kernel<K, T, CL>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const uintptr_t base = reinterpret_cast<uintptr_t>(a.params);
+    int mode = 0;
+    if (base % 16 == 0 && (a.N * (int64_t)sizeof(T)) % 16 == 0 && SPC * sizeof(T) >= 16) mode = 2;
+    else if (base % 4 == 0 && (a.N * (int64_t)sizeof(T)) % 4 == 0 && SPC * sizeof(T) >= 4) mode = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(a.nseg * CL));
+    cfg.blockDim = dim3(64 * SPC);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CL;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = CL > 1 ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kern, static_cast<const T*>(a.params), a.N, a.S, a.T, a.words, a.n_words,
+                              a.offsets, a.out, a.err, a.stats, mode);
+}
+
 template <int K, typename T, int CL>
 cudaError_t launch_wide(const DecodeArgs& a, cudaStream_t st)
 {
@@ -642,10 +915,12 @@ cudaError_t launch_wide(const DecodeArgs& a, cudaStream_t st)
 template <int K, typename T>
 cudaError_t launch_wide_cl(const DecodeArgs& a, int CL, cudaStream_t st)
 {
+    // warp-specialised when the CTA has room for a producer warp per stream
+    // (CL >= 2: at most 1024 threads); CL = 1 keeps one warp per stream
     switch (CL) {
-    case 8: return launch_wide<K, T, 8>(a, st);
-    case 4: return launch_wide<K, T, 4>(a, st);
-    case 2: return launch_wide<K, T, 2>(a, st);
+    case 8: return launch_ws<K, T, 8>(a, st);
+    case 4: return launch_ws<K, T, 4>(a, st);
+    case 2: return launch_ws<K, T, 2>(a, st);
     default: return launch_wide<K, T, 1>(a, st);
     }
 }
