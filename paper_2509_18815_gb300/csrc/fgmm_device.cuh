@@ -42,7 +42,12 @@ __device__ __forceinline__ float exp_cw(float a)
     const float kLog2e = 0x1.715476p+0f;
     const float kLn2Hi = 0x1.62e4p-1f;
     const float kLn2Lo = 0x1.7f7d1cp-20f;
-    float k = rintf(__fmul_rn(a, kLog2e));
+    // k = rint(a log2 e) by adding and removing 1.5 * 2^23 (round to nearest
+    // even, exact for |a log2 e| < 2^22); the sum's low mantissa bits hold k
+    // in two's complement, so (bits << 23) is k * 2^23 modulo 2^32.
+    const float kMagic = 0x1.8p23f;
+    const float tm = __fadd_rn(__fmul_rn(a, kLog2e), kMagic);
+    const float k = __fsub_rn(tm, kMagic);
     float r = __fmaf_rn(-k, kLn2Hi, a);
     r = __fmaf_rn(-k, kLn2Lo, r);
     float p = 0x1.a01a02p-13f;           // fp32(1/7!)
@@ -53,8 +58,7 @@ __device__ __forceinline__ float exp_cw(float a)
     p = __fmaf_rn(p, r, 0.5f);
     p = __fmaf_rn(p, r, 1.0f);
     p = __fmaf_rn(p, r, 1.0f);
-    uint32_t bits = __float_as_uint(p) + (static_cast<uint32_t>(static_cast<int32_t>(k)) << 23);
-    return __uint_as_float(bits);
+    return __uint_as_float(__float_as_uint(p) + (__float_as_uint(tm) << 23));
 }
 
 // 1/d, correctly rounded, for normal d with a normal reciprocal
@@ -87,9 +91,11 @@ __device__ __forceinline__ float phi_hat(float z)
     const float kC3 = 0x1.6be1c6p-1f;
     const float kC4 = -0x1.7401c6p-1f;
     const float kC5 = 0x1.0fb844p-1f;
-    float zc = fminf(fmaxf(z, -12.0f), 12.0f);
-    float zs = __fmul_rn(rintf(__fmul_rn(zc, 0x1p22f)), 0x1p-22f);
-    float x = fabsf(zs);
+    // |z| clamped to 12, rounded to the grid (rint is odd, so this is
+    // |rint(clamp(z) 2^22)| 2^-22); the mirror below tests z's sign, which
+    // agrees with the rounded value's except when that is +-0, where both
+    // branches give 1/2 (Phi-hat(0) = 1 - q(0) = q(0) = 1/2 exactly).
+    const float x = __fmul_rn(rintf(__fmul_rn(fminf(fabsf(z), 12.0f), 0x1p22f)), 0x1p-22f);
     float d = __fmaf_rn(kP, x, 1.0f);   // d in [1, 3.78]
     float t = recip(d);
     float h = __fmaf_rn(kC5, t, kC4);
@@ -99,7 +105,7 @@ __device__ __forceinline__ float phi_hat(float z)
     float g = __fmul_rn(h, t);
     float a = __fmul_rn(-0.5f, __fmul_rn(x, x));
     float q = __fmul_rn(exp_cw(a), g);
-    return zs >= 0.0f ? __fsub_rn(1.0f, q) : q;
+    return z >= 0.0f ? __fsub_rn(1.0f, q) : q;
 }
 
 // Parameter loads from the planar [3][K][N] layout.
@@ -199,21 +205,17 @@ __device__ __forceinline__ void interval_of(const Mix<K>& m, int32_t s, uint32_t
 }
 
 // Decoder search: the symbol whose interval holds `slot`, by binary search
-// over Q on [lo, hi+1] after the escape test (Sec. III-A). Returns true for
-// the escape slot. `probes` counts CDF evaluations.
+// over Q (Sec. III-A). The escape slot is searched as one more symbol: the
+// range is [lo, hi + 2) with Q(hi + 2) = 2^16 standing in for the end of the
+// escape interval (never evaluated), so landing on hi + 1 means escape and no
+// separate escape test is needed. Returns true for the escape slot.
+// `probes` counts CDF evaluations (ceil or floor of log2(W + 1)).
 template <int K>
 __device__ __forceinline__ bool search_slot(const Mix<K>& m, uint32_t slot, int32_t& s, uint32_t& start,
                                             uint32_t& freq, int& probes)
 {
-    const uint32_t qe = q_at<K>(m, m.hi + 1);
-    ++probes;
-    if (slot >= qe) {
-        start = qe;
-        freq = kM - qe;
-        return true;
-    }
-    int a = m.lo, b = m.hi + 1;
-    uint32_t qa = 0, qb = qe;
+    int a = m.lo, b = m.hi + 2;
+    uint32_t qa = 0, qb = kM;
     while (b - a > 1) {
         const int mid = a + ((b - a) >> 1);
         const uint32_t qm = q_at<K>(m, mid);
@@ -224,7 +226,7 @@ __device__ __forceinline__ bool search_slot(const Mix<K>& m, uint32_t slot, int3
     s = a;
     start = qa;
     freq = qb - qa;
-    return false;
+    return a == m.hi + 1;
 }
 
 __device__ __forceinline__ uint32_t lanemask_lt()

@@ -280,5 +280,6 @@ def test_decode_counts_cdf_evaluations():
     assert nsym == lat.N
     lo, hi = oracle.window(lat.params)
     W = (hi - lo + 1).astype(np.float64)
-    # one escape test plus floor/ceil(log2 W) bisection probes per symbol
-    assert np.sum(1 + np.floor(np.log2(W))) <= evals <= np.sum(1 + np.ceil(np.log2(W)))
+    # bisection of [lo, hi + 2) (the escape slot searched as symbol hi + 1):
+    # floor or ceil of log2(W + 1) CDF evaluations per symbol
+    assert np.sum(np.floor(np.log2(W + 1))) <= evals <= np.sum(np.ceil(np.log2(W + 1)))
