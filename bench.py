@@ -35,11 +35,10 @@ WORKLOAD = dict(name="latent_192x32x48_k3_s1024", C=192, H=32, W=48, K=3, S=1024
 OPS_PER_COMPONENT = 32
 OPS_PER_EVAL = 7
 FP32_LANES_PER_SM = 128
-# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from
-# the ncu capture summarised in
-# profiles/fgmm_dec_wide_kernel_latent_192x32x48_k3_s1024.md; valid for the
-# kernel as captured there.
-DECODE_TRAFFIC_BYTES = {"fgmm_dec_wide_kernel": 10777856}
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of
+# the decoder the plan names, from the ncu captures summarised under
+# profiles/; valid for each kernel as captured there (null otherwise).
+DECODE_TRAFFIC_BYTES = {"fgmm_dec_ws_kernel": 10785536}
 
 
 def parse():
@@ -469,6 +468,7 @@ def run_fgmm(args):
     (e2e_ms,) = max_over_ranks([e2e_ms], device=dev)
 
     value = world * N / (ms_step * 1e-3) / 1e6
+    plan = codec.decode_plan(S, h=h)
     props = torch.cuda.get_device_properties(dev)
     peaks = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
@@ -509,13 +509,10 @@ def run_fgmm(args):
         "wall_s_timed_region": t_wall,
         "e2e": {"value": world * N / (e2e_ms * 1e-3) / 1e6, "unit": "Msymbols/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
-        "roofline": {"kernel": {0: "fgmm_dec_wide_kernel", 1: "fgmm_dec_kernel", 32: "fgmm_dec_wide_kernel"}.get(
-                         args.decode_lanes, "fgmm_dec_coop_kernel"),
+        "roofline": {"kernel": plan["kernel"], "lanes": plan["lanes"], "cluster": plan["cluster"],
                      "bound": "alu", "achieved": achieved, "peak": alu_peak,
                      "unit": "Tops/s (FP32 lane ops)", "frac": achieved / alu_peak,
-                     "traffic": DECODE_TRAFFIC_BYTES.get(
-                         {0: "fgmm_dec_wide_kernel", 1: "fgmm_dec_kernel", 32: "fgmm_dec_wide_kernel"}.get(
-                             args.decode_lanes, "fgmm_dec_coop_kernel")),
+                     "traffic": DECODE_TRAFFIC_BYTES.get(plan["kernel"]),
                      "peak_source": f"derived: {props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
                                     f"{sm_max:.0f} MHz"},
         "clocks": clk,

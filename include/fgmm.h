@@ -293,6 +293,22 @@ fgmm_status fgmm_decode_proposal(fgmm_handle *h, const fgmm_latent *lat, const v
 enum { FGMM_OPT_DECODE_LANES = 1, FGMM_OPT_DECODE_CLUSTER = 2 };
 fgmm_status fgmm_set_option(fgmm_handle *h, int32_t option, int64_t value);
 
+/* The decoder fgmm_decode would run for S streams (S / 32 segments) under
+ * the handle's current options; host only, no GPU work, nothing allocated.
+ * out (host, 3 entries): out[0] = lanes per stream, out[1] = CTAs per
+ * segment (cluster size), out[2] = the kernel:
+ *   FGMM_DEC_LANE  one lane per stream, binary search over the window
+ *                  (Sec. III-B), one warp per segment;
+ *   FGMM_DEC_COOP  G = 2..16 lanes per stream, G-ary search;
+ *   FGMM_DEC_WIDE  32 lanes per stream, 32-point search, one CTA per segment;
+ *   FGMM_DEC_WS    32 lanes per stream, producer/consumer warps, a
+ *                  thread-block cluster per segment.
+ * The paper has no counterpart: it decodes with one thread per stream.
+ * Errors: FGMM_ERR_INVALID_ARG for a NULL argument or S not a positive
+ * multiple of 32. */
+enum { FGMM_DEC_LANE = 0, FGMM_DEC_COOP = 1, FGMM_DEC_WIDE = 2, FGMM_DEC_WS = 3 };
+fgmm_status fgmm_decode_plan(fgmm_handle *h, int32_t S, int32_t out[3]);
+
 /* Optional counters. When enabled, decoders add the number of quantised-CDF
  * evaluations they make to a device counter; fgmm_stats_read synchronises
  * `stream` and copies {cdf_evals, symbols_decoded, proposal_hits} to host

@@ -27,6 +27,9 @@ FGMM_DTYPE_BF16 = 1
 FGMM_MAX_K = 4
 FGMM_OPT_DECODE_LANES = 1
 FGMM_OPT_DECODE_CLUSTER = 2
+FGMM_DEC_LANE, FGMM_DEC_COOP, FGMM_DEC_WIDE, FGMM_DEC_WS = 0, 1, 2, 3
+DECODE_KERNELS = {FGMM_DEC_LANE: "fgmm_dec_kernel", FGMM_DEC_COOP: "fgmm_dec_coop_kernel",
+                  FGMM_DEC_WIDE: "fgmm_dec_wide_kernel", FGMM_DEC_WS: "fgmm_dec_ws_kernel"}
 FGMM_MLP_PARAMS = 4929
 FGMM_MLP_PACKED_BYTES = 11024
 
@@ -63,6 +66,7 @@ SIGNATURES = {
     "fgmm_stats_enable": (I32, [P, I32]),
     "fgmm_stats_read": (I32, [P, P, P]),
     "fgmm_set_option": (I32, [P, I32, I64]),
+    "fgmm_decode_plan": (I32, [P, I32, P]),
     "fgmm_table_bytes": (I64, [I64]),
     "fgmm_table_build": (I32, [P, LATP, P, P]),
     "fgmm_table_encode": (I32, [P, LATP, P, I32, P, P, I64, P, P, P]),

@@ -156,6 +156,15 @@ def decode(params: torch.Tensor, words: torch.Tensor, offsets: torch.Tensor, S: 
     return out
 
 
+def decode_plan(S: int, h: Handle | None = None) -> dict:
+    """Decoder that decode() runs for S streams under the handle's options:
+    lanes per stream, CTAs per segment and the kernel's name."""
+    h = h or handle()
+    out = (ctypes.c_int32 * 3)()
+    h.check(_abi.fgmm_decode_plan(h.ptr, S, out))
+    return {"lanes": int(out[0]), "cluster": int(out[1]), "kernel": _abi.DECODE_KERNELS[int(out[2])]}
+
+
 def stats_enable(on: bool = True, h: Handle | None = None):
     h = h or handle()
     h.check(_abi.fgmm_stats_enable(h.ptr, 1 if on else 0))

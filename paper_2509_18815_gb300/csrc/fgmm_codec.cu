@@ -543,15 +543,22 @@ fgmm_status fgmm_decode(fgmm_handle* h, const fgmm_latent* lat, const uint16_t* 
     a.out = symbols_out;
     a.err = h->d_err;
     a.stats = h->stats_on ? h->d_stats : nullptr;
-    int lanes = 1, cluster = 1;
-    decode_config_auto(a.nseg, h->num_sms, &lanes, &cluster);
-    if (h->decode_lanes > 0) {
-        lanes = h->decode_lanes;
-        cluster = 1;
-    }
-    if (h->decode_cluster > 0) cluster = h->decode_cluster;
+    int lanes = 1, cluster = 1, kernel = 0;
+    decode_resolve(a.nseg, h->num_sms, h->decode_lanes, h->decode_cluster, &lanes, &cluster, &kernel);
     cudaError_t e = launch_decode(a, lat->K, lat->dtype, lanes, cluster, st);
     return e == cudaSuccess ? FGMM_OK : cuda_fail(h, e, "fgmm_decode launch");
+}
+
+fgmm_status fgmm_decode_plan(fgmm_handle* h, int32_t S, int32_t* out)
+{
+    if (!h || !out) return fail(h, FGMM_ERR_INVALID_ARG, "fgmm_decode_plan: NULL argument");
+    if (S <= 0 || S % 32 != 0) return fail(h, FGMM_ERR_INVALID_ARG, "S must be a positive multiple of 32");
+    int lanes = 1, cluster = 1, kernel = 0;
+    decode_resolve(S / 32, h->num_sms, h->decode_lanes, h->decode_cluster, &lanes, &cluster, &kernel);
+    out[0] = lanes;
+    out[1] = cluster;
+    out[2] = kernel;
+    return FGMM_OK;
 }
 
 fgmm_status fgmm_set_option(fgmm_handle* h, int32_t option, int64_t value)

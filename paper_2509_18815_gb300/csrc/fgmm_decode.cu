@@ -20,12 +20,27 @@ void decode_config_auto(int64_t nseg, int num_sms, int* lanes, int* cluster)
     *cluster = 1;
 }
 
-cudaError_t launch_decode(const DecodeArgs& a, int K, int dtype, int G, int CL, cudaStream_t st)
+void decode_resolve(int64_t nseg, int num_sms, int opt_lanes, int opt_cluster, int* lanes, int* cluster,
+                    int* kernel)
 {
-    if (a.nseg == 0) return cudaSuccess;
+    int G = 1, CL = 1;
+    decode_config_auto(nseg, num_sms, &G, &CL);
+    if (opt_lanes > 0) {
+        G = opt_lanes;
+        CL = 1;
+    }
+    if (opt_cluster > 0) CL = opt_cluster;
     if (G < 2) CL = 1;
     if (G < 32 && CL > 4) CL = 4;   // the G-ary kernel takes clusters of up to 4
     if (CL > G) CL = G;
+    *lanes = G;
+    *cluster = CL;
+    *kernel = G == 1 ? FGMM_DEC_LANE : (G < 32 ? FGMM_DEC_COOP : (CL == 1 ? FGMM_DEC_WIDE : FGMM_DEC_WS));
+}
+
+cudaError_t launch_decode(const DecodeArgs& a, int K, int dtype, int G, int CL, cudaStream_t st)
+{
+    if (a.nseg == 0) return cudaSuccess;
     if (dtype == FGMM_DTYPE_BF16) return launch_decode_bf16(a, K, G, CL, st);
     return launch_decode_t<float>(a, K, G, CL, st);
 }

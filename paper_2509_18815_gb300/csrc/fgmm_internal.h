@@ -84,6 +84,10 @@ struct DecodeArgs {
     unsigned long long* stats;
 };
 void decode_config_auto(int64_t nseg, int num_sms, int* lanes, int* cluster);
+// Final decoder choice: automatic plan, then the handle's options, then the
+// limits of each kernel (clusters only with G >= 2, at most 4 below G = 32).
+void decode_resolve(int64_t nseg, int num_sms, int opt_lanes, int opt_cluster, int* lanes, int* cluster,
+                    int* kernel);
 cudaError_t launch_decode(const DecodeArgs& a, int K, int dtype, int lanes, int cluster, cudaStream_t st);
 
 }  // namespace fgmm

@@ -239,6 +239,36 @@ def test_decode_clusters_give_identical_symbols(case, G, CL):
     np.testing.assert_array_equal(out, s)
 
 
+def test_decode_plan_follows_segments_and_options():
+    """The plan names the decoder fgmm_decode runs: one lane per stream when
+    segments fill the SMs several times over, 32 lanes and a cluster per
+    segment when segments are few, and the options override both (with the
+    cluster clamped to what each kernel takes)."""
+    codec = _codec()
+    from paper_2509_18815_gb300._abi import FgmmError
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    many = 32 * 4 * sms
+    assert codec.decode_plan(many) == {"lanes": 1, "cluster": 1, "kernel": "fgmm_dec_kernel"}
+    few = 32 * max(1, sms // 4)
+    assert codec.decode_plan(few) == {"lanes": 32, "cluster": 8, "kernel": "fgmm_dec_ws_kernel"}
+    try:
+        _set_lanes(4)
+        assert codec.decode_plan(few) == {"lanes": 4, "cluster": 1, "kernel": "fgmm_dec_coop_kernel"}
+        _set_cluster(8)
+        assert codec.decode_plan(few) == {"lanes": 4, "cluster": 4, "kernel": "fgmm_dec_coop_kernel"}
+        _set_lanes(1)
+        assert codec.decode_plan(few) == {"lanes": 1, "cluster": 1, "kernel": "fgmm_dec_kernel"}
+        _set_lanes(32)
+        _set_cluster(1)
+        assert codec.decode_plan(few) == {"lanes": 32, "cluster": 1, "kernel": "fgmm_dec_wide_kernel"}
+    finally:
+        _set_lanes(0)
+        _set_cluster(0)
+    for bad in (0, -32, 33):
+        with pytest.raises(FgmmError):
+            codec.decode_plan(bad)
+
+
 @pytest.mark.parametrize("G,CL", [(1, 1), (8, 1), (32, 1), (8, 4), (32, 8)])
 def test_decode_lanes_report_corruption(G, CL):
     codec = _codec()
