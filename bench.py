@@ -51,6 +51,10 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=30)
     ap.add_argument("--decode-lanes", type=int, default=0, help="0 = automatic")
     ap.add_argument("--no-throughput", action="store_true", help="skip the large-workload section")
+    ap.add_argument("--batch-only", type=int, default=0, metavar="N",
+                    help="run only the batch case on the first N latents of the 64-latent batch (for profiling)")
+    ap.add_argument("--batch-overhead", type=float, default=0.01,
+                    help="container-overhead bound given to the stream autotuner in --batch-only mode")
     return ap.parse_args()
 
 
@@ -154,6 +158,45 @@ def _events_ms(fn, reps, flush=None):
     return statistics.median(ts)
 
 
+def batch_case(dev, h, out, name, lats, alu_peak_tops, hbm_gbs, reps=5, max_overhead=0.01):
+    """Batch of latents: one persistent launch per direction replayed from a
+    CUDA graph, autotuned streams per latent; adds out[name]."""
+    import torch
+    from paper_2509_18815_gb300 import codec
+    params = [torch.from_numpy(l.params).to(dev) for l in lats]
+    syms = [torch.from_numpy(l.symbols).to(dev) for l in lats]
+    N = sum(l.N for l in lats)
+    b = codec.Batch(params, syms, S=codec.autotune([l.N for l in lats], max_overhead=max_overhead, h=h), h=h)
+    b.capture()
+    b.encode()
+    b.decode()
+    assert all(torch.equal(b.decoded[i], syms[i]) for i in range(len(lats))), name
+    nw = int(b.total.item())
+    codec.stats_enable(True, h); codec.stats_read(h)
+    b.decode()
+    evals, _ = codec.stats_read(h)
+    codec.stats_enable(False, h)
+    te = _events_ms(lambda: b.encode(sync=False), reps)
+    td = _events_ms(lambda: b.decode(sync=False), reps)
+    coded = 0.0
+    for p_, s_ in zip(params, syms):
+        coded += codec.rate_audit(p_, s_, h)[1]
+    b.close()
+    bytes_sym = 36.0 + 4.0 + 16.0 * nw / N / 8.0
+    enc_ops = 2 * N * (32 * 3 + 7)
+    dec_ops = evals * (32 * 3 + 7)
+    out[name] = {
+        "symbols": N, "latents": len(lats), "segments": sum(s // 32 for s in b.S),
+        "encode_msym_s": N / te / 1e3, "decode_msym_s": N / td / 1e3, "ms_encode": te, "ms_decode": td,
+        "container_overhead_pct": 100.0 * (16.0 * nw / coded - 1.0),
+        "encode_roofline": {"hbm_frac": N * bytes_sym / (te * 1e-3) / 1e9 / hbm_gbs,
+                            "alu_frac": enc_ops / (te * 1e-3) / 1e12 / alu_peak_tops},
+        "decode_roofline": {"alu_frac": dec_ops / (td * 1e-3) / 1e12 / alu_peak_tops,
+                            "hbm_frac": N * bytes_sym / (td * 1e-3) / 1e9 / hbm_gbs},
+    }
+    del params, syms
+
+
 def throughput_workloads(dev, alu_peak_tops, hbm_gbs, reps=5):
     """Large workloads where the GPU can be filled: one 320x64x96 latent and a
     batch of 64 uneven latents (both K = 3, autotuned stream counts, one
@@ -164,40 +207,6 @@ def throughput_workloads(dev, alu_peak_tops, hbm_gbs, reps=5):
     from paper_2509_18815_gb300 import _abi, codec, synth
     h = codec.handle(dev)
     out = {}
-
-    def batch_case(name, lats):
-        params = [torch.from_numpy(l.params).to(dev) for l in lats]
-        syms = [torch.from_numpy(l.symbols).to(dev) for l in lats]
-        N = sum(l.N for l in lats)
-        b = codec.Batch(params, syms)
-        b.capture()
-        b.encode()
-        b.decode()
-        assert all(torch.equal(b.decoded[i], syms[i]) for i in range(len(lats))), name
-        nw = int(b.total.item())
-        codec.stats_enable(True, h); codec.stats_read(h)
-        b.decode()
-        evals, _ = codec.stats_read(h)
-        codec.stats_enable(False, h)
-        te = _events_ms(lambda: b.encode(sync=False), reps)
-        td = _events_ms(lambda: b.decode(sync=False), reps)
-        coded = 0.0
-        for p_, s_ in zip(params, syms):
-            coded += codec.rate_audit(p_, s_, h)[1]
-        b.close()
-        bytes_sym = 36.0 + 4.0 + 16.0 * nw / N / 8.0
-        enc_ops = 2 * N * (32 * 3 + 7)
-        dec_ops = evals * (32 * 3 + 7)
-        out[name] = {
-            "symbols": N, "latents": len(lats), "segments": sum(s // 32 for s in b.S),
-            "encode_msym_s": N / te / 1e3, "decode_msym_s": N / td / 1e3, "ms_encode": te, "ms_decode": td,
-            "container_overhead_pct": 100.0 * (16.0 * nw / coded - 1.0),
-            "encode_roofline": {"hbm_frac": N * bytes_sym / (te * 1e-3) / 1e9 / hbm_gbs,
-                                "alu_frac": enc_ops / (te * 1e-3) / 1e12 / alu_peak_tops},
-            "decode_roofline": {"alu_frac": dec_ops / (td * 1e-3) / 1e12 / alu_peak_tops,
-                                "hbm_frac": N * bytes_sym / (td * 1e-3) / 1e9 / hbm_gbs},
-        }
-        del params, syms
 
     # one latent: autotuned S, single-latent encode / decode (automatic
     # decoder configuration)
@@ -219,7 +228,9 @@ def throughput_workloads(dev, alu_peak_tops, hbm_gbs, reps=5):
                                   "container_overhead_pct": 100.0 * (16.0 * w3.numel() / coded3 - 1.0)}
     del dp3, ds3, w3, o3, out3, flush
     shapes = synth.batch_shapes(64, seed=1004)
-    batch_case("batch64_uneven_k3", [synth.make_latent(C, H, W, 3, 1004 + i) for i, (C, H, W) in enumerate(shapes)])
+    batch_case(dev, h, out, "batch64_uneven_k3",
+               [synth.make_latent(C, H, W, 3, 1004 + i) for i, (C, H, W) in enumerate(shapes)], alu_peak_tops,
+               hbm_gbs, reps)
 
     # learned proposal: trained on 2^21 triples, decoding 16 latents of
     # 320x64x96 with scales up to 64
@@ -527,9 +538,29 @@ def run_fgmm(args):
         dist.destroy_process_group()
 
 
+def run_batch_only(args):
+    import torch
+    from paper_2509_18815_gb300 import build, codec, synth
+    build.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    h = codec.handle(dev)
+    props = torch.cuda.get_device_properties(dev)
+    peaks = measured_peaks()
+    alu_peak = props.multi_processor_count * FP32_LANES_PER_SM * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+    shapes = synth.batch_shapes(64, seed=1004)[: args.batch_only]
+    out = {}
+    batch_case(dev, h, out, f"batch{len(shapes)}_uneven_k3",
+               [synth.make_latent(C, H, W, 3, 1004 + i) for i, (C, H, W) in enumerate(shapes)], alu_peak,
+               float(peaks.get("hbm_gbs", 6800.0)), reps=max(args.steps, 1), max_overhead=args.batch_overhead)
+    print(json.dumps(out))
+
+
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.batch_only > 0:
+        run_batch_only(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_fgmm(args)

@@ -625,10 +625,20 @@ __global__ void __launch_bounds__(32 * 32 / CL) fgmm_dec_wide_kernel(const T* __
 // consumer that runs only the state-dependent chain of each step: one
 // ballot over the precomputed round 0, one round of CDF evaluations inside
 // the bracket, the inverse rANS step and the segment's refill exchange.
-// Producers and consumers meet at the per-step segment barrier.
+//
+// The exchange is a flag per stream, not a cluster barrier: each consumer
+// writes (exchange number, refill bit, escape bit) into a double-buffered
+// slot of every CTA of the cluster, then polls its own CTA's copies until
+// all 32 streams of the segment have posted that exchange. A slot is reused
+// two exchanges later, by which time every stream has read it (a stream
+// posts exchange e + 1 only after its wait for exchange e has ended).
+// Producers and consumers of one CTA meet at a CTA barrier once per step.
+// Every wait is bounded: a consumer that gives up records an error and
+// raises an abort flag in all CTAs, after which no wait blocks.
 // ---------------------------------------------------------------------------
 constexpr int kLead = 2;          // producer lead (steps)
 constexpr int kPre = 4;           // precomputed-step slots (>= kLead + 2)
+constexpr uint32_t kSpinLimit = 1u << 24;   // polls before a wait gives up
 
 template <int K>
 struct PreStep {
@@ -638,6 +648,44 @@ struct PreStep {
     float tp;
     int ok;
 };
+
+// Stores v at `local` in the CTA of cluster rank r (CL > 1) or locally.
+template <int CL>
+__device__ __forceinline__ void store_rank(uint32_t* local, uint32_t r, uint32_t v)
+{
+    if constexpr (CL == 1) {
+        *reinterpret_cast<volatile uint32_t*>(local) = v;
+    } else {
+        const uint32_t a = (uint32_t)__cvta_generic_to_shared(local);
+        uint32_t ra;
+        asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(a), "r"(r));
+        asm volatile("st.relaxed.cluster.shared::cluster.u32 [%0], %1;" ::"r"(ra), "r"(v) : "memory");
+    }
+}
+
+// One refill exchange of the segment (called by the 32 lanes of every
+// consumer warp). bits: this stream's flags (bit 0 refill, bit 1 escape).
+// Returns, in lane q, stream q's flags for exchange e.
+template <int CL>
+__device__ __forceinline__ uint32_t exchange(uint32_t* xflag, uint32_t* abort_flag, uint32_t e, int ws, int lane,
+                                             uint32_t bits, int32_t* err)
+{
+    uint32_t* slot = xflag + (e & 1u) * 32;
+    const uint32_t tag = e & 0x3fffffffu;
+    if (lane < CL) store_rank<CL>(slot + ws, (uint32_t)lane, (tag << 2) | bits);
+    const volatile uint32_t* vs = slot;
+    const volatile uint32_t* va = abort_flag;
+    for (uint32_t spin = 0;; ++spin) {
+        const uint32_t f = vs[lane];
+        if (__all_sync(kFull, (f >> 2) == tag)) return f & 3u;
+        if (__any_sync(kFull, *va != 0u)) return 0u;
+        if (spin >= kSpinLimit) {
+            if (lane == 0) set_error(err, kErrCorrupt);
+            if (lane < CL) store_rank<CL>(abort_flag, (uint32_t)lane, 1u);
+            return 0u;
+        }
+    }
+}
 
 template <int K, typename T, int CL>
 __global__ void __launch_bounds__(64 * 32 / CL) fgmm_dec_ws_kernel(const T* __restrict__ params, int64_t N, int32_t S,
@@ -654,9 +702,10 @@ __global__ void __launch_bounds__(64 * 32 / CL) fgmm_dec_ws_kernel(const T* __re
     extern __shared__ __align__(16) unsigned char smem[];
     PreStep<K>* pre = reinterpret_cast<PreStep<K>*>(smem);                                  // [kPre][SPC]
     T* ring = reinterpret_cast<T*>(smem + sizeof(PreStep<K>) * kPre * SPC);               // [kRing][3K][SPC]
-    uint32_t* masks = reinterpret_cast<uint32_t*>(reinterpret_cast<unsigned char*>(ring) +
-                                                  sizeof(T) * kRing * 3 * K * SPC);     // [3][4]
-    uint16_t* wsm = reinterpret_cast<uint16_t*>(masks + 12);                                // [kWordCap]
+    uint32_t* xflag = reinterpret_cast<uint32_t*>(reinterpret_cast<unsigned char*>(ring) +
+                                                  sizeof(T) * kRing * 3 * K * SPC);     // [2][32]
+    uint32_t* abort_flag = xflag + 64;                                                      // [1] (+3 pad)
+    uint16_t* wsm = reinterpret_cast<uint16_t*>(xflag + 68);                                // [kWordCap]
 
     const int rank = CL > 1 ? (int)cluster_rank() : 0;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -700,9 +749,20 @@ __global__ void __launch_bounds__(64 * 32 / CL) fgmm_dec_ws_kernel(const T* __re
             P.tp = m.tp;
         }
     };
+    // consumer side: step u's precomputed round and mixture, from shared
+    // memory into registers
+    auto fetch = [&](int64_t u, Mix<K>& m, uint32_t& q0) {
+        const PreStep<K>& P = pre[(u % kPre) * SPC + wl];
+#pragma unroll
+        for (int k = 0; k < K; ++k) { m.w[k] = P.w[k]; m.mu[k] = P.mu[k]; m.inv[k] = P.inv[k]; }
+        m.lo = P.lo;
+        m.hi = P.hi;
+        m.tp = P.tp;
+        q0 = P.q0[lane];
+    };
 
-    // prologue: parameters of steps 0 .. kLead+1, words, round 0 of steps
-    // 0 .. kLead-1
+    // prologue: parameters of steps 0 .. kLead+1, words, exchange flags,
+    // round 0 of steps 0 .. kLead-1
     for (int p = 0; p < kLead + 2; ++p) {
         if (producer && p < T_steps)
             stage_params<K, T, SPC>(ring + (p % kRing) * 3 * K * SPC, params, N, p * (int64_t)S + nbase, ptid, PNT,
@@ -711,17 +771,22 @@ __global__ void __launch_bounds__(64 * 32 / CL) fgmm_dec_ws_kernel(const T* __re
     }
     if (staged)
         for (int64_t i = tid; i < seg_len; i += NT) wsm[i] = __ldg(words + beg + i);
-    if (tid < 12) masks[tid] = 0u;
+    if (tid < 68) xflag[tid] = 0xffffffffu;   // tags no exchange number reaches
+    if (tid == 64) xflag[64] = 0u;            // abort flag
     cp_async_wait<1>();   // steps 0 .. kLead resident
     __syncthreads();
     if (producer)
         for (int64_t u = 0; u < kLead && u < T_steps; ++u) produce(u);
-    seg_sync<CL>();
+    seg_sync<CL>();       // flags initialised in every CTA before any exchange
 
     uint32_t x = (uint32_t)wsrc[end - 64 + 2 * ws - wbase] | ((uint32_t)wsrc[end - 63 + 2 * ws - wbase] << 16);
     int64_t ptr = end - 64;
     bool bad = false;
     int decoded = 0;
+    uint32_t e = 0;       // exchange number (the same in every stream)
+    Mix<K> m;
+    uint32_t q0 = 0;
+    if (!producer && T_steps > 0) fetch(0, m, q0);
 
     for (int64_t t = 0; t < T_steps; ++t) {
         if (producer) {
@@ -731,21 +796,12 @@ __global__ void __launch_bounds__(64 * 32 / CL) fgmm_dec_ws_kernel(const T* __re
             cp_async_commit();
             if (t + kLead < T_steps) produce(t + kLead);
             cp_async_wait<1>();   // step t + kLead + 1 resident for the next iteration
-        }
-        const int64_t n = t * (int64_t)S + g * 32 + ws;
-        const bool act = !producer && n < N;
-        int32_t s = 0;
-        bool esc = false;
-        uint32_t start = 0, freq = 1;
-        if (!producer) {
-            const PreStep<K>& P = pre[(t % kPre) * SPC + wl];
-            Mix<K> m;
-#pragma unroll
-            for (int k = 0; k < K; ++k) { m.w[k] = P.w[k]; m.mu[k] = P.mu[k]; m.inv[k] = P.inv[k]; }
-            m.lo = P.lo;
-            m.hi = P.hi;
-            m.tp = P.tp;
-            const uint32_t q0 = P.q0[lane];
+        } else {
+            const int64_t n = t * (int64_t)S + g * 32 + ws;
+            const bool act = n < N;
+            int32_t s = 0;
+            bool esc = false;
+            uint32_t start = 0, freq = 1;
             const uint32_t slot = x & 0xffffu;
             const int c = __popc(__ballot_sync(kFull, act && q0 <= slot));
             const uint32_t q_last = __shfl_sync(kFull, q0, 31);
@@ -776,39 +832,17 @@ __global__ void __launch_bounds__(64 * 32 / CL) fgmm_dec_ws_kernel(const T* __re
                 x = freq * (x >> 16) + slot - start;
                 decoded += (lane == 0);
             }
-        }
-        uint32_t* mk = masks + (int)(t % 3) * 4;
-        const bool need = act && x < kL;
-        if (lane == 0 && !producer) {
-            if (need) or_all<CL>(mk, bit);
-            if (esc) or_all<CL>(mk + 1, bit);
-        }
-        seg_sync<CL>();
-        const uint32_t M = mk[0], E = mk[1];
-        if (tid < 4) masks[(int)((t + 2) % 3) * 4 + tid] = 0u;
-        const uint32_t below = bit - 1u;
-        if (M) {
-            const int cnt = __popc(M);
-            if (need) {
-                const int64_t idx = ptr - cnt + __popc(M & below);
-                uint32_t v = 0;
-                if (idx >= beg) v = wsrc[idx - wbase];
-                else bad = true;
-                x = (x << 16) | v;
-            }
-            ptr -= cnt;
-        }
-        if (E) {   // uniform over the segment's CTAs (producers take part in the barriers)
-            uint32_t hi16 = 0, lo16 = 0;
-            if (esc) { hi16 = x & 0xffffu; x >>= 16; }
-            const bool n2 = esc && x < kL;
-            if (lane == 0 && n2) or_all<CL>(mk + 2, bit);
-            seg_sync<CL>();
-            const uint32_t M2 = mk[2];
-            if (M2) {
-                const int cnt = __popc(M2);
-                if (n2) {
-                    const int64_t idx = ptr - cnt + __popc(M2 & below);
+            // step t + 1's round (produced two barriers ago) overlaps the
+            // exchange
+            if (t + 1 < T_steps) fetch(t + 1, m, q0);
+            const bool need = act && x < kL;
+            const uint32_t below = bit - 1u;
+            const uint32_t f = exchange<CL>(xflag, abort_flag, e++, ws, lane, (need ? 1u : 0u) | (esc ? 2u : 0u), err);
+            const uint32_t M = __ballot_sync(kFull, f & 1u), E = __ballot_sync(kFull, f & 2u);
+            if (M) {
+                const int cnt = __popc(M);
+                if (need) {
+                    const int64_t idx = ptr - cnt + __popc(M & below);
                     uint32_t v = 0;
                     if (idx >= beg) v = wsrc[idx - wbase];
                     else bad = true;
@@ -816,25 +850,43 @@ __global__ void __launch_bounds__(64 * 32 / CL) fgmm_dec_ws_kernel(const T* __re
                 }
                 ptr -= cnt;
             }
-            if (esc) { lo16 = x & 0xffffu; x >>= 16; }
-            const bool n3 = esc && x < kL;
-            if (lane == 0 && n3) or_all<CL>(mk + 3, bit);
-            seg_sync<CL>();
-            const uint32_t M3 = mk[3];
-            if (M3) {
-                const int cnt = __popc(M3);
-                if (n3) {
-                    const int64_t idx = ptr - cnt + __popc(M3 & below);
-                    uint32_t v = 0;
-                    if (idx >= beg) v = wsrc[idx - wbase];
-                    else bad = true;
-                    x = (x << 16) | v;
+            if (E) {   // the same in every stream of the segment
+                uint32_t hi16 = 0, lo16 = 0;
+                if (esc) { hi16 = x & 0xffffu; x >>= 16; }
+                const bool n2 = esc && x < kL;
+                const uint32_t M2 = __ballot_sync(kFull, exchange<CL>(xflag, abort_flag, e++, ws, lane, n2 ? 1u : 0u,
+                                                                      err) & 1u);
+                if (M2) {
+                    const int cnt = __popc(M2);
+                    if (n2) {
+                        const int64_t idx = ptr - cnt + __popc(M2 & below);
+                        uint32_t v = 0;
+                        if (idx >= beg) v = wsrc[idx - wbase];
+                        else bad = true;
+                        x = (x << 16) | v;
+                    }
+                    ptr -= cnt;
                 }
-                ptr -= cnt;
+                if (esc) { lo16 = x & 0xffffu; x >>= 16; }
+                const bool n3 = esc && x < kL;
+                const uint32_t M3 = __ballot_sync(kFull, exchange<CL>(xflag, abort_flag, e++, ws, lane, n3 ? 1u : 0u,
+                                                                      err) & 1u);
+                if (M3) {
+                    const int cnt = __popc(M3);
+                    if (n3) {
+                        const int64_t idx = ptr - cnt + __popc(M3 & below);
+                        uint32_t v = 0;
+                        if (idx >= beg) v = wsrc[idx - wbase];
+                        else bad = true;
+                        x = (x << 16) | v;
+                    }
+                    ptr -= cnt;
+                }
+                if (esc) s = (int32_t)((hi16 << 16) | lo16);
             }
-            if (esc) s = (int32_t)((hi16 << 16) | lo16);
+            if (act && lane == 0) out[n] = s;
         }
-        if (act && lane == 0) out[n] = s;
+        __syncthreads();   // producers' round for step t + 2 visible; slots read
     }
     cp_async_wait<0>();
     const bool fail = !producer && (bad || x != kL || ptr != beg);
@@ -852,15 +904,16 @@ __global__ void __launch_bounds__(64 * 32 / CL) fgmm_dec_ws_kernel(const T* __re
             atomicAdd(stats + 1, (unsigned long long)d);
         }
     }
-    seg_sync<CL>();
+    seg_sync<CL>();       // no CTA leaves while another may still write its flags
 }
 
 template <int K, typename T, int CL>
 cudaError_t launch_ws(const DecodeArgs& a, cudaStream_t st)
 {
     constexpr int SPC = 32 / CL;
-    const size_t smem = sizeof(PreStep<K>) * kPre * SPC + sizeof(T) * kRing * 3 * K * SPC + sizeof(uint32_t) * 12 +
+    const size_t smem = sizeof(PreStep<K>) * kPre * SPC + sizeof(T) * kRing * 3 * K * SPC + sizeof(uint32_t) * 68 +
                         sizeof(uint16_t) * kWordCap;
+    if (a.T >= ((int64_t)1 << 28)) return cudaErrorInvalidValue;   // exchange numbers stay below 2^30
     auto kern = fgmm_dec_ws_kernel<K, T, CL>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
