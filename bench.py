@@ -38,7 +38,7 @@ FP32_LANES_PER_SM = 128
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of
 # the decoder the plan names, from the ncu captures summarised under
 # profiles/; valid for each kernel as captured there (null otherwise).
-DECODE_TRAFFIC_BYTES = {"fgmm_dec_ws_kernel": 10785536}
+DECODE_TRAFFIC_BYTES = {"fgmm_dec_ws_kernel/16/4": 10791168}   # kernel / lanes / cluster
 
 
 def parse():
@@ -523,7 +523,7 @@ def run_fgmm(args):
         "roofline": {"kernel": plan["kernel"], "lanes": plan["lanes"], "cluster": plan["cluster"],
                      "bound": "alu", "achieved": achieved, "peak": alu_peak,
                      "unit": "Tops/s (FP32 lane ops)", "frac": achieved / alu_peak,
-                     "traffic": DECODE_TRAFFIC_BYTES.get(plan["kernel"]),
+                     "traffic": DECODE_TRAFFIC_BYTES.get(f'{plan["kernel"]}/{plan["lanes"]}/{plan["cluster"]}'),
                      "peak_source": f"derived: {props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
                                     f"{sm_max:.0f} MHz"},
         "clocks": clk,

@@ -288,8 +288,8 @@ fgmm_status fgmm_decode_proposal(fgmm_handle *h, const fgmm_latent *lat, const v
  * stream), 2, 4, 8, 16 or 32 (G-ary search, G lanes per stream), or 0 to
  * choose from the number of segments (default). FGMM_OPT_DECODE_CLUSTER:
  * CTAs (a thread-block cluster, one SM each) sharing one segment when G > 1:
- * 1, 2 or 4 (at most G), 8 for G = 32, or 0 for automatic. The decoded symbols do not
- * depend on either. */
+ * 1, 2 or 4 (at most G), 8 for G >= 8, or 0 for automatic. The decoded
+ * symbols do not depend on either. */
 enum { FGMM_OPT_DECODE_LANES = 1, FGMM_OPT_DECODE_CLUSTER = 2 };
 fgmm_status fgmm_set_option(fgmm_handle *h, int32_t option, int64_t value);
 
@@ -299,10 +299,13 @@ fgmm_status fgmm_set_option(fgmm_handle *h, int32_t option, int64_t value);
  * segment (cluster size), out[2] = the kernel:
  *   FGMM_DEC_LANE  one lane per stream, binary search over the window
  *                  (Sec. III-B), one warp per segment;
- *   FGMM_DEC_COOP  G = 2..16 lanes per stream, G-ary search;
+ *   FGMM_DEC_COOP  G = 2..16 lanes per stream, G-ary search (clusters of
+ *                  up to 4 CTAs for G = 2, 4; one CTA for G = 8, 16);
  *   FGMM_DEC_WIDE  32 lanes per stream, 32-point search, one CTA per segment;
- *   FGMM_DEC_WS    32 lanes per stream, producer/consumer warps, a
- *                  thread-block cluster per segment.
+ *   FGMM_DEC_WS    G = 8, 16 or 32 with a cluster of 2, 4 or 8 CTAs per
+ *                  segment: producer warps evaluate a 32-point first round
+ *                  two steps ahead, consumer warps (32 / G streams each,
+ *                  G lanes per stream) search inside the bracket.
  * The paper has no counterpart: it decodes with one thread per stream.
  * Errors: FGMM_ERR_INVALID_ARG for a NULL argument or S not a positive
  * multiple of 32. */

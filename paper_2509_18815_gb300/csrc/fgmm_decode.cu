@@ -10,13 +10,18 @@ void decode_config_auto(int64_t nseg, int num_sms, int* lanes, int* cluster)
 {
     // Enough segments to give every SM several warps: one lane per stream,
     // binary search (least work). Fewer: G lanes per stream, and a cluster of
-    // CTAs per segment when the segments leave most SMs idle.
-    // (measured on GB300: 1,024 streams -> 32 lanes x clusters of 8;
-    // 2,176 streams -> 8 lanes; 61,440 streams -> 1 lane.)
-    if (nseg >= 4 * (int64_t)num_sms) { *lanes = 1; *cluster = 1; return; }
-    if (nseg >= (int64_t)num_sms) { *lanes = 4; *cluster = 1; return; }
-    if (nseg * 4 <= (int64_t)num_sms) { *lanes = 32; *cluster = 8; return; }
-    *lanes = 8;
+    // CTAs per segment when the segments leave most SMs idle; the fewer the
+    // segments, the more lanes per stream. Measured on GB300 (152 SMs):
+    // 1-8 segments -> 32 lanes x clusters of 8; 16-32 -> 16 lanes x clusters
+    // of 4; 48-100 -> 8 lanes x clusters of 8; 152 -> 8 lanes; 200-304 ->
+    // 4 lanes; 608 -> 1 lane.
+    const int64_t sms = num_sms;
+    if (nseg >= 4 * sms) { *lanes = 1; *cluster = 1; return; }
+    if (nseg * 16 <= sms) { *lanes = 32; *cluster = 8; return; }
+    if (nseg * 4 <= sms) { *lanes = 16; *cluster = 4; return; }
+    if (nseg * 3 <= sms * 2) { *lanes = 8; *cluster = 8; return; }
+    if (nseg * 4 <= sms * 5) { *lanes = 8; *cluster = 1; return; }
+    *lanes = 4;
     *cluster = 1;
 }
 
@@ -31,11 +36,16 @@ void decode_resolve(int64_t nseg, int num_sms, int opt_lanes, int opt_cluster, i
     }
     if (opt_cluster > 0) CL = opt_cluster;
     if (G < 2) CL = 1;
-    if (G < 32 && CL > 4) CL = 4;   // the G-ary kernel takes clusters of up to 4
+    if (G < 8 && CL > 4) CL = 4;   // the G-ary kernel takes clusters of up to 4
     if (CL > G) CL = G;
     *lanes = G;
     *cluster = CL;
-    *kernel = G == 1 ? FGMM_DEC_LANE : (G < 32 ? FGMM_DEC_COOP : (CL == 1 ? FGMM_DEC_WIDE : FGMM_DEC_WS));
+    // G >= 8 with a cluster: the warp-specialised kernel (32 / G streams per
+    // consumer warp); G = 32 in one CTA: the wide kernel
+    if (G == 1) *kernel = FGMM_DEC_LANE;
+    else if (CL >= 2 && G >= 8) *kernel = FGMM_DEC_WS;
+    else if (G == 32) *kernel = FGMM_DEC_WIDE;
+    else *kernel = FGMM_DEC_COOP;
 }
 
 cudaError_t launch_decode(const DecodeArgs& a, int K, int dtype, int G, int CL, cudaStream_t st)

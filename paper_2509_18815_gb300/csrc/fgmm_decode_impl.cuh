@@ -618,325 +618,6 @@ __global__ void __launch_bounds__(32 * 32 / CL) fgmm_dec_wide_kernel(const T* __
     seg_sync<CL>();
 }
 
-// ---------------------------------------------------------------------------
-// Warp-specialised wide decoder. Per stream two warps: a producer that,
-// kLead steps ahead, prepares the stream's mixture (reciprocal scales,
-// window) and evaluates its 32-point round 0 into shared memory, and a
-// consumer that runs only the state-dependent chain of each step: one
-// ballot over the precomputed round 0, one round of CDF evaluations inside
-// the bracket, the inverse rANS step and the segment's refill exchange.
-//
-// The exchange is a flag per stream, not a cluster barrier: each consumer
-// writes (exchange number, refill bit, escape bit) into a double-buffered
-// slot of every CTA of the cluster, then polls its own CTA's copies until
-// all 32 streams of the segment have posted that exchange. A slot is reused
-// two exchanges later, by which time every stream has read it (a stream
-// posts exchange e + 1 only after its wait for exchange e has ended).
-// Producers and consumers of one CTA meet at a CTA barrier once per step.
-// Every wait is bounded: a consumer that gives up records an error and
-// raises an abort flag in all CTAs, after which no wait blocks.
-// ---------------------------------------------------------------------------
-constexpr int kLead = 2;          // producer lead (steps)
-constexpr int kPre = 4;           // precomputed-step slots (>= kLead + 2)
-constexpr uint32_t kSpinLimit = 1u << 24;   // polls before a wait gives up
-
-template <int K>
-struct PreStep {
-    uint32_t q0[32];              // Q at the 32 round-0 points
-    float w[K], mu[K], inv[K];
-    int lo, hi;
-    float tp;
-    int ok;
-};
-
-// Stores v at `local` in the CTA of cluster rank r (CL > 1) or locally.
-template <int CL>
-__device__ __forceinline__ void store_rank(uint32_t* local, uint32_t r, uint32_t v)
-{
-    if constexpr (CL == 1) {
-        *reinterpret_cast<volatile uint32_t*>(local) = v;
-    } else {
-        const uint32_t a = (uint32_t)__cvta_generic_to_shared(local);
-        uint32_t ra;
-        asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(a), "r"(r));
-        asm volatile("st.relaxed.cluster.shared::cluster.u32 [%0], %1;" ::"r"(ra), "r"(v) : "memory");
-    }
-}
-
-// One refill exchange of the segment (called by the 32 lanes of every
-// consumer warp). bits: this stream's flags (bit 0 refill, bit 1 escape).
-// Returns, in lane q, stream q's flags for exchange e.
-template <int CL>
-__device__ __forceinline__ uint32_t exchange(uint32_t* xflag, uint32_t* abort_flag, uint32_t e, int ws, int lane,
-                                             uint32_t bits, int32_t* err)
-{
-    uint32_t* slot = xflag + (e & 1u) * 32;
-    const uint32_t tag = e & 0x3fffffffu;
-    if (lane < CL) store_rank<CL>(slot + ws, (uint32_t)lane, (tag << 2) | bits);
-    const volatile uint32_t* vs = slot;
-    const volatile uint32_t* va = abort_flag;
-    for (uint32_t spin = 0;; ++spin) {
-        const uint32_t f = vs[lane];
-        if (__all_sync(kFull, (f >> 2) == tag)) return f & 3u;
-        if (__any_sync(kFull, *va != 0u)) return 0u;
-        if (spin >= kSpinLimit) {
-            if (lane == 0) set_error(err, kErrCorrupt);
-            if (lane < CL) store_rank<CL>(abort_flag, (uint32_t)lane, 1u);
-            return 0u;
-        }
-    }
-}
-
-template <int K, typename T, int CL>
-__global__ void __launch_bounds__(64 * 32 / CL) fgmm_dec_ws_kernel(const T* __restrict__ params, int64_t N, int32_t S,
-                                                                   int64_t T_steps,
-                                                                   const uint16_t* __restrict__ words,
-                                                                   int64_t n_words,
-                                                                   const int64_t* __restrict__ offsets,
-                                                                   int32_t* __restrict__ out, int32_t* err,
-                                                                   unsigned long long* stats, int mode)
-{
-    constexpr int SPC = 32 / CL;              // streams per CTA
-    constexpr int NT = 64 * SPC;              // SPC consumer warps + SPC producer warps
-    constexpr int PNT = 32 * SPC;             // producer threads
-    extern __shared__ __align__(16) unsigned char smem[];
-    PreStep<K>* pre = reinterpret_cast<PreStep<K>*>(smem);                                  // [kPre][SPC]
-    T* ring = reinterpret_cast<T*>(smem + sizeof(PreStep<K>) * kPre * SPC);               // [kRing][3K][SPC]
-    uint32_t* xflag = reinterpret_cast<uint32_t*>(reinterpret_cast<unsigned char*>(ring) +
-                                                  sizeof(T) * kRing * 3 * K * SPC);     // [2][32]
-    uint32_t* abort_flag = xflag + 64;                                                      // [1] (+3 pad)
-    uint16_t* wsm = reinterpret_cast<uint16_t*>(xflag + 68);                                // [kWordCap]
-
-    const int rank = CL > 1 ? (int)cluster_rank() : 0;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const bool producer = warp >= SPC;
-    const int wl = producer ? warp - SPC : warp;      // stream slot in this CTA
-    const int ws = rank * SPC + wl;                   // stream within the segment
-    const uint32_t bit = 1u << ws;
-    const int ptid = tid - PNT;                       // producer thread index
-    const int64_t g = blockIdx.x / CL;
-    const int64_t beg = offsets[g], end = offsets[g + 1];
-    if (!(beg >= 0 && end <= n_words && end - beg >= 64)) {
-        if (tid == 0 && rank == 0) set_error(err, kErrCorrupt);
-        return;
-    }
-    const int64_t seg_len = end - beg;
-    const bool staged = seg_len <= kWordCap;
-    const uint16_t* wsrc = staged ? wsm : words;
-    const int64_t wbase = staged ? beg : 0;
-    const int64_t nbase = g * 32 + rank * SPC;
-
-    // producer side: prepare step u of this warp's stream into pre[u % kPre]
-    bool badp = false;
-    int probes = 0;
-    auto produce = [&](int64_t u) {
-        const T* slot_p = ring + (u % kRing) * 3 * K * SPC;
-        RawParams<K> r;
-#pragma unroll
-        for (int i = 0; i < 3 * K; ++i) r.v[i] = smem_param<T>(slot_p + i * SPC + wl);
-        Mix<K> m;
-        const bool ok = mix_from_params<K>(r, m);
-        const bool act = u * (int64_t)S + g * 32 + ws < N;
-        badp |= act && !ok;
-        PreStep<K>& P = pre[(u % kPre) * SPC + wl];
-        P.q0[lane] = q_at<K>(m, wide_point<K>(m, lane));
-        probes += act;
-        if (lane == 0) {
-#pragma unroll
-            for (int k = 0; k < K; ++k) { P.w[k] = m.w[k]; P.mu[k] = m.mu[k]; P.inv[k] = m.inv[k]; }
-            P.lo = m.lo;
-            P.hi = m.hi;
-            P.tp = m.tp;
-        }
-    };
-    // consumer side: step u's precomputed round and mixture, from shared
-    // memory into registers
-    auto fetch = [&](int64_t u, Mix<K>& m, uint32_t& q0) {
-        const PreStep<K>& P = pre[(u % kPre) * SPC + wl];
-#pragma unroll
-        for (int k = 0; k < K; ++k) { m.w[k] = P.w[k]; m.mu[k] = P.mu[k]; m.inv[k] = P.inv[k]; }
-        m.lo = P.lo;
-        m.hi = P.hi;
-        m.tp = P.tp;
-        q0 = P.q0[lane];
-    };
-
-    // prologue: parameters of steps 0 .. kLead+1, words, exchange flags,
-    // round 0 of steps 0 .. kLead-1
-    for (int p = 0; p < kLead + 2; ++p) {
-        if (producer && p < T_steps)
-            stage_params<K, T, SPC>(ring + (p % kRing) * 3 * K * SPC, params, N, p * (int64_t)S + nbase, ptid, PNT,
-                                    mode);
-        cp_async_commit();
-    }
-    if (staged)
-        for (int64_t i = tid; i < seg_len; i += NT) wsm[i] = __ldg(words + beg + i);
-    if (tid < 68) xflag[tid] = 0xffffffffu;   // tags no exchange number reaches
-    if (tid == 64) xflag[64] = 0u;            // abort flag
-    cp_async_wait<1>();   // steps 0 .. kLead resident
-    __syncthreads();
-    if (producer)
-        for (int64_t u = 0; u < kLead && u < T_steps; ++u) produce(u);
-    seg_sync<CL>();       // flags initialised in every CTA before any exchange
-
-    uint32_t x = (uint32_t)wsrc[end - 64 + 2 * ws - wbase] | ((uint32_t)wsrc[end - 63 + 2 * ws - wbase] << 16);
-    int64_t ptr = end - 64;
-    bool bad = false;
-    int decoded = 0;
-    uint32_t e = 0;       // exchange number (the same in every stream)
-    Mix<K> m;
-    uint32_t q0 = 0;
-    if (!producer && T_steps > 0) fetch(0, m, q0);
-
-    for (int64_t t = 0; t < T_steps; ++t) {
-        if (producer) {
-            if (t + kLead + 2 < T_steps)
-                stage_params<K, T, SPC>(ring + ((t + kLead + 2) % kRing) * 3 * K * SPC, params, N,
-                                        (t + kLead + 2) * (int64_t)S + nbase, ptid, PNT, mode);
-            cp_async_commit();
-            if (t + kLead < T_steps) produce(t + kLead);
-            cp_async_wait<1>();   // step t + kLead + 1 resident for the next iteration
-        } else {
-            const int64_t n = t * (int64_t)S + g * 32 + ws;
-            const bool act = n < N;
-            int32_t s = 0;
-            bool esc = false;
-            uint32_t start = 0, freq = 1;
-            const uint32_t slot = x & 0xffffu;
-            const int c = __popc(__ballot_sync(kFull, act && q0 <= slot));
-            const uint32_t q_last = __shfl_sync(kFull, q0, 31);
-            if (act && c == 32) {
-                esc = true;
-                start = q_last;
-                freq = kM - start;
-            }
-            const int W = m.hi - m.lo + 1;
-            const int a = c > 0 ? m.lo + (c * W + 31) / 32 : m.lo;
-            const int b = m.lo + ((min(c, 31) + 1) * W + 31) / 32;
-            const uint32_t qc1 = __shfl_sync(kFull, q0, c > 0 ? c - 1 : 0);
-            const uint32_t qa0 = c > 0 ? qc1 : 0u;
-            const uint32_t qb0 = __shfl_sync(kFull, q0, c < 32 ? c : 31);
-            const int L = b - a;
-            const bool valid = act && !esc && lane < L - 1;
-            const uint32_t q1 = q_at<K>(m, min(a + 1 + lane, m.hi + 1));
-            probes += valid;
-            const int c1 = __popc(__ballot_sync(kFull, valid && q1 <= slot));
-            const uint32_t q1a = __shfl_sync(kFull, q1, c1 > 0 ? c1 - 1 : 0);
-            const uint32_t q1b = __shfl_sync(kFull, q1, c1 < 31 ? c1 : 31);
-            if (act && !esc) {
-                s = a + c1;
-                start = c1 > 0 ? q1a : qa0;
-                freq = (c1 < L - 1 ? q1b : qb0) - start;
-            }
-            if (act) {
-                x = freq * (x >> 16) + slot - start;
-                decoded += (lane == 0);
-            }
-            // step t + 1's round (produced two barriers ago) overlaps the
-            // exchange
-            if (t + 1 < T_steps) fetch(t + 1, m, q0);
-            const bool need = act && x < kL;
-            const uint32_t below = bit - 1u;
-            const uint32_t f = exchange<CL>(xflag, abort_flag, e++, ws, lane, (need ? 1u : 0u) | (esc ? 2u : 0u), err);
-            const uint32_t M = __ballot_sync(kFull, f & 1u), E = __ballot_sync(kFull, f & 2u);
-            if (M) {
-                const int cnt = __popc(M);
-                if (need) {
-                    const int64_t idx = ptr - cnt + __popc(M & below);
-                    uint32_t v = 0;
-                    if (idx >= beg) v = wsrc[idx - wbase];
-                    else bad = true;
-                    x = (x << 16) | v;
-                }
-                ptr -= cnt;
-            }
-            if (E) {   // the same in every stream of the segment
-                uint32_t hi16 = 0, lo16 = 0;
-                if (esc) { hi16 = x & 0xffffu; x >>= 16; }
-                const bool n2 = esc && x < kL;
-                const uint32_t M2 = __ballot_sync(kFull, exchange<CL>(xflag, abort_flag, e++, ws, lane, n2 ? 1u : 0u,
-                                                                      err) & 1u);
-                if (M2) {
-                    const int cnt = __popc(M2);
-                    if (n2) {
-                        const int64_t idx = ptr - cnt + __popc(M2 & below);
-                        uint32_t v = 0;
-                        if (idx >= beg) v = wsrc[idx - wbase];
-                        else bad = true;
-                        x = (x << 16) | v;
-                    }
-                    ptr -= cnt;
-                }
-                if (esc) { lo16 = x & 0xffffu; x >>= 16; }
-                const bool n3 = esc && x < kL;
-                const uint32_t M3 = __ballot_sync(kFull, exchange<CL>(xflag, abort_flag, e++, ws, lane, n3 ? 1u : 0u,
-                                                                      err) & 1u);
-                if (M3) {
-                    const int cnt = __popc(M3);
-                    if (n3) {
-                        const int64_t idx = ptr - cnt + __popc(M3 & below);
-                        uint32_t v = 0;
-                        if (idx >= beg) v = wsrc[idx - wbase];
-                        else bad = true;
-                        x = (x << 16) | v;
-                    }
-                    ptr -= cnt;
-                }
-                if (esc) s = (int32_t)((hi16 << 16) | lo16);
-            }
-            if (act && lane == 0) out[n] = s;
-        }
-        __syncthreads();   // producers' round for step t + 2 visible; slots read
-    }
-    cp_async_wait<0>();
-    const bool fail = !producer && (bad || x != kL || ptr != beg);
-    if (__syncthreads_or(fail) && tid == 0) set_error(err, kErrCorrupt);
-    if (__syncthreads_or(badp) && tid == 0) set_error(err, kErrBadParams);
-    if (stats) {
-        int p = probes, d = decoded;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            p += __shfl_xor_sync(kFull, p, o);
-            d += __shfl_xor_sync(kFull, d, o);
-        }
-        if (lane == 0) {
-            atomicAdd(stats, (unsigned long long)p);
-            atomicAdd(stats + 1, (unsigned long long)d);
-        }
-    }
-    seg_sync<CL>();       // no CTA leaves while another may still write its flags
-}
-
-template <int K, typename T, int CL>
-cudaError_t launch_ws(const DecodeArgs& a, cudaStream_t st)
-{
-    constexpr int SPC = 32 / CL;
-    const size_t smem = sizeof(PreStep<K>) * kPre * SPC + sizeof(T) * kRing * 3 * K * SPC + sizeof(uint32_t) * 68 +
-                        sizeof(uint16_t) * kWordCap;
-    if (a.T >= ((int64_t)1 << 28)) return cudaErrorInvalidValue;   // exchange numbers stay below 2^30
-    auto kern = fgmm_dec_ws_kernel<K, T, CL>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    const uintptr_t base = reinterpret_cast<uintptr_t>(a.params);
-    int mode = 0;
-    if (base % 16 == 0 && (a.N * (int64_t)sizeof(T)) % 16 == 0 && SPC * sizeof(T) >= 16) mode = 2;
-    else if (base % 4 == 0 && (a.N * (int64_t)sizeof(T)) % 4 == 0 && SPC * sizeof(T) >= 4) mode = 1;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)(a.nseg * CL));
-    cfg.blockDim = dim3(64 * SPC);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = CL;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = CL > 1 ? 1 : 0;
-    return cudaLaunchKernelEx(&cfg, kern, static_cast<const T*>(a.params), a.N, a.S, a.T, a.words, a.n_words,
-                              a.offsets, a.out, a.err, a.stats, mode);
-}
-
 template <int K, typename T, int CL>
 cudaError_t launch_wide(const DecodeArgs& a, cudaStream_t st)
 {
@@ -965,17 +646,21 @@ cudaError_t launch_wide(const DecodeArgs& a, cudaStream_t st)
                               a.offsets, a.out, a.err, a.stats, mode);
 }
 
+// Warp-specialised decoder (fgmm_decode_ws.cuh), compiled in its own units.
+template <typename T>
+cudaError_t launch_ws_any(const DecodeArgs& a, int K, int CL, int SPW, cudaStream_t st)
+{
+    if constexpr (sizeof(T) == 2) return launch_ws_bf16(a, K, CL, SPW, st);
+    else return launch_ws_f32(a, K, CL, SPW, st);
+}
+
 template <int K, typename T>
 cudaError_t launch_wide_cl(const DecodeArgs& a, int CL, cudaStream_t st)
 {
-    // warp-specialised when the CTA has room for a producer warp per stream
-    // (CL >= 2: at most 1024 threads); CL = 1 keeps one warp per stream
-    switch (CL) {
-    case 8: return launch_ws<K, T, 8>(a, st);
-    case 4: return launch_ws<K, T, 4>(a, st);
-    case 2: return launch_ws<K, T, 2>(a, st);
-    default: return launch_wide<K, T, 1>(a, st);
-    }
+    // warp-specialised with a cluster per segment; CL = 1 keeps one warp per
+    // stream in one CTA
+    if (CL >= 2) return launch_ws_any<T>(a, K, CL, 1, st);
+    return launch_wide<K, T, 1>(a, st);
 }
 
 template <int K, typename T, int G, int CL>
@@ -1026,8 +711,8 @@ cudaError_t launch_k(const DecodeArgs& a, int G, int CL, cudaStream_t st)
     switch (G) {
     case 2: return launch_coop_cl<K, T, 2>(a, CL, st);
     case 4: return launch_coop_cl<K, T, 4>(a, CL, st);
-    case 8: return launch_coop_cl<K, T, 8>(a, CL, st);
-    case 16: return launch_coop_cl<K, T, 16>(a, CL, st);
+    case 8: return CL >= 2 ? launch_ws_any<T>(a, K, CL, 4, st) : launch_coop_cl<K, T, 8>(a, 1, st);
+    case 16: return CL >= 2 ? launch_ws_any<T>(a, K, CL, 2, st) : launch_coop_cl<K, T, 16>(a, 1, st);
     case 32: return launch_wide_cl<K, T>(a, CL, st);
     default: {
         const int threads = 32;   // one warp (segment) per block: segments spread over all SMs

@@ -1,0 +1,406 @@
+// fgmm_decode_ws.cuh -- warp-specialised decoder (included by the fp32 and
+// bf16 instantiation units fgmm_decode_ws.cu and fgmm_decode_ws_bf16.cu).
+//
+// Binary search over the on-the-fly quantised CDF (Sec. III-A) split into a
+// state-independent part and a state-dependent chain. Per stream, a producer
+// warp prepares, kLead steps ahead, the stream's mixture (reciprocal scales,
+// window) and evaluates Q at 32 points spread over the window (round 0).
+// Consumer warps run the chain of each step: a count of the round-0 values
+// at or below the slot brackets the symbol between two round-0 points, the
+// points inside the bracket (at most ceil(W/32) - 1) are evaluated in one
+// round, then the inverse rANS step (Eq. 3) and the segment's refill
+// exchange. A consumer warp serves SPW streams with 32/SPW lanes each (one
+// bracket round when the bracket interior fits the lanes, more otherwise).
+//
+// The exchange is a flag per stream, not a barrier: each stream writes
+// (exchange number, refill bit, escape bit) into a double-buffered slot of
+// every CTA of the cluster, then polls its own CTA's copies until all 32
+// streams of the segment have posted that exchange. A slot is reused two
+// exchanges later, by which time every stream has read it (a stream posts
+// exchange e + 1 only after its wait for exchange e has ended). Producers
+// and consumers of one CTA meet at a CTA barrier once per step. Every wait
+// is bounded: a consumer that gives up records an error and raises an abort
+// flag in all CTAs, after which no wait blocks.
+#pragma once
+
+#include "fgmm_decode_impl.cuh"
+
+namespace {
+
+constexpr int kLead = 2;                     // producer lead (steps)
+constexpr int kPre = 4;                      // precomputed-step slots (>= kLead + 2)
+constexpr uint32_t kSpinLimit = 1u << 24;    // polls before a wait gives up
+
+template <int K>
+struct __align__(16) PreStep {
+    uint32_t q0[32];              // Q at the 32 round-0 points
+    float w[K], mu[K], inv[K];
+    int lo, hi;
+    float tp;
+};
+
+// Stores v at `local` in the CTA of cluster rank r.
+__device__ __forceinline__ void store_rank(uint32_t* local, uint32_t r, uint32_t v)
+{
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(local);
+    uint32_t ra;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(a), "r"(r));
+    asm volatile("st.relaxed.cluster.shared::cluster.u32 [%0], %1;" ::"r"(ra), "r"(v) : "memory");
+}
+
+// One refill exchange of the segment, called by every lane of every
+// consumer warp. Lane j (< CL) of the group of stream ws posts that stream's
+// flags (bit 0 refill, bit 1 escape) to CTA j. Returns, in lane q, stream
+// q's flags for exchange e.
+template <int CL>
+__device__ __forceinline__ uint32_t exchange(uint32_t* xflag, uint32_t* abort_flag, uint32_t e, int ws, int j,
+                                             int lane, uint32_t bits, int32_t* err)
+{
+    uint32_t* slot = xflag + (e & 1u) * 32;
+    const uint32_t tag = e & 0x3fffffffu;
+    if (j < CL) store_rank(slot + ws, (uint32_t)j, (tag << 2) | bits);
+    const volatile uint32_t* vs = slot;
+    const volatile uint32_t* va = abort_flag;
+    for (uint32_t spin = 0;; ++spin) {
+        const uint32_t f = vs[lane];
+        if (__all_sync(kFull, (f >> 2) == tag)) return f & 3u;
+        if (__any_sync(kFull, *va != 0u)) return 0u;
+        if (spin >= kSpinLimit) {
+            if (lane == 0) set_error(err, kErrCorrupt);
+            if (lane < CL) store_rank(abort_flag, (uint32_t)lane, 1u);
+            return 0u;
+        }
+    }
+}
+
+// Refill of one sub-step: M holds the segment's refill bits (stream q at
+// bit q); streams read in rank order from the words just below ptr.
+__device__ __forceinline__ void ws_refill(uint32_t& x, bool need, uint32_t M, uint32_t below,
+                                          const uint16_t* wsrc, int64_t wbase, int64_t& ptr, int64_t beg, bool& bad)
+{
+    if (M) {
+        const int cnt = __popc(M);
+        if (need) {
+            const int64_t idx = ptr - cnt + __popc(M & below);
+            uint32_t v = 0;
+            if (idx >= beg) v = wsrc[idx - wbase];
+            else bad = true;
+            x = (x << 16) | v;
+        }
+        ptr -= cnt;
+    }
+}
+
+template <int K, typename T, int CL, int SPW>
+__global__ void __launch_bounds__(32 * (32 / CL / SPW + 32 / CL))
+    fgmm_dec_ws_kernel(const T* __restrict__ params, int64_t N, int32_t S, int64_t T_steps,
+                       const uint16_t* __restrict__ words, int64_t n_words, const int64_t* __restrict__ offsets,
+                       int32_t* __restrict__ out, int32_t* err, unsigned long long* stats, int mode)
+{
+    constexpr int SPC = 32 / CL;              // streams per CTA
+    constexpr int LPS = 32 / SPW;             // consumer lanes per stream
+    constexpr int VPL = SPW;                  // round-0 values per consumer lane
+    constexpr int CW = SPC / SPW;             // consumer warps
+    constexpr int NT = 32 * (CW + SPC);       // consumer warps + one producer warp per stream
+    constexpr int PNT = 32 * SPC;             // producer threads
+    static_assert(SPC % SPW == 0 && LPS >= CL, "a consumer warp's streams lie in one CTA");
+    extern __shared__ __align__(16) unsigned char smem[];
+    PreStep<K>* pre = reinterpret_cast<PreStep<K>*>(smem);                                  // [kPre][SPC]
+    T* ring = reinterpret_cast<T*>(smem + sizeof(PreStep<K>) * kPre * SPC);               // [kRing][3K][SPC]
+    uint32_t* xflag = reinterpret_cast<uint32_t*>(reinterpret_cast<unsigned char*>(ring) +
+                                                  sizeof(T) * kRing * 3 * K * SPC);     // [2][32]
+    uint32_t* abort_flag = xflag + 64;                                                      // [1] (+3 pad)
+    uint16_t* wsm = reinterpret_cast<uint16_t*>(xflag + 68);                                // [kWordCap]
+
+    const int rank = (int)cluster_rank();
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const bool producer = warp >= CW;
+    const int grp = lane / LPS, j = lane % LPS;       // consumer: stream group, lane in group
+    const int wl = producer ? warp - CW : warp * SPW + grp;   // stream slot in this CTA
+    const int ws = rank * SPC + wl;                   // stream within the segment
+    const uint32_t bit = 1u << ws;
+    const int gbase = grp * LPS;
+    const uint32_t gmask = LPS == 32 ? kFull : (((1u << LPS) - 1u) << gbase);
+    const int ptid = tid - 32 * CW;                   // producer thread index
+    const int64_t g = blockIdx.x / CL;
+    const int64_t beg = offsets[g], end = offsets[g + 1];
+    if (!(beg >= 0 && end <= n_words && end - beg >= 64)) {
+        if (tid == 0 && rank == 0) set_error(err, kErrCorrupt);
+        return;
+    }
+    const int64_t seg_len = end - beg;
+    const bool staged = seg_len <= kWordCap;
+    const uint16_t* wsrc = staged ? wsm : words;
+    const int64_t wbase = staged ? beg : 0;
+    const int64_t nbase = g * 32 + rank * SPC;
+
+    // producer: prepare step u of this warp's stream into pre[u % kPre]
+    bool badp = false;
+    int probes = 0;
+    auto produce = [&](int64_t u) {
+        const T* slot_p = ring + (u % kRing) * 3 * K * SPC;
+        RawParams<K> r;
+#pragma unroll
+        for (int i = 0; i < 3 * K; ++i) r.v[i] = smem_param<T>(slot_p + i * SPC + wl);
+        Mix<K> m;
+        const bool ok = mix_from_params<K>(r, m);
+        const bool act = u * (int64_t)S + g * 32 + ws < N;
+        badp |= act && !ok;
+        PreStep<K>& P = pre[(u % kPre) * SPC + wl];
+        P.q0[lane] = q_at<K>(m, wide_point<K>(m, lane));
+        probes += act;
+        if (lane == 0) {
+#pragma unroll
+            for (int k = 0; k < K; ++k) { P.w[k] = m.w[k]; P.mu[k] = m.mu[k]; P.inv[k] = m.inv[k]; }
+            P.lo = m.lo;
+            P.hi = m.hi;
+            P.tp = m.tp;
+        }
+    };
+    // consumer: step u's mixture and this lane's VPL round-0 values (round-0
+    // point i at lane i / VPL, element i % VPL), into registers
+    auto fetch = [&](int64_t u, Mix<K>& m, uint32_t (&q0)[VPL]) {
+        const PreStep<K>& P = pre[(u % kPre) * SPC + wl];
+#pragma unroll
+        for (int k = 0; k < K; ++k) { m.w[k] = P.w[k]; m.mu[k] = P.mu[k]; m.inv[k] = P.inv[k]; }
+        m.lo = P.lo;
+        m.hi = P.hi;
+        m.tp = P.tp;
+        if constexpr (VPL == 1) {
+            q0[0] = P.q0[j];
+        } else if constexpr (VPL == 2) {
+            const uint2 v = reinterpret_cast<const uint2*>(P.q0)[j];
+            q0[0] = v.x;
+            q0[1] = v.y;
+        } else {
+            const uint4 v = reinterpret_cast<const uint4*>(P.q0)[j];
+            q0[0] = v.x;
+            q0[1] = v.y;
+            q0[2] = v.z;
+            q0[3] = v.w;
+        }
+    };
+
+    // prologue: parameters of steps 0 .. kLead+1, words, exchange flags,
+    // round 0 of steps 0 .. kLead-1
+    for (int p = 0; p < kLead + 2; ++p) {
+        if (producer && p < T_steps)
+            stage_params<K, T, SPC>(ring + (p % kRing) * 3 * K * SPC, params, N, p * (int64_t)S + nbase, ptid, PNT,
+                                    mode);
+        cp_async_commit();
+    }
+    if (staged)
+        for (int64_t i = tid; i < seg_len; i += NT) wsm[i] = __ldg(words + beg + i);
+    if (tid < 68) xflag[tid] = tid == 64 ? 0u : 0xffffffffu;   // tags no exchange number reaches; abort flag 0
+    cp_async_wait<1>();   // steps 0 .. kLead resident
+    __syncthreads();
+    if (producer)
+        for (int64_t u = 0; u < kLead && u < T_steps; ++u) produce(u);
+    seg_sync<CL>();       // flags initialised in every CTA before any exchange
+
+    uint32_t x = (uint32_t)wsrc[end - 64 + 2 * ws - wbase] | ((uint32_t)wsrc[end - 63 + 2 * ws - wbase] << 16);
+    int64_t ptr = end - 64;
+    bool bad = false;
+    int decoded = 0;
+    uint32_t e = 0;       // exchange number (the same in every stream)
+    Mix<K> m;
+    uint32_t q0[VPL];
+#pragma unroll
+    for (int v = 0; v < VPL; ++v) q0[v] = 0;
+    if (!producer && T_steps > 0) fetch(0, m, q0);
+
+    for (int64_t t = 0; t < T_steps; ++t) {
+        if (producer) {
+            if (t + kLead + 2 < T_steps)
+                stage_params<K, T, SPC>(ring + ((t + kLead + 2) % kRing) * 3 * K * SPC, params, N,
+                                        (t + kLead + 2) * (int64_t)S + nbase, ptid, PNT, mode);
+            cp_async_commit();
+            if (t + kLead < T_steps) produce(t + kLead);
+            cp_async_wait<1>();   // step t + kLead + 1 resident for the next iteration
+        } else {
+            const int64_t n = t * (int64_t)S + g * 32 + ws;
+            const bool act = n < N;
+            int32_t s = 0;
+            bool esc = false;
+            uint32_t start = 0, freq = 1;
+            const uint32_t slot = x & 0xffffu;
+            // round 0: c = number of round-0 points with Q <= slot
+            int c = 0;
+#pragma unroll
+            for (int v = 0; v < VPL; ++v) c += __popc(__ballot_sync(kFull, act && q0[v] <= slot) & gmask);
+            uint32_t qa0, qb0;   // Q at the round-0 points that bracket the symbol
+            if constexpr (VPL == 1) {
+                const uint32_t qc1 = __shfl_sync(kFull, q0[0], c > 0 ? c - 1 : 0);
+                qa0 = c > 0 ? qc1 : 0u;
+                qb0 = __shfl_sync(kFull, q0[0], c < 32 ? c : 31);
+            } else {
+                const PreStep<K>& P = pre[(t % kPre) * SPC + wl];   // rewritten two steps later
+                qb0 = P.q0[c < 32 ? c : 31];
+                qa0 = c > 0 ? P.q0[c - 1] : 0u;
+            }
+            if (act && c == 32) {   // Q(hi+1) <= slot: escape
+                esc = true;
+                start = qa0;
+                freq = kM - start;
+            }
+            const int W = m.hi - m.lo + 1;
+            const int a = c > 0 ? m.lo + (c * W + 31) / 32 : m.lo;
+            const int b = m.lo + ((min(c, 31) + 1) * W + 31) / 32;
+            const int L = b - a;   // the symbol lies in [a, b); its L - 1 inner points are evaluated
+            if constexpr (LPS >= 16) {
+                // W <= 511, so the bracket has at most 15 inner points: one round
+                const bool valid = act && !esc && j < L - 1;
+                const uint32_t q1 = q_at<K>(m, min(a + 1 + j, m.hi + 1));
+                probes += valid;
+                const int c1 = __popc(__ballot_sync(kFull, valid && q1 <= slot) & gmask);
+                const uint32_t q1a = __shfl_sync(kFull, q1, gbase + (c1 > 0 ? c1 - 1 : 0));
+                const uint32_t q1b = __shfl_sync(kFull, q1, gbase + (c1 < LPS - 1 ? c1 : LPS - 1));
+                if (act && !esc) {
+                    s = a + c1;
+                    start = c1 > 0 ? q1a : qa0;
+                    freq = (c1 < L - 1 ? q1b : qb0) - start;
+                }
+            } else {
+                // 8 lanes per stream: rounds of 8 inner points
+                int c1 = 0;
+                uint32_t lastq = qa0, endq = qb0;
+                bool open = act && !esc && L > 1;
+                for (int base = 0; __any_sync(kFull, open); base += LPS) {
+                    const int idx = base + j;
+                    const bool valid = open && idx < L - 1;
+                    const uint32_t q1 = q_at<K>(m, min(a + 1 + idx, m.hi + 1));
+                    probes += valid;
+                    const int cnt = __popc(__ballot_sync(kFull, valid && q1 <= slot) & gmask);
+                    const uint32_t qlo = __shfl_sync(kFull, q1, gbase + (cnt > 0 ? cnt - 1 : 0));
+                    const uint32_t qhi = __shfl_sync(kFull, q1, gbase + (cnt < LPS ? cnt : LPS - 1));
+                    if (open) {
+                        c1 += cnt;
+                        if (cnt > 0) lastq = qlo;
+                        if (cnt < min(LPS, L - 1 - base)) {
+                            endq = qhi;
+                            open = false;
+                        } else if (base + LPS >= L - 1) {
+                            open = false;   // every inner point <= slot: the bracket's end bounds the symbol
+                        }
+                    }
+                }
+                if (act && !esc) {
+                    s = a + c1;
+                    start = lastq;
+                    freq = endq - start;
+                }
+            }
+            if (act) {
+                x = freq * (x >> 16) + slot - start;
+                decoded += (j == 0);
+            }
+            // step t + 1's round (produced two barriers ago) overlaps the
+            // exchange
+            if (t + 1 < T_steps) fetch(t + 1, m, q0);
+            const bool need = act && x < kL;
+            const uint32_t below = bit - 1u;
+            const uint32_t f =
+                exchange<CL>(xflag, abort_flag, e++, ws, j, lane, (need ? 1u : 0u) | (esc ? 2u : 0u), err);
+            const uint32_t M = __ballot_sync(kFull, f & 1u), E = __ballot_sync(kFull, f & 2u);
+            ws_refill(x, need, M, below, wsrc, wbase, ptr, beg, bad);
+            if (E) {   // the same in every stream of the segment
+                uint32_t hi16 = 0, lo16 = 0;
+                if (esc) { hi16 = x & 0xffffu; x >>= 16; }
+                const bool n2 = esc && x < kL;
+                const uint32_t M2 =
+                    __ballot_sync(kFull, exchange<CL>(xflag, abort_flag, e++, ws, j, lane, n2 ? 1u : 0u, err) & 1u);
+                ws_refill(x, n2, M2, below, wsrc, wbase, ptr, beg, bad);
+                if (esc) { lo16 = x & 0xffffu; x >>= 16; }
+                const bool n3 = esc && x < kL;
+                const uint32_t M3 =
+                    __ballot_sync(kFull, exchange<CL>(xflag, abort_flag, e++, ws, j, lane, n3 ? 1u : 0u, err) & 1u);
+                ws_refill(x, n3, M3, below, wsrc, wbase, ptr, beg, bad);
+                if (esc) s = (int32_t)((hi16 << 16) | lo16);
+            }
+            if (act && j == 0) out[n] = s;
+        }
+        __syncthreads();   // producers' round for step t + 2 visible; slots read
+    }
+    cp_async_wait<0>();
+    const bool fail = !producer && (bad || x != kL || ptr != beg);
+    if (__syncthreads_or(fail) && tid == 0) set_error(err, kErrCorrupt);
+    if (__syncthreads_or(badp) && tid == 0) set_error(err, kErrBadParams);
+    if (stats) {
+        int p = probes, d = decoded;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            p += __shfl_xor_sync(kFull, p, o);
+            d += __shfl_xor_sync(kFull, d, o);
+        }
+        if (lane == 0) {
+            atomicAdd(stats, (unsigned long long)p);
+            atomicAdd(stats + 1, (unsigned long long)d);
+        }
+    }
+    seg_sync<CL>();       // no CTA leaves while another may still write its flags
+}
+
+template <int K, typename T, int CL, int SPW>
+cudaError_t launch_ws(const DecodeArgs& a, cudaStream_t st)
+{
+    constexpr int SPC = 32 / CL;
+    constexpr int NT = 32 * (SPC / SPW + SPC);
+    const size_t smem = sizeof(PreStep<K>) * kPre * SPC + sizeof(T) * kRing * 3 * K * SPC + sizeof(uint32_t) * 68 +
+                        sizeof(uint16_t) * kWordCap;
+    if (a.T >= ((int64_t)1 << 28)) return cudaErrorInvalidValue;   // exchange numbers stay below 2^30
+    auto kern = fgmm_dec_ws_kernel<K, T, CL, SPW>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const uintptr_t base = reinterpret_cast<uintptr_t>(a.params);
+    int mode = 0;
+    if (base % 16 == 0 && (a.N * (int64_t)sizeof(T)) % 16 == 0 && SPC * sizeof(T) >= 16) mode = 2;
+    else if (base % 4 == 0 && (a.N * (int64_t)sizeof(T)) % 4 == 0 && SPC * sizeof(T) >= 4) mode = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(a.nseg * CL));
+    cfg.blockDim = dim3(NT);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CL;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, static_cast<const T*>(a.params), a.N, a.S, a.T, a.words, a.n_words,
+                              a.offsets, a.out, a.err, a.stats, mode);
+}
+
+template <int K, typename T, int SPW>
+cudaError_t launch_ws_cl(const DecodeArgs& a, int CL, cudaStream_t st)
+{
+    switch (CL) {
+    case 8: return launch_ws<K, T, 8, SPW>(a, st);
+    case 4: return launch_ws<K, T, 4, SPW>(a, st);
+    default: return launch_ws<K, T, 2, SPW>(a, st);
+    }
+}
+
+template <int K, typename T>
+cudaError_t launch_ws_k(const DecodeArgs& a, int CL, int SPW, cudaStream_t st)
+{
+    switch (SPW) {
+    case 4: return launch_ws_cl<K, T, 4>(a, CL, st);
+    case 2: return launch_ws_cl<K, T, 2>(a, CL, st);
+    default: return launch_ws_cl<K, T, 1>(a, CL, st);
+    }
+}
+
+template <typename T>
+cudaError_t launch_ws_t(const DecodeArgs& a, int K, int CL, int SPW, cudaStream_t st)
+{
+    if (a.nseg == 0) return cudaSuccess;
+    switch (K) {
+    case 1: return launch_ws_k<1, T>(a, CL, SPW, st);
+    case 2: return launch_ws_k<2, T>(a, CL, SPW, st);
+    case 3: return launch_ws_k<3, T>(a, CL, SPW, st);
+    default: return launch_ws_k<4, T>(a, CL, SPW, st);
+    }
+}
+
+}  // namespace

@@ -84,6 +84,10 @@ struct DecodeArgs {
     unsigned long long* stats;
 };
 void decode_config_auto(int64_t nseg, int num_sms, int* lanes, int* cluster);
+// Warp-specialised decoder for fp32 / bf16 parameters: CL CTAs per segment,
+// SPW streams per consumer warp (1, 2 or 4).
+cudaError_t launch_ws_f32(const DecodeArgs& a, int K, int CL, int SPW, cudaStream_t st);
+cudaError_t launch_ws_bf16(const DecodeArgs& a, int K, int CL, int SPW, cudaStream_t st);
 // Final decoder choice: automatic plan, then the handle's options, then the
 // limits of each kernel (clusters only with G >= 2, at most 4 below G = 32).
 void decode_resolve(int64_t nseg, int num_sms, int opt_lanes, int opt_cluster, int* lanes, int* cluster,

@@ -217,7 +217,8 @@ def _set_cluster(CL):
 
 
 @pytest.mark.parametrize("case", range(len(DECODE_CASES)))
-@pytest.mark.parametrize("G,CL", [(2, 2), (4, 4), (8, 2), (8, 4), (16, 4), (32, 1), (32, 2), (32, 4), (32, 8)])
+@pytest.mark.parametrize("G,CL", [(2, 2), (4, 4), (8, 2), (8, 4), (8, 8), (16, 2), (16, 4), (16, 8), (32, 1), (32, 2),
+                                  (32, 4), (32, 8)])
 def test_decode_clusters_give_identical_symbols(case, G, CL):
     """A segment spread over a cluster of CL CTAs (refill ranks exchanged
     through distributed shared memory) decodes the same symbols."""
@@ -249,13 +250,23 @@ def test_decode_plan_follows_segments_and_options():
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     many = 32 * 4 * sms
     assert codec.decode_plan(many) == {"lanes": 1, "cluster": 1, "kernel": "fgmm_dec_kernel"}
+    assert codec.decode_plan(32) == {"lanes": 32, "cluster": 8, "kernel": "fgmm_dec_ws_kernel"}
     few = 32 * max(1, sms // 4)
-    assert codec.decode_plan(few) == {"lanes": 32, "cluster": 8, "kernel": "fgmm_dec_ws_kernel"}
+    assert codec.decode_plan(few) == {"lanes": 16, "cluster": 4, "kernel": "fgmm_dec_ws_kernel"}
     try:
         _set_lanes(4)
         assert codec.decode_plan(few) == {"lanes": 4, "cluster": 1, "kernel": "fgmm_dec_coop_kernel"}
+        _set_lanes(32)
+        assert codec.decode_plan(few) == {"lanes": 32, "cluster": 1, "kernel": "fgmm_dec_wide_kernel"}
+        _set_lanes(4)
         _set_cluster(8)
         assert codec.decode_plan(few) == {"lanes": 4, "cluster": 4, "kernel": "fgmm_dec_coop_kernel"}
+        _set_lanes(8)
+        assert codec.decode_plan(few) == {"lanes": 8, "cluster": 8, "kernel": "fgmm_dec_ws_kernel"}
+        _set_lanes(16)
+        _set_cluster(1)
+        assert codec.decode_plan(few) == {"lanes": 16, "cluster": 1, "kernel": "fgmm_dec_coop_kernel"}
+        _set_cluster(8)
         _set_lanes(1)
         assert codec.decode_plan(few) == {"lanes": 1, "cluster": 1, "kernel": "fgmm_dec_kernel"}
         _set_lanes(32)
@@ -269,7 +280,7 @@ def test_decode_plan_follows_segments_and_options():
             codec.decode_plan(bad)
 
 
-@pytest.mark.parametrize("G,CL", [(1, 1), (8, 1), (32, 1), (8, 4), (32, 8)])
+@pytest.mark.parametrize("G,CL", [(1, 1), (8, 1), (32, 1), (8, 4), (8, 8), (16, 2), (32, 8)])
 def test_decode_lanes_report_corruption(G, CL):
     codec = _codec()
     from paper_2509_18815_gb300._abi import FGMM_ERR_CORRUPT, FgmmError
