@@ -114,6 +114,46 @@ __device__ __forceinline__ void enc_stage(uint32_t* dst, const uint32_t* __restr
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(s), "l"(src), "r"(bytes));
 }
 
+// Step values of one interval: start, freq, freq << 16 (the renormalisation
+// bound), 1/freq (correctly rounded; recip is exact for freq <= 2^16) and
+// the escape test.
+struct EncStep {
+    uint32_t st, fr, fs;
+    float rf;
+    bool esc;
+};
+
+__device__ __forceinline__ EncStep enc_step(uint32_t v, bool act)
+{
+    EncStep e;
+    e.st = v & 0xffffu;
+    e.fr = v >> 16;
+    e.fs = e.fr << 16;
+    e.rf = recip((float)(e.fr > 0u ? e.fr : 1u));
+    e.esc = act && (e.st + e.fr == kM);
+    return e;
+}
+
+// x -> C(x) for the interval of e, with the renormalisation word appended
+// in ascending lane order (the rANS step of enc_put_warp with 1/freq known).
+__device__ __forceinline__ void enc_put_pre(uint32_t& x, const EncStep& e, bool part, uint16_t* __restrict__ out,
+                                            int64_t& base, uint32_t lt)
+{
+    const bool need = part && x >= e.fs;
+    const uint32_t m = __ballot_sync(kFull, need);
+    if (need) out[base + __popc(m & lt)] = (uint16_t)(x & 0xffffu);
+    base += __popc(m);
+    const uint32_t y = need ? x >> 16 : x;
+    uint32_t q = __float2uint_rz(__fmul_rn(__uint2float_rn(y), e.rf));
+    int32_t rem = (int32_t)(y - q * e.fr);
+    if (rem < 0) { --q; rem += (int32_t)e.fr; }
+    else if (rem >= (int32_t)e.fr) { ++q; rem -= (int32_t)e.fr; }
+    if (part) x = (q << 16) + (uint32_t)rem + e.st;
+}
+
+// Software pipelined: while step k's state chain runs, step k+1's interval
+// is already in registers with its reciprocal and escape test, and step
+// k + kEncPF's interval is in flight.
 __global__ void __launch_bounds__(32) fgmm_rans_enc_kernel(const uint32_t* __restrict__ sf,
                                                            const int32_t* __restrict__ sym, int64_t N, int32_t S,
                                                            int64_t T, uint16_t* __restrict__ seg_words,
@@ -134,23 +174,25 @@ __global__ void __launch_bounds__(32) fgmm_rans_enc_kernel(const uint32_t* __res
         if (k < T) enc_stage(&ring[k % kEncRing][lane], sf, n_top - (int64_t)k * S, N);
         asm volatile("cp.async.commit_group;\n" ::);
     }
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(kEncPF - 1));   // step 0 resident
+    __syncwarp();
+    EncStep cur = enc_step(T > 0 ? ring[0][lane] : 0u, n_top < N);
     for (int64_t k = 0; k < T; ++k) {
         const int64_t n = n_top - k * S;
+        const bool act = n < N;
         if (k + kEncPF < T) enc_stage(&ring[(k + kEncPF) % kEncRing][lane], sf, n - (int64_t)kEncPF * S, N);
         asm volatile("cp.async.commit_group;\n" ::);
-        asm volatile("cp.async.wait_group %0;\n" ::"n"(kEncPF));
+        asm volatile("cp.async.wait_group %0;\n" ::"n"(kEncPF - 1));   // step k+1 resident
         __syncwarp();
-        const bool act = n < N;
-        const uint32_t v = ring[k % kEncRing][lane];
-        const uint32_t start = v & 0xffffu, freq = v >> 16;
-        const bool esc = act && (start + freq == kM);
-        if (__ballot_sync(kFull, esc)) {
-            const uint32_t raw = esc ? (uint32_t)__ldg(sym + n) : 0u;
-            enc_put_warp(x, raw & 0xffffu, 1u, esc, out, base, lt);
-            enc_put_warp(x, raw >> 16, 1u, esc, out, base, lt);
+        const EncStep nxt = enc_step(k + 1 < T ? ring[(k + 1) % kEncRing][lane] : 0u, n - S < N);
+        if (__ballot_sync(kFull, cur.esc)) {
+            const uint32_t raw = cur.esc ? (uint32_t)__ldg(sym + n) : 0u;
+            const EncStep one = enc_step(1u << 16, false);   // raw chunk: freq 1
+            enc_put_pre(x, EncStep{raw & 0xffffu, one.fr, one.fs, one.rf, false}, cur.esc, out, base, lt);
+            enc_put_pre(x, EncStep{raw >> 16, one.fr, one.fs, one.rf, false}, cur.esc, out, base, lt);
         }
-        enc_put_warp(x, start, freq, act, out, base, lt);
-        __syncwarp();   // slot k is refilled kEncRing - kEncPF steps later
+        enc_put_pre(x, cur, act, out, base, lt);
+        cur = nxt;
     }
     asm volatile("cp.async.wait_group 0;\n" ::);
     out[base + 2 * lane] = (uint16_t)(x & 0xffffu);
@@ -208,6 +250,10 @@ __global__ void __launch_bounds__(1024) fgmm_scan_kernel(const int64_t* __restri
 // ---------------------------------------------------------------------------
 // 4. Segment compaction: one warp per segment.
 // ---------------------------------------------------------------------------
+// One warp per (segment, chunk of kCompactChunk words): 16-byte loads from
+// the segment's 16-byte-aligned scratch, 2-byte stores to its offset.
+constexpr int64_t kCompactChunk = 2048;
+
 __global__ void __launch_bounds__(256) fgmm_compact_kernel(const uint16_t* __restrict__ seg_words, int64_t seg_cap,
                                                            const int64_t* __restrict__ seg_len,
                                                            const int64_t* __restrict__ offsets, int64_t nseg,
@@ -215,11 +261,24 @@ __global__ void __launch_bounds__(256) fgmm_compact_kernel(const uint16_t* __res
 {
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int lane = threadIdx.x & 31;
-    for (int64_t g = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; g < nseg; g += nwarps) {
+    const int64_t chunks = (seg_cap + kCompactChunk - 1) / kCompactChunk;
+    for (int64_t item = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; item < nseg * chunks;
+         item += nwarps) {
+        const int64_t g = item / chunks, i0 = (item % chunks) * kCompactChunk;
         const int64_t len = seg_len[g], dst = offsets[g];
-        if (dst + len > cap) continue;   // capacity error already recorded
-        const uint16_t* src = seg_words + g * seg_cap;
-        for (int64_t i = lane; i < len; i += 32) words[dst + i] = src[i];
+        if (dst + len > cap || i0 >= len) continue;   // capacity error already recorded / chunk past the end
+        const int64_t n = len - i0 < kCompactChunk ? len - i0 : kCompactChunk;
+        const uint16_t* src = seg_words + g * seg_cap + i0;
+        uint16_t* d = words + dst + i0;
+#pragma unroll 4
+        for (int64_t i = 8 * lane; i < n; i += 256) {
+            // i + 8 <= seg_cap - i0: segments hold a multiple of 8 words
+            const uint4 v = *reinterpret_cast<const uint4*>(src + i);
+            const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int e = 0; e < 8; ++e)
+                if (i + e < n) d[i + e] = (uint16_t)(w[e >> 1] >> (16 * (e & 1)));
+        }
     }
 }
 
@@ -272,6 +331,15 @@ inline int seg_threads(int64_t, int) { return 32; }
 // escape emits for two chunks and the main symbol) plus the flush block;
 // rounded to 8 words so that every segment starts 16-byte aligned.
 inline int64_t seg_cap_words(int64_t T) { return (int64_t)align_up((size_t)(3 * 32 * T + 64), 8); }
+
+// One warp per (segment, chunk) item of the compaction.
+inline void launch_compact(const uint16_t* seg, int64_t cap, const int64_t* len, const int64_t* offsets,
+                           int64_t nseg, uint16_t* words, int64_t words_cap, int sms, cudaStream_t st)
+{
+    const int64_t items = nseg * ((cap + kCompactChunk - 1) / kCompactChunk);
+    fgmm_compact_kernel<<<grid_for(items * 32, 256, sms * 8), 256, 0, st>>>(seg, cap, len, offsets, nseg, words,
+                                                                            words_cap);
+}
 
 }  // namespace
 
@@ -327,8 +395,7 @@ void encode_from_intervals(const EncodeWs& ws, const int32_t* symbols, int64_t N
     fgmm_rans_enc_kernel<<<(unsigned)((nseg * 32 + thr - 1) / thr), thr, 0, st>>>(ws.sf, symbols, N, S, T, ws.seg,
                                                                                   ws.cap, ws.len, nseg);
     fgmm_scan_kernel<<<1, 1024, 0, st>>>(ws.len, nseg, offsets, n_words_out, words_cap, err);
-    fgmm_compact_kernel<<<grid_for(nseg * 32, 256, sms * 8), 256, 0, st>>>(ws.seg, ws.cap, ws.len, offsets, nseg,
-                                                                            words, words_cap);
+    launch_compact(ws.seg, ws.cap, ws.len, offsets, nseg, words, words_cap, sms, st);
 }
 
 void launch_scan(const int64_t* len, int64_t nseg, int64_t* offsets, int64_t* total_out, int64_t cap, int32_t* err,
@@ -668,8 +735,7 @@ extern "C" fgmm_status fgmm_encode_noalloc(const fgmm_latent* lat, const int32_t
     fgmm_rans_enc_kernel<<<(unsigned)((nseg * 32 + thr - 1) / thr), thr, 0, st>>>(sf, symbols, N, S, T, seg, cap,
                                                                                   len, nseg);
     fgmm_scan_kernel<<<1, 1024, 0, st>>>(len, nseg, offsets, n_words_out, words_cap, status_out);
-    fgmm_compact_kernel<<<grid_for(nseg * 32, 256, sms * 8), 256, 0, st>>>(seg, cap, len, offsets, nseg, words,
-                                                                            words_cap);
+    launch_compact(seg, cap, len, offsets, nseg, words, words_cap, sms, st);
     e = cudaGetLastError();
     return e == cudaSuccess ? FGMM_OK : FGMM_ERR_CUDA;
 }

@@ -66,7 +66,7 @@ __device__ __forceinline__ bool mix_from_params(const RawParams<K>& r, Mix<K>& m
 // makes it exact.
 __device__ __forceinline__ uint32_t divmod_small(uint32_t x, uint32_t f, uint32_t& r)
 {
-    const float rf = __frcp_rn((float)f);
+    const float rf = recip((float)f);   // equal to __frcp_rn for f <= 2^16
     uint32_t q = __float2uint_rz(__fmul_rn(__uint2float_rn(x), rf));
     int32_t rem = (int32_t)(x - q * f);
     if (rem < 0) { --q; rem += (int32_t)f; }
