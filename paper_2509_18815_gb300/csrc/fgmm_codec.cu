@@ -104,7 +104,7 @@ __global__ void __launch_bounds__(256) fgmm_interval_kernel(const T* __restrict_
 // Intervals reach the warp through a shared-memory ring filled by cp.async
 // kEncPF steps ahead (4 bytes per lane; zero past N), so the dependent rANS
 // chain never waits on a global load.
-constexpr int kEncRing = 8, kEncPF = 6;
+constexpr int kEncRing = 8, kEncPF = 6;   // read two steps ahead: kEncPF + 2 <= kEncRing
 
 __device__ __forceinline__ void enc_stage(uint32_t* dst, const uint32_t* __restrict__ sf, int64_t n, int64_t N)
 {
@@ -115,8 +115,7 @@ __device__ __forceinline__ void enc_stage(uint32_t* dst, const uint32_t* __restr
 }
 
 // Step values of one interval: start, freq, freq << 16 (the renormalisation
-// bound), 1/freq (correctly rounded; recip is exact for freq <= 2^16) and
-// the escape test.
+// bound), 1/freq rounded toward zero and the escape test.
 struct EncStep {
     uint32_t st, fr, fs;
     float rf;
@@ -129,13 +128,17 @@ __device__ __forceinline__ EncStep enc_step(uint32_t v, bool act)
     e.st = v & 0xffffu;
     e.fr = v >> 16;
     e.fs = e.fr << 16;
-    e.rf = recip((float)(e.fr > 0u ? e.fr : 1u));
+    e.rf = __frcp_rz((float)(e.fr > 0u ? e.fr : 1u));
     e.esc = act && (e.st + e.fr == kM);
     return e;
 }
 
 // x -> C(x) for the interval of e, with the renormalisation word appended
 // in ascending lane order (the rANS step of enc_put_warp with 1/freq known).
+// y = x after renormalisation is below freq * 2^16, so q = floor(y / freq)
+// is below 2^16. Every rounding of the estimate is toward zero (y, 1/freq,
+// the product), so it is at most q and, with relative error below 3 * 2^-23,
+// above q - 1: one upward correction makes it exact.
 __device__ __forceinline__ void enc_put_pre(uint32_t& x, const EncStep& e, bool part, uint16_t* __restrict__ out,
                                             int64_t& base, uint32_t lt)
 {
@@ -144,16 +147,15 @@ __device__ __forceinline__ void enc_put_pre(uint32_t& x, const EncStep& e, bool 
     if (need) out[base + __popc(m & lt)] = (uint16_t)(x & 0xffffu);
     base += __popc(m);
     const uint32_t y = need ? x >> 16 : x;
-    uint32_t q = __float2uint_rz(__fmul_rn(__uint2float_rn(y), e.rf));
-    int32_t rem = (int32_t)(y - q * e.fr);
-    if (rem < 0) { --q; rem += (int32_t)e.fr; }
-    else if (rem >= (int32_t)e.fr) { ++q; rem -= (int32_t)e.fr; }
-    if (part) x = (q << 16) + (uint32_t)rem + e.st;
+    uint32_t q = __float2uint_rz(__fmul_rz(__uint2float_rz(y), e.rf));
+    uint32_t rem = y - q * e.fr;
+    if (rem >= e.fr) { ++q; rem -= e.fr; }
+    if (part) x = (q << 16) + rem + e.st;
 }
 
 // Software pipelined: while step k's state chain runs, step k+1's interval
-// is already in registers with its reciprocal and escape test, and step
-// k + kEncPF's interval is in flight.
+// is already in registers with its reciprocal and escape vote, step k+2's
+// interval is read from the ring and step k + kEncPF's is in flight.
 __global__ void __launch_bounds__(32) fgmm_rans_enc_kernel(const uint32_t* __restrict__ sf,
                                                            const int32_t* __restrict__ sym, int64_t N, int32_t S,
                                                            int64_t T, uint16_t* __restrict__ seg_words,
@@ -174,18 +176,23 @@ __global__ void __launch_bounds__(32) fgmm_rans_enc_kernel(const uint32_t* __res
         if (k < T) enc_stage(&ring[k % kEncRing][lane], sf, n_top - (int64_t)k * S, N);
         asm volatile("cp.async.commit_group;\n" ::);
     }
-    asm volatile("cp.async.wait_group %0;\n" ::"n"(kEncPF - 1));   // step 0 resident
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(kEncPF - 2));   // steps 0 and 1 resident
     __syncwarp();
     EncStep cur = enc_step(T > 0 ? ring[0][lane] : 0u, n_top < N);
+    bool cur_any = __ballot_sync(kFull, cur.esc) != 0u;
+    uint32_t v1 = T > 1 ? ring[1][lane] : 0u;
+#pragma unroll 2
     for (int64_t k = 0; k < T; ++k) {
         const int64_t n = n_top - k * S;
         const bool act = n < N;
         if (k + kEncPF < T) enc_stage(&ring[(k + kEncPF) % kEncRing][lane], sf, n - (int64_t)kEncPF * S, N);
         asm volatile("cp.async.commit_group;\n" ::);
-        asm volatile("cp.async.wait_group %0;\n" ::"n"(kEncPF - 1));   // step k+1 resident
+        asm volatile("cp.async.wait_group %0;\n" ::"n"(kEncPF - 2));   // step k+2 resident
         __syncwarp();
-        const EncStep nxt = enc_step(k + 1 < T ? ring[(k + 1) % kEncRing][lane] : 0u, n - S < N);
-        if (__ballot_sync(kFull, cur.esc)) {
+        const uint32_t v2 = k + 2 < T ? ring[(k + 2) % kEncRing][lane] : 0u;
+        const EncStep nxt = enc_step(v1, n - S < N);
+        const bool nxt_any = __ballot_sync(kFull, nxt.esc) != 0u;
+        if (cur_any) {
             const uint32_t raw = cur.esc ? (uint32_t)__ldg(sym + n) : 0u;
             const EncStep one = enc_step(1u << 16, false);   // raw chunk: freq 1
             enc_put_pre(x, EncStep{raw & 0xffffu, one.fr, one.fs, one.rf, false}, cur.esc, out, base, lt);
@@ -193,6 +200,8 @@ __global__ void __launch_bounds__(32) fgmm_rans_enc_kernel(const uint32_t* __res
         }
         enc_put_pre(x, cur, act, out, base, lt);
         cur = nxt;
+        cur_any = nxt_any;
+        v1 = v2;
     }
     asm volatile("cp.async.wait_group 0;\n" ::);
     out[base + 2 * lane] = (uint16_t)(x & 0xffffu);

@@ -34,7 +34,7 @@ constexpr uint32_t kSpinLimit = 1u << 24;    // polls before a wait gives up
 template <int K>
 struct __align__(16) PreStep {
     uint32_t q0[32];              // Q at the 32 round-0 points
-    float w[K], mu[K], inv[K];
+    float w[K], mu[K], isg[K];
     int lo, hi;
     float tp;
 };
@@ -151,7 +151,7 @@ __global__ void __launch_bounds__(32 * (32 / CL / SPW + 32 / CL))
         probes += act;
         if (lane == 0) {
 #pragma unroll
-            for (int k = 0; k < K; ++k) { P.w[k] = m.w[k]; P.mu[k] = m.mu[k]; P.inv[k] = m.inv[k]; }
+            for (int k = 0; k < K; ++k) { P.w[k] = m.w[k]; P.mu[k] = m.mu[k]; P.isg[k] = m.isg[k]; }
             P.lo = m.lo;
             P.hi = m.hi;
             P.tp = m.tp;
@@ -162,7 +162,7 @@ __global__ void __launch_bounds__(32 * (32 / CL / SPW + 32 / CL))
     auto fetch = [&](int64_t u, Mix<K>& m, uint32_t (&q0)[VPL]) {
         const PreStep<K>& P = pre[(u % kPre) * SPC + wl];
 #pragma unroll
-        for (int k = 0; k < K; ++k) { m.w[k] = P.w[k]; m.mu[k] = P.mu[k]; m.inv[k] = P.inv[k]; }
+        for (int k = 0; k < K; ++k) { m.w[k] = P.w[k]; m.mu[k] = P.mu[k]; m.isg[k] = P.isg[k]; }
         m.lo = P.lo;
         m.hi = P.hi;
         m.tp = P.tp;

@@ -83,30 +83,40 @@ __device__ __forceinline__ float recip_scale(float s) { return s < 0x1p125f ? re
 // the 1/sqrt(2 pi) of the density Z is pre-multiplied into the b_i
 // (c_i = fp32(b_i / sqrt(2 pi))). z is clamped to [-12, 12] and rounded to the
 // grid 2^-22 (half to even), where this FP32 evaluation is monotone.
-__device__ __forceinline__ float phi_hat(float z)
+//
+// phi_hat_s takes zs = z * 2^22 and works on the grid index r = x * 2^22
+// (an integer below 2^26) with constants scaled by powers of two, which
+// changes no rounding: fma(p 2^-22, r, 1) = fma(p, x, 1) and
+// (r r) (-2^-45) = (x x) (-1/2) exactly, since every scaled value stays a
+// normal float.
+__device__ __forceinline__ float phi_hat_s(float zs)
 {
-    const float kP = 0x1.da6712p-3f;
+    const float kP22 = 0x1.da6712p-25f;   // fp32(p) * 2^-22
     const float kC1 = 0x1.04f20cp-3f;
     const float kC2 = -0x1.23531cp-3f;
     const float kC3 = 0x1.6be1c6p-1f;
     const float kC4 = -0x1.7401c6p-1f;
     const float kC5 = 0x1.0fb844p-1f;
-    // |z| clamped to 12, rounded to the grid (rint is odd, so this is
-    // |rint(clamp(z) 2^22)| 2^-22); the mirror below tests z's sign, which
-    // agrees with the rounded value's except when that is +-0, where both
-    // branches give 1/2 (Phi-hat(0) = 1 - q(0) = q(0) = 1/2 exactly).
-    const float x = __fmul_rn(rintf(__fmul_rn(fminf(fabsf(z), 12.0f), 0x1p22f)), 0x1p-22f);
-    float d = __fmaf_rn(kP, x, 1.0f);   // d in [1, 3.78]
+    // r = |rint(clamp(z) 2^22)| (rint is odd); the mirror below tests z's
+    // sign, which agrees with the rounded value's except when that is +-0,
+    // where both branches give 1/2 (Phi-hat(0) = 1 - q(0) = q(0) = 1/2
+    // exactly).
+    const float r = rintf(fminf(fabsf(zs), 0x1.8p25f));   // 12 * 2^22
+    float d = __fmaf_rn(kP22, r, 1.0f);   // 1 + p x, in [1, 3.78]
     float t = recip(d);
     float h = __fmaf_rn(kC5, t, kC4);
     h = __fmaf_rn(h, t, kC3);
     h = __fmaf_rn(h, t, kC2);
     h = __fmaf_rn(h, t, kC1);
     float g = __fmul_rn(h, t);
-    float a = __fmul_rn(-0.5f, __fmul_rn(x, x));
+    float a = __fmul_rn(__fmul_rn(r, r), -0x1p-45f);   // -x^2 / 2
     float q = __fmul_rn(exp_cw(a), g);
-    return z >= 0.0f ? __fsub_rn(1.0f, q) : q;
+    return zs >= 0.0f ? __fsub_rn(1.0f, q) : q;
 }
+
+// Phi-hat(z) for any z: z * 2^22 is exact (or overflows to +-inf, which the
+// clamp maps to 12 as it does z).
+__device__ __forceinline__ float phi_hat(float z) { return phi_hat_s(__fmul_rn(z, 0x1p22f)); }
 
 // Parameter loads from the planar [3][K][N] layout.
 __device__ __forceinline__ float load_param(const float* p, int64_t i) { return __ldg(p + i); }
@@ -116,11 +126,13 @@ __device__ __forceinline__ float load_param(const __nv_bfloat16* p, int64_t i)
     return __uint_as_float(static_cast<uint32_t>(b) << 16);
 }
 
-// One symbol's mixture, ready for CDF probes: weights, means, reciprocal
-// floored scales, the window [lo, hi] and T' = 2^16 - W - 1.
+// One symbol's mixture, ready for CDF probes: weights, means, 2^22 times the
+// reciprocal floored scales (1/sigma' scaled exactly, so that (b - mu) isg
+// = z 2^22 with the same rounding as (b - mu) / sigma'), the window [lo, hi]
+// and T' = 2^16 - W - 1.
 template <int K>
 struct Mix {
-    float w[K], mu[K], inv[K];
+    float w[K], mu[K], isg[K];
     int lo, hi;
     float tp;
 };
@@ -144,13 +156,13 @@ __device__ __forceinline__ bool load_mix(const T* params, int64_t N, int64_t n, 
         float sp = fmaxf(s, kSigmaMin);
         m.w[k] = w;
         m.mu[k] = mu;
-        m.inv[k] = recip_scale(sp);
+        m.isg[k] = __fmul_rn(recip_scale(sp), 0x1p22f);
         lo_f = fminf(lo_f, __fmaf_rn(-kR, sp, mu));
         hi_f = fmaxf(hi_f, __fmaf_rn(kR, sp, mu));
     }
     if (!ok) {
 #pragma unroll
-        for (int k = 0; k < K; ++k) { m.w[k] = 0.0f; m.mu[k] = 0.0f; m.inv[k] = 1.0f; }
+        for (int k = 0; k < K; ++k) { m.w[k] = 0.0f; m.mu[k] = 0.0f; m.isg[k] = 0x1p22f; }
         lo_f = -1.0f;
         hi_f = 1.0f;
     }
@@ -172,8 +184,8 @@ __device__ __forceinline__ float mix_cdf(const Mix<K>& m, int j)
     float acc = 0.0f;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-        float z = __fmul_rn(__fsub_rn(b, m.mu[k]), m.inv[k]);
-        acc = __fmaf_rn(m.w[k], phi_hat(z), acc);
+        const float zs = __fmul_rn(__fsub_rn(b, m.mu[k]), m.isg[k]);   // z 2^22
+        acc = __fmaf_rn(m.w[k], phi_hat_s(zs), acc);
     }
     return acc;
 }
@@ -184,7 +196,7 @@ template <int K>
 __device__ __forceinline__ uint32_t q_at(const Mix<K>& m, int j)
 {
     const float v = fminf(mix_cdf<K>(m, j), 1.0f);
-    return (uint32_t)(j - m.lo) + (uint32_t)floorf(__fmul_rn(m.tp, v));
+    return (uint32_t)(j - m.lo) + __float2uint_rd(__fmul_rn(m.tp, v));   // floor of a value >= 0
 }
 
 // The rANS interval of symbol s. Escape (s outside [lo, hi]) gets

@@ -39,13 +39,13 @@ __device__ __forceinline__ bool mix_from_params(const RawParams<K>& r, Mix<K>& m
         const float sp = fmaxf(s, kSigmaMin);
         m.w[k] = w;
         m.mu[k] = mu;
-        m.inv[k] = recip_scale(sp);
+        m.isg[k] = __fmul_rn(recip_scale(sp), 0x1p22f);
         lo_f = fminf(lo_f, __fmaf_rn(-kR, sp, mu));
         hi_f = fmaxf(hi_f, __fmaf_rn(kR, sp, mu));
     }
     if (!ok) {
 #pragma unroll
-        for (int k = 0; k < K; ++k) { m.w[k] = 0.0f; m.mu[k] = 0.0f; m.inv[k] = 1.0f; }
+        for (int k = 0; k < K; ++k) { m.w[k] = 0.0f; m.mu[k] = 0.0f; m.isg[k] = 0x1p22f; }
         lo_f = -1.0f;
         hi_f = 1.0f;
     }
