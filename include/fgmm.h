@@ -52,7 +52,7 @@ typedef enum {
     FGMM_ERR_BAD_PARAMS = 2,  /* a mixture parameter is NaN/Inf/negative weight/scale <= 0 */
     FGMM_ERR_CAPACITY = 3,    /* output buffer too small */
     FGMM_ERR_CORRUPT = 4,     /* stream fails the end-of-decode check or would read out of its segment */
-    FGMM_ERR_TIMEOUT = 5,     /* a bounded wait gave up (reserved; no kernel here waits) */
+    FGMM_ERR_TIMEOUT = 5,     /* a bounded wait in a decoder gave up (the refill exchange of fgmm_dec_ws_kernel) */
     FGMM_ERR_CUDA = 6,        /* a CUDA runtime call or launch failed */
     FGMM_ERR_NO_MEMORY = 7,   /* workspace allocation failed */
     FGMM_ERR_TOO_LARGE = 8    /* request exceeds the fixed scratch of fgmm_encode_noalloc */
@@ -288,15 +288,20 @@ fgmm_status fgmm_decode_proposal(fgmm_handle *h, const fgmm_latent *lat, const v
  * stream), 2, 4, 8, 16 or 32 (G-ary search, G lanes per stream), or 0 to
  * choose from the number of segments (default). FGMM_OPT_DECODE_CLUSTER:
  * CTAs (a thread-block cluster, one SM each) sharing one segment when G > 1:
- * 1, 2 or 4 (at most G), 8 for G >= 8, or 0 for automatic. The decoded
- * symbols do not depend on either. */
-enum { FGMM_OPT_DECODE_LANES = 1, FGMM_OPT_DECODE_CLUSTER = 2 };
+ * 1, 2 or 4 (at most G), 8 for G >= 8, or 0 for automatic.
+ * FGMM_OPT_DECODE_ROUND0: points of the first search round that producer
+ * warps of the warp-specialised decoder evaluate ahead of the state chain
+ * when G = 16: 16 (two streams per producer warp) or 32, or 0 for
+ * automatic; G = 8 and 32 always take 32. The decoded symbols depend on
+ * none of these. */
+enum { FGMM_OPT_DECODE_LANES = 1, FGMM_OPT_DECODE_CLUSTER = 2, FGMM_OPT_DECODE_ROUND0 = 3 };
 fgmm_status fgmm_set_option(fgmm_handle *h, int32_t option, int64_t value);
 
 /* The decoder fgmm_decode would run for S streams (S / 32 segments) under
  * the handle's current options; host only, no GPU work, nothing allocated.
- * out (host, 3 entries): out[0] = lanes per stream, out[1] = CTAs per
- * segment (cluster size), out[2] = the kernel:
+ * out (host, 4 entries): out[0] = lanes per stream, out[1] = CTAs per
+ * segment (cluster size), out[3] = first-round points (FGMM_DEC_WS and
+ * FGMM_DEC_WIDE; 0 for the others), out[2] = the kernel:
  *   FGMM_DEC_LANE  one lane per stream, binary search over the window
  *                  (Sec. III-B), one warp per segment;
  *   FGMM_DEC_COOP  G = 2..16 lanes per stream, G-ary search (clusters of
@@ -310,7 +315,7 @@ fgmm_status fgmm_set_option(fgmm_handle *h, int32_t option, int64_t value);
  * Errors: FGMM_ERR_INVALID_ARG for a NULL argument or S not a positive
  * multiple of 32. */
 enum { FGMM_DEC_LANE = 0, FGMM_DEC_COOP = 1, FGMM_DEC_WIDE = 2, FGMM_DEC_WS = 3 };
-fgmm_status fgmm_decode_plan(fgmm_handle *h, int32_t S, int32_t out[3]);
+fgmm_status fgmm_decode_plan(fgmm_handle *h, int32_t S, int32_t out[4]);
 
 /* Optional counters. When enabled, decoders add the number of quantised-CDF
  * evaluations they make to a device counter; fgmm_stats_read synchronises

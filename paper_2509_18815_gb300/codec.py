@@ -158,11 +158,13 @@ def decode(params: torch.Tensor, words: torch.Tensor, offsets: torch.Tensor, S: 
 
 def decode_plan(S: int, h: Handle | None = None) -> dict:
     """Decoder that decode() runs for S streams under the handle's options:
-    lanes per stream, CTAs per segment and the kernel's name."""
+    lanes per stream, CTAs per segment, first-round points and the kernel's
+    name."""
     h = h or handle()
-    out = (ctypes.c_int32 * 3)()
+    out = (ctypes.c_int32 * 4)()
     h.check(_abi.fgmm_decode_plan(h.ptr, S, out))
-    return {"lanes": int(out[0]), "cluster": int(out[1]), "kernel": _abi.DECODE_KERNELS[int(out[2])]}
+    return {"lanes": int(out[0]), "cluster": int(out[1]), "round0": int(out[3]),
+            "kernel": _abi.DECODE_KERNELS[int(out[2])]}
 
 
 def stats_enable(on: bool = True, h: Handle | None = None):

@@ -619,8 +619,10 @@ fgmm_status fgmm_decode(fgmm_handle* h, const fgmm_latent* lat, const uint16_t* 
     a.out = symbols_out;
     a.err = h->d_err;
     a.stats = h->stats_on ? h->d_stats : nullptr;
-    int lanes = 1, cluster = 1, kernel = 0;
-    decode_resolve(a.nseg, h->num_sms, h->decode_lanes, h->decode_cluster, &lanes, &cluster, &kernel);
+    int lanes = 1, cluster = 1, round0 = 0, kernel = 0;
+    decode_resolve(a.nseg, h->num_sms, h->decode_lanes, h->decode_cluster, h->decode_round0, &lanes, &cluster, &round0,
+                   &kernel);
+    a.r0 = round0 > 0 ? round0 : 32;
     cudaError_t e = launch_decode(a, lat->K, lat->dtype, lanes, cluster, st);
     return e == cudaSuccess ? FGMM_OK : cuda_fail(h, e, "fgmm_decode launch");
 }
@@ -629,11 +631,13 @@ fgmm_status fgmm_decode_plan(fgmm_handle* h, int32_t S, int32_t* out)
 {
     if (!h || !out) return fail(h, FGMM_ERR_INVALID_ARG, "fgmm_decode_plan: NULL argument");
     if (S <= 0 || S % 32 != 0) return fail(h, FGMM_ERR_INVALID_ARG, "S must be a positive multiple of 32");
-    int lanes = 1, cluster = 1, kernel = 0;
-    decode_resolve(S / 32, h->num_sms, h->decode_lanes, h->decode_cluster, &lanes, &cluster, &kernel);
+    int lanes = 1, cluster = 1, round0 = 0, kernel = 0;
+    decode_resolve(S / 32, h->num_sms, h->decode_lanes, h->decode_cluster, h->decode_round0, &lanes, &cluster,
+                   &round0, &kernel);
     out[0] = lanes;
     out[1] = cluster;
     out[2] = kernel;
+    out[3] = round0;
     return FGMM_OK;
 }
 
@@ -650,6 +654,11 @@ fgmm_status fgmm_set_option(fgmm_handle* h, int32_t option, int64_t value)
         if (!(value == 0 || value == 1 || value == 2 || value == 4 || value == 8))
             return fail(h, FGMM_ERR_INVALID_ARG, "decode cluster must be 0 (auto), 1, 2, 4 or 8");
         h->decode_cluster = (int)value;
+        return FGMM_OK;
+    case FGMM_OPT_DECODE_ROUND0:
+        if (!(value == 0 || value == 16 || value == 32))
+            return fail(h, FGMM_ERR_INVALID_ARG, "decode first-round points must be 0 (auto), 16 or 32");
+        h->decode_round0 = (int)value;
         return FGMM_OK;
     default:
         return fail(h, FGMM_ERR_INVALID_ARG, "unknown option");

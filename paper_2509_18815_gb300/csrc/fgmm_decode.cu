@@ -6,33 +6,39 @@ namespace fgmm {
 
 cudaError_t launch_decode_bf16(const DecodeArgs& a, int K, int G, int CL, cudaStream_t st);
 
-void decode_config_auto(int64_t nseg, int num_sms, int* lanes, int* cluster)
+void decode_config_auto(int64_t nseg, int num_sms, int* lanes, int* cluster, int* round0)
 {
     // Enough segments to give every SM several warps: one lane per stream,
     // binary search (least work). Fewer: G lanes per stream, and a cluster of
     // CTAs per segment when the segments leave most SMs idle; the fewer the
-    // segments, the more lanes per stream. Measured on GB300 (152 SMs):
-    // 1-8 segments -> 32 lanes x clusters of 8; 16-32 -> 16 lanes x clusters
-    // of 4; 48-100 -> 8 lanes x clusters of 8; 152 -> 8 lanes; 200-304 ->
+    // segments, the more lanes per stream. With more segments per SM the
+    // issue slots bind, and a 16-point first round (two streams per producer
+    // warp) beats a 32-point one. Measured on GB300 (152 SMs): 1-8 segments
+    // -> 32 lanes x clusters of 8; 16-32 -> 16 lanes x clusters of 4 with 32
+    // first-round points; 48-68 -> 16 lanes x clusters of 8, 16 points;
+    // 100 -> 16 lanes x clusters of 4, 16 points; 152 -> 8 lanes; 200-304 ->
     // 4 lanes; 608 -> 1 lane.
     const int64_t sms = num_sms;
+    *round0 = 32;
     if (nseg >= 4 * sms) { *lanes = 1; *cluster = 1; return; }
     if (nseg * 16 <= sms) { *lanes = 32; *cluster = 8; return; }
     if (nseg * 4 <= sms) { *lanes = 16; *cluster = 4; return; }
-    if (nseg * 3 <= sms * 2) { *lanes = 8; *cluster = 8; return; }
+    if (nseg * 2 <= sms) { *lanes = 16; *cluster = 8; *round0 = 16; return; }
+    if (nseg * 3 <= sms * 2) { *lanes = 16; *cluster = 4; *round0 = 16; return; }
     if (nseg * 4 <= sms * 5) { *lanes = 8; *cluster = 1; return; }
     *lanes = 4;
     *cluster = 1;
 }
 
-void decode_resolve(int64_t nseg, int num_sms, int opt_lanes, int opt_cluster, int* lanes, int* cluster,
-                    int* kernel)
+void decode_resolve(int64_t nseg, int num_sms, int opt_lanes, int opt_cluster, int opt_round0, int* lanes,
+                    int* cluster, int* round0, int* kernel)
 {
-    int G = 1, CL = 1;
-    decode_config_auto(nseg, num_sms, &G, &CL);
+    int G = 1, CL = 1, R0 = 32;
+    decode_config_auto(nseg, num_sms, &G, &CL, &R0);
     if (opt_lanes > 0) {
         G = opt_lanes;
         CL = 1;
+        R0 = 32;
     }
     if (opt_cluster > 0) CL = opt_cluster;
     if (G < 2) CL = 1;
@@ -41,11 +47,15 @@ void decode_resolve(int64_t nseg, int num_sms, int opt_lanes, int opt_cluster, i
     *lanes = G;
     *cluster = CL;
     // G >= 8 with a cluster: the warp-specialised kernel (32 / G streams per
-    // consumer warp); G = 32 in one CTA: the wide kernel
+    // consumer warp; a 16-point first round only with 16 lanes per stream);
+    // G = 32 in one CTA: the wide kernel
     if (G == 1) *kernel = FGMM_DEC_LANE;
     else if (CL >= 2 && G >= 8) *kernel = FGMM_DEC_WS;
     else if (G == 32) *kernel = FGMM_DEC_WIDE;
     else *kernel = FGMM_DEC_COOP;
+    if (opt_round0 > 0) R0 = opt_round0;
+    if (*kernel == FGMM_DEC_WS) *round0 = G == 16 ? R0 : 32;
+    else *round0 = *kernel == FGMM_DEC_WIDE ? 32 : 0;
 }
 
 cudaError_t launch_decode(const DecodeArgs& a, int K, int dtype, int G, int CL, cudaStream_t st)

@@ -4,13 +4,14 @@
 // Binary search over the on-the-fly quantised CDF (Sec. III-A) split into a
 // state-independent part and a state-dependent chain. Per stream, a producer
 // warp prepares, kLead steps ahead, the stream's mixture (reciprocal scales,
-// window) and evaluates Q at 32 points spread over the window (round 0).
-// Consumer warps run the chain of each step: a count of the round-0 values
-// at or below the slot brackets the symbol between two round-0 points, the
-// points inside the bracket (at most ceil(W/32) - 1) are evaluated in one
-// round, then the inverse rANS step (Eq. 3) and the segment's refill
-// exchange. A consumer warp serves SPW streams with 32/SPW lanes each (one
-// bracket round when the bracket interior fits the lanes, more otherwise).
+// window) and evaluates Q at R0 (16 or 32) points spread over the window
+// (round 0); a producer warp serves 32/R0 streams. Consumer warps run the
+// chain of each step: a count of the round-0 values at or below the slot
+// brackets the symbol between two round-0 points, the points inside the
+// bracket (at most ceil(W/R0) - 1) are evaluated, then the inverse rANS step
+// (Eq. 3) and the segment's refill exchange. A consumer warp serves SPW
+// streams with 32/SPW lanes each (one bracket round when the bracket
+// interior always fits the lanes, rounds of 32/SPW points otherwise).
 //
 // The exchange is a flag per stream, not a barrier: each stream writes
 // (exchange number, refill bit, escape bit) into a double-buffered slot of
@@ -66,7 +67,7 @@ __device__ __forceinline__ uint32_t exchange(uint32_t* xflag, uint32_t* abort_fl
         if (__all_sync(kFull, (f >> 2) == tag)) return f & 3u;
         if (__any_sync(kFull, *va != 0u)) return 0u;
         if (spin >= kSpinLimit) {
-            if (lane == 0) set_error(err, kErrCorrupt);
+            if (lane == 0) set_error(err, kErrTimeout);
             if (lane < CL) store_rank(abort_flag, (uint32_t)lane, 1u);
             return 0u;
         }
@@ -91,19 +92,32 @@ __device__ __forceinline__ void ws_refill(uint32_t& x, bool need, uint32_t M, ui
     }
 }
 
-template <int K, typename T, int CL, int SPW>
-__global__ void __launch_bounds__(32 * (32 / CL / SPW + 32 / CL))
+// Round-0 point i of R0 over the window [lo, hi]: the (i+1)/R0 quantile of
+// the positions lo+1 .. hi+1 (point R0-1 is hi+1, the escape boundary).
+template <int K, int R0>
+__device__ __forceinline__ int round0_point(const Mix<K>& m, int i)
+{
+    const int W = m.hi - m.lo + 1;
+    return m.lo + ((i + 1) * W + R0 - 1) / R0;
+}
+
+template <int K, typename T, int CL, int SPW, int R0>
+__global__ void __launch_bounds__(32 * (32 / CL / SPW + 32 / CL * R0 / 32))
     fgmm_dec_ws_kernel(const T* __restrict__ params, int64_t N, int32_t S, int64_t T_steps,
                        const uint16_t* __restrict__ words, int64_t n_words, const int64_t* __restrict__ offsets,
                        int32_t* __restrict__ out, int32_t* err, unsigned long long* stats, int mode)
 {
     constexpr int SPC = 32 / CL;              // streams per CTA
     constexpr int LPS = 32 / SPW;             // consumer lanes per stream
-    constexpr int VPL = SPW;                  // round-0 values per consumer lane
+    constexpr int VPL = R0 / LPS;             // round-0 values per consumer lane
     constexpr int CW = SPC / SPW;             // consumer warps
-    constexpr int NT = 32 * (CW + SPC);       // consumer warps + one producer warp per stream
-    constexpr int PNT = 32 * SPC;             // producer threads
-    static_assert(SPC % SPW == 0 && LPS >= CL, "a consumer warp's streams lie in one CTA");
+    constexpr int SPP = 32 / R0;              // streams per producer warp
+    constexpr int PW = SPC / SPP;             // producer warps
+    constexpr int NT = 32 * (CW + PW);
+    constexpr int PNT = 32 * PW;              // producer threads
+    // W <= 511, so the bracket interior has at most ceil(511 / R0) - 1 points
+    constexpr bool kOneRound = LPS >= (511 + R0 - 1) / R0 - 1;
+    static_assert(SPC % SPW == 0 && SPC % SPP == 0 && LPS >= CL && VPL >= 1, "stream groups lie in one CTA");
     extern __shared__ __align__(16) unsigned char smem[];
     PreStep<K>* pre = reinterpret_cast<PreStep<K>*>(smem);                                  // [kPre][SPC]
     T* ring = reinterpret_cast<T*>(smem + sizeof(PreStep<K>) * kPre * SPC);               // [kRing][3K][SPC]
@@ -116,7 +130,8 @@ __global__ void __launch_bounds__(32 * (32 / CL / SPW + 32 / CL))
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const bool producer = warp >= CW;
     const int grp = lane / LPS, j = lane % LPS;       // consumer: stream group, lane in group
-    const int wl = producer ? warp - CW : warp * SPW + grp;   // stream slot in this CTA
+    const int pi = lane % R0;                         // producer: round-0 point of this lane
+    const int wl = producer ? (warp - CW) * SPP + lane / R0 : warp * SPW + grp;   // stream slot in this CTA
     const int ws = rank * SPC + wl;                   // stream within the segment
     const uint32_t bit = 1u << ws;
     const int gbase = grp * LPS;
@@ -147,9 +162,9 @@ __global__ void __launch_bounds__(32 * (32 / CL / SPW + 32 / CL))
         const bool act = u * (int64_t)S + g * 32 + ws < N;
         badp |= act && !ok;
         PreStep<K>& P = pre[(u % kPre) * SPC + wl];
-        P.q0[lane] = q_at<K>(m, wide_point<K>(m, lane));
+        P.q0[pi] = q_at<K>(m, round0_point<K, R0>(m, pi));
         probes += act;
-        if (lane == 0) {
+        if (pi == 0) {
 #pragma unroll
             for (int k = 0; k < K; ++k) { P.w[k] = m.w[k]; P.mu[k] = m.mu[k]; P.isg[k] = m.isg[k]; }
             P.lo = m.lo;
@@ -230,25 +245,24 @@ __global__ void __launch_bounds__(32 * (32 / CL / SPW + 32 / CL))
             for (int v = 0; v < VPL; ++v) c += __popc(__ballot_sync(kFull, act && q0[v] <= slot) & gmask);
             uint32_t qa0, qb0;   // Q at the round-0 points that bracket the symbol
             if constexpr (VPL == 1) {
-                const uint32_t qc1 = __shfl_sync(kFull, q0[0], c > 0 ? c - 1 : 0);
+                const uint32_t qc1 = __shfl_sync(kFull, q0[0], gbase + (c > 0 ? c - 1 : 0));
                 qa0 = c > 0 ? qc1 : 0u;
-                qb0 = __shfl_sync(kFull, q0[0], c < 32 ? c : 31);
+                qb0 = __shfl_sync(kFull, q0[0], gbase + (c < R0 ? c : R0 - 1));
             } else {
                 const PreStep<K>& P = pre[(t % kPre) * SPC + wl];   // rewritten two steps later
-                qb0 = P.q0[c < 32 ? c : 31];
+                qb0 = P.q0[c < R0 ? c : R0 - 1];
                 qa0 = c > 0 ? P.q0[c - 1] : 0u;
             }
-            if (act && c == 32) {   // Q(hi+1) <= slot: escape
+            if (act && c == R0) {   // Q(hi+1) <= slot: escape
                 esc = true;
                 start = qa0;
                 freq = kM - start;
             }
             const int W = m.hi - m.lo + 1;
-            const int a = c > 0 ? m.lo + (c * W + 31) / 32 : m.lo;
-            const int b = m.lo + ((min(c, 31) + 1) * W + 31) / 32;
+            const int a = c > 0 ? m.lo + (c * W + R0 - 1) / R0 : m.lo;
+            const int b = m.lo + ((min(c, R0 - 1) + 1) * W + R0 - 1) / R0;
             const int L = b - a;   // the symbol lies in [a, b); its L - 1 inner points are evaluated
-            if constexpr (LPS >= 16) {
-                // W <= 511, so the bracket has at most 15 inner points: one round
+            if constexpr (kOneRound) {
                 const bool valid = act && !esc && j < L - 1;
                 const uint32_t q1 = q_at<K>(m, min(a + 1 + j, m.hi + 1));
                 probes += valid;
@@ -261,7 +275,7 @@ __global__ void __launch_bounds__(32 * (32 / CL / SPW + 32 / CL))
                     freq = (c1 < L - 1 ? q1b : qb0) - start;
                 }
             } else {
-                // 8 lanes per stream: rounds of 8 inner points
+                // rounds of LPS inner points
                 int c1 = 0;
                 uint32_t lastq = qa0, endq = qb0;
                 bool open = act && !esc && L > 1;
@@ -340,15 +354,15 @@ __global__ void __launch_bounds__(32 * (32 / CL / SPW + 32 / CL))
     seg_sync<CL>();       // no CTA leaves while another may still write its flags
 }
 
-template <int K, typename T, int CL, int SPW>
+template <int K, typename T, int CL, int SPW, int R0>
 cudaError_t launch_ws(const DecodeArgs& a, cudaStream_t st)
 {
     constexpr int SPC = 32 / CL;
-    constexpr int NT = 32 * (SPC / SPW + SPC);
+    constexpr int NT = 32 * (SPC / SPW + SPC * R0 / 32);
     const size_t smem = sizeof(PreStep<K>) * kPre * SPC + sizeof(T) * kRing * 3 * K * SPC + sizeof(uint32_t) * 68 +
                         sizeof(uint16_t) * kWordCap;
     if (a.T >= ((int64_t)1 << 28)) return cudaErrorInvalidValue;   // exchange numbers stay below 2^30
-    auto kern = fgmm_dec_ws_kernel<K, T, CL, SPW>;
+    auto kern = fgmm_dec_ws_kernel<K, T, CL, SPW, R0>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const uintptr_t base = reinterpret_cast<uintptr_t>(a.params);
@@ -371,23 +385,25 @@ cudaError_t launch_ws(const DecodeArgs& a, cudaStream_t st)
                               a.offsets, a.out, a.err, a.stats, mode);
 }
 
-template <int K, typename T, int SPW>
+template <int K, typename T, int SPW, int R0>
 cudaError_t launch_ws_cl(const DecodeArgs& a, int CL, cudaStream_t st)
 {
     switch (CL) {
-    case 8: return launch_ws<K, T, 8, SPW>(a, st);
-    case 4: return launch_ws<K, T, 4, SPW>(a, st);
-    default: return launch_ws<K, T, 2, SPW>(a, st);
+    case 8: return launch_ws<K, T, 8, SPW, R0>(a, st);
+    case 4: return launch_ws<K, T, 4, SPW, R0>(a, st);
+    default: return launch_ws<K, T, 2, SPW, R0>(a, st);
     }
 }
 
+// Round-0 width: 32 points for 32 and 8 lanes per stream; 16 lanes per
+// stream take 16 (two streams per producer warp) or 32, as a.r0 says.
 template <int K, typename T>
 cudaError_t launch_ws_k(const DecodeArgs& a, int CL, int SPW, cudaStream_t st)
 {
     switch (SPW) {
-    case 4: return launch_ws_cl<K, T, 4>(a, CL, st);
-    case 2: return launch_ws_cl<K, T, 2>(a, CL, st);
-    default: return launch_ws_cl<K, T, 1>(a, CL, st);
+    case 4: return launch_ws_cl<K, T, 4, 32>(a, CL, st);
+    case 2: return a.r0 == 16 ? launch_ws_cl<K, T, 2, 16>(a, CL, st) : launch_ws_cl<K, T, 2, 32>(a, CL, st);
+    default: return launch_ws_cl<K, T, 1, 32>(a, CL, st);
     }
 }
 

@@ -27,6 +27,7 @@ constexpr float kSigmaMin = 0.11f;         // scale floor
 constexpr int32_t kErrBadParams = 2;
 constexpr int32_t kErrCapacity = 3;
 constexpr int32_t kErrCorrupt = 4;
+constexpr int32_t kErrTimeout = 5;
 
 __device__ __forceinline__ void set_error(int32_t* err, int32_t code)
 {

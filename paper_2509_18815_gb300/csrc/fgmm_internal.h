@@ -18,7 +18,8 @@ struct fgmm_handle {
     size_t ws_bytes = 0;
     int num_sms = 0;
     int decode_lanes = 0;              // 0 = automatic; else lanes per stream (1, 2, 4, 8, 16, 32)
-    int decode_cluster = 0;            // 0 = automatic; else CTAs per segment (1, 2, 4)
+    int decode_cluster = 0;            // 0 = automatic; else CTAs per segment (1, 2, 4, 8)
+    int decode_round0 = 0;             // 0 = automatic; else first-round points of the ws decoder (16, 32)
     std::string last_error;
 };
 
@@ -82,16 +83,17 @@ struct DecodeArgs {
     int32_t* out;
     int32_t* err;
     unsigned long long* stats;
+    int r0 = 32;                       // first-round points of the warp-specialised decoder
 };
-void decode_config_auto(int64_t nseg, int num_sms, int* lanes, int* cluster);
+void decode_config_auto(int64_t nseg, int num_sms, int* lanes, int* cluster, int* round0);
 // Warp-specialised decoder for fp32 / bf16 parameters: CL CTAs per segment,
 // SPW streams per consumer warp (1, 2 or 4).
 cudaError_t launch_ws_f32(const DecodeArgs& a, int K, int CL, int SPW, cudaStream_t st);
 cudaError_t launch_ws_bf16(const DecodeArgs& a, int K, int CL, int SPW, cudaStream_t st);
 // Final decoder choice: automatic plan, then the handle's options, then the
 // limits of each kernel (clusters only with G >= 2, at most 4 below G = 32).
-void decode_resolve(int64_t nseg, int num_sms, int opt_lanes, int opt_cluster, int* lanes, int* cluster,
-                    int* kernel);
+void decode_resolve(int64_t nseg, int num_sms, int opt_lanes, int opt_cluster, int opt_round0, int* lanes,
+                    int* cluster, int* round0, int* kernel);
 cudaError_t launch_decode(const DecodeArgs& a, int K, int dtype, int lanes, int cluster, cudaStream_t st);
 
 }  // namespace fgmm

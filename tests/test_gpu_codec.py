@@ -249,35 +249,81 @@ def test_decode_plan_follows_segments_and_options():
     from paper_2509_18815_gb300._abi import FgmmError
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     many = 32 * 4 * sms
-    assert codec.decode_plan(many) == {"lanes": 1, "cluster": 1, "kernel": "fgmm_dec_kernel"}
-    assert codec.decode_plan(32) == {"lanes": 32, "cluster": 8, "kernel": "fgmm_dec_ws_kernel"}
+    assert codec.decode_plan(many) == {"lanes": 1, "cluster": 1, "round0": 0, "kernel": "fgmm_dec_kernel"}
+    assert codec.decode_plan(32) == {"lanes": 32, "cluster": 8, "round0": 32, "kernel": "fgmm_dec_ws_kernel"}
     few = 32 * max(1, sms // 4)
-    assert codec.decode_plan(few) == {"lanes": 16, "cluster": 4, "kernel": "fgmm_dec_ws_kernel"}
+    assert codec.decode_plan(few) == {"lanes": 16, "cluster": 4, "round0": 32, "kernel": "fgmm_dec_ws_kernel"}
     try:
         _set_lanes(4)
-        assert codec.decode_plan(few) == {"lanes": 4, "cluster": 1, "kernel": "fgmm_dec_coop_kernel"}
+        assert codec.decode_plan(few) == {"lanes": 4, "cluster": 1, "round0": 0, "kernel": "fgmm_dec_coop_kernel"}
         _set_lanes(32)
-        assert codec.decode_plan(few) == {"lanes": 32, "cluster": 1, "kernel": "fgmm_dec_wide_kernel"}
+        assert codec.decode_plan(few) == {"lanes": 32, "cluster": 1, "round0": 32, "kernel": "fgmm_dec_wide_kernel"}
         _set_lanes(4)
         _set_cluster(8)
-        assert codec.decode_plan(few) == {"lanes": 4, "cluster": 4, "kernel": "fgmm_dec_coop_kernel"}
+        assert codec.decode_plan(few) == {"lanes": 4, "cluster": 4, "round0": 0, "kernel": "fgmm_dec_coop_kernel"}
         _set_lanes(8)
-        assert codec.decode_plan(few) == {"lanes": 8, "cluster": 8, "kernel": "fgmm_dec_ws_kernel"}
+        assert codec.decode_plan(few) == {"lanes": 8, "cluster": 8, "round0": 32, "kernel": "fgmm_dec_ws_kernel"}
         _set_lanes(16)
         _set_cluster(1)
-        assert codec.decode_plan(few) == {"lanes": 16, "cluster": 1, "kernel": "fgmm_dec_coop_kernel"}
+        assert codec.decode_plan(few) == {"lanes": 16, "cluster": 1, "round0": 0, "kernel": "fgmm_dec_coop_kernel"}
         _set_cluster(8)
         _set_lanes(1)
-        assert codec.decode_plan(few) == {"lanes": 1, "cluster": 1, "kernel": "fgmm_dec_kernel"}
+        assert codec.decode_plan(few) == {"lanes": 1, "cluster": 1, "round0": 0, "kernel": "fgmm_dec_kernel"}
         _set_lanes(32)
         _set_cluster(1)
-        assert codec.decode_plan(few) == {"lanes": 32, "cluster": 1, "kernel": "fgmm_dec_wide_kernel"}
+        assert codec.decode_plan(few) == {"lanes": 32, "cluster": 1, "round0": 32, "kernel": "fgmm_dec_wide_kernel"}
+        _set_lanes(0)
+        _set_cluster(0)
+        _set_round0(16)
+        assert codec.decode_plan(few) == {"lanes": 16, "cluster": 4, "round0": 16, "kernel": "fgmm_dec_ws_kernel"}
+        _set_lanes(8)
+        _set_cluster(8)
+        assert codec.decode_plan(few) == {"lanes": 8, "cluster": 8, "round0": 32, "kernel": "fgmm_dec_ws_kernel"}
     finally:
         _set_lanes(0)
         _set_cluster(0)
+        _set_round0(0)
+    for bad in (8, 64, -1):
+        with pytest.raises(FgmmError):
+            _set_round0(bad)
     for bad in (0, -32, 33):
         with pytest.raises(FgmmError):
             codec.decode_plan(bad)
+
+
+def _set_round0(R0):
+    from paper_2509_18815_gb300 import _abi
+    codec = _codec()
+    h = codec.handle()
+    h.check(_abi.fgmm_set_option(h.ptr, _abi.FGMM_OPT_DECODE_ROUND0, R0))
+
+
+@pytest.mark.parametrize("case", range(len(DECODE_CASES)))
+@pytest.mark.parametrize("CL", [2, 4, 8])
+@pytest.mark.parametrize("R0", [16, 32])
+def test_decode_round0_widths_give_identical_symbols(case, CL, R0):
+    """16 lanes per stream with a 16- or 32-point first round (two or one
+    streams per producer warp; with 16 points a wide window's bracket can
+    need two rounds of 16 inner points) decode the same symbols."""
+    codec = _codec()
+    C, H, W, K, seed, esc, smax, S, bf16, cut = DECODE_CASES[case]
+    lat = synth.make_latent(C, H, W, K, seed=seed, escape_stress=esc, sigma_max=smax)
+    p, s = lat.params, lat.symbols
+    if cut is not None:
+        p, s = np.ascontiguousarray(p[:, :, :cut]), np.ascontiguousarray(s[:cut])
+    dp, ds = dev_params(p, bf16), dev_i32(s)
+    words, off = codec.encode(dp, ds, S)
+    try:
+        _set_lanes(16)
+        _set_cluster(CL)
+        _set_round0(R0)
+        assert codec.decode_plan(S)["round0"] == R0
+        out = codec.decode(dp, words, off, S).cpu().numpy()
+    finally:
+        _set_lanes(0)
+        _set_cluster(0)
+        _set_round0(0)
+    np.testing.assert_array_equal(out, s)
 
 
 @pytest.mark.parametrize("G,CL", [(1, 1), (8, 1), (32, 1), (8, 4), (8, 8), (16, 2), (32, 8)])
