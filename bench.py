@@ -441,42 +441,110 @@ def run_fgmm(args):
     ideal_bits, coded_bits, max_cdf_err, n_esc = aud.cpu().tolist()
 
     # end to end through the C ABI from pinned host buffers: H2D parameters
-    # and symbols, encode, D2H stream; H2D stream, decode, D2H symbols
+    # and symbols, encode, D2H stream (its length read on the host); H2D
+    # stream, decode, D2H symbols. Serial: one step at a time. Pipelined:
+    # the same calls with NB buffer sets, input copies on one stream and
+    # result copies on another, so step i+1's copies and encode overlap step
+    # i's decode.
+    NB = 3
     hp = torch.from_numpy(lat.params).pin_memory()
     hs = torch.from_numpy(lat.symbols).pin_memory()
-    hw = torch.empty(cap, dtype=torch.int16).pin_memory()
-    ho = torch.empty(S // 32 + 1, dtype=torch.int64).pin_memory()
-    ht = torch.empty(1, dtype=torch.int64).pin_memory()
-    hout = torch.empty(N, dtype=torch.int32).pin_memory()
-    dwords = torch.empty(cap, dtype=torch.int16, device=dev)
-    doff = torch.empty(S // 32 + 1, dtype=torch.int64, device=dev)
+    hw = [torch.empty(cap, dtype=torch.int16).pin_memory() for _ in range(NB)]
+    ho = [torch.empty(S // 32 + 1, dtype=torch.int64).pin_memory() for _ in range(NB)]
+    ht = [torch.empty(1, dtype=torch.int64).pin_memory() for _ in range(NB)]
+    hout = [torch.empty(N, dtype=torch.int32).pin_memory() for _ in range(NB)]
+    dp2 = [dp] + [torch.empty_like(dp) for _ in range(NB - 1)]
+    ds2 = [ds] + [torch.empty_like(ds) for _ in range(NB - 1)]
+    desc2 = [codec.latent(x) for x in dp2]
+    words2 = [words] + [torch.empty_like(words) for _ in range(NB - 1)]
+    off2 = [offsets] + [torch.empty_like(offsets) for _ in range(NB - 1)]
+    tot2 = [total] + [torch.empty_like(total) for _ in range(NB - 1)]
+    dwords2 = [torch.empty(cap, dtype=torch.int16, device=dev) for _ in range(NB)]
+    doff2 = [torch.empty(S // 32 + 1, dtype=torch.int64, device=dev) for _ in range(NB)]
+    out2 = [out] + [torch.empty_like(out) for _ in range(NB - 1)]
+    cs = stream
+    xs = torch.cuda.Stream(dev)    # host-to-device inputs
+    ys = torch.cuda.Stream(dev)    # words round trip and decoded symbols
+    csp = ctypes.c_void_p(cs.cuda_stream)
+    ev_in, ev_enc, ev_words, ev_dec, ev_free = ([torch.cuda.Event() for _ in range(NB)] for _ in range(5))
+    nw_last = [0] * NB
+
+    def issue_inputs(i, xst):
+        b = i % NB
+        with torch.cuda.stream(xst):
+            if i >= NB:
+                xst.wait_event(ev_free[b])
+            dp2[b].copy_(hp, non_blocking=True)
+            ds2[b].copy_(hs, non_blocking=True)
+            ev_in[b].record(xst)
+
+    def issue_encode(i):
+        b = i % NB
+        cs.wait_event(ev_in[b])
+        h.check(_abi.fgmm_encode(h.ptr, ctypes.byref(desc2[b]), ds2[b].data_ptr(), S, words2[b].data_ptr(), cap,
+                                 off2[b].data_ptr(), tot2[b].data_ptr(), csp))
+        with torch.cuda.stream(cs):
+            ht[b].copy_(tot2[b], non_blocking=True)
+            ho[b].copy_(off2[b], non_blocking=True)
+        ev_enc[b].record(cs)
+
+    def finish(i, yst):
+        b = i % NB
+        ev_enc[b].synchronize()
+        nw = int(ht[b].item())
+        nw_last[b] = nw
+        with torch.cuda.stream(yst):
+            yst.wait_event(ev_enc[b])
+            hw[b][:nw].copy_(words2[b][:nw], non_blocking=True)
+            dwords2[b][:nw].copy_(hw[b][:nw], non_blocking=True)
+            doff2[b].copy_(ho[b], non_blocking=True)
+            ev_words[b].record(yst)
+        cs.wait_event(ev_words[b])
+        h.check(_abi.fgmm_decode(h.ptr, ctypes.byref(desc2[b]), dwords2[b].data_ptr(), nw, doff2[b].data_ptr(), S,
+                                 out2[b].data_ptr(), csp))
+        ev_dec[b].record(cs)
+        with torch.cuda.stream(yst):
+            yst.wait_event(ev_dec[b])
+            hout[b].copy_(out2[b], non_blocking=True)
+            ev_free[b].record(yst)
+
+    # serial: every step waits for the previous one (one stream, one buffer set)
     e2e_t = []
-    h2d = d2h = 0
     for i in range(args.e2e_steps + 2):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        dp.copy_(hp, non_blocking=True)
-        ds.copy_(hs, non_blocking=True)
-        enc()
-        ht.copy_(total, non_blocking=True)
-        ho.copy_(offsets, non_blocking=True)
-        stream.synchronize()
-        nw = int(ht.item())
-        hw[:nw].copy_(words[:nw], non_blocking=True)
-        dwords[:nw].copy_(hw[:nw], non_blocking=True)
-        doff.copy_(ho, non_blocking=True)
-        h.check(_abi.fgmm_decode(h.ptr, L, dwords.data_ptr(), nw, doff.data_ptr(), S, out.data_ptr(), sptr))
-        hout.copy_(out, non_blocking=True)
-        stream.synchronize()
+        issue_inputs(0, cs)
+        issue_encode(0)
+        finish(0, cs)
+        cs.synchronize()
         dt = time.perf_counter() - t0
         if i >= 2:
             e2e_t.append(dt)
-        h2d = hp.numel() * 4 + hs.numel() * 4 + nw * 2 + ho.numel() * 8
-        d2h = 8 + ho.numel() * 8 + nw * 2 + hout.numel() * 4
     h.sync()
-    assert torch.equal(hout, hs), "end-to-end round trip failed"
-    e2e_ms = 1e3 * statistics.median(e2e_t)
-    (e2e_ms,) = max_over_ranks([e2e_ms], device=dev)
+    assert torch.equal(hout[0], hs), "end-to-end round trip failed"
+    e2e_serial_ms = 1e3 * statistics.median(e2e_t)
+    # pipelined: step i+1's inputs and encode are issued before step i's decode
+    n_pipe = max(args.e2e_steps, 2 * NB)
+    for rep in range(2):   # the first pass warms the second stream and the buffers
+        for x in hout:
+            x.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        issue_inputs(0, xs)
+        issue_encode(0)
+        for i in range(n_pipe):
+            if i + 1 < n_pipe:
+                issue_inputs(i + 1, xs)
+                issue_encode(i + 1)
+            finish(i, ys)
+        torch.cuda.synchronize()
+        e2e_ms = 1e3 * (time.perf_counter() - t0) / n_pipe
+    h.sync()
+    assert all(torch.equal(x, hs) for x in hout), "pipelined end-to-end round trip failed"
+    nw = nw_last[0]
+    h2d = hp.numel() * 4 + hs.numel() * 4 + nw * 2 + ho[0].numel() * 8
+    d2h = 8 + ho[0].numel() * 8 + nw * 2 + hout[0].numel() * 4
+    e2e_ms, e2e_serial_ms = max_over_ranks([e2e_ms, e2e_serial_ms], device=dev)
 
     value = world * N / (ms_step * 1e-3) / 1e6
     plan = codec.decode_plan(S, h=h)
@@ -519,7 +587,8 @@ def run_fgmm(args):
         "gpu_launches": launches_per_step * args.steps,
         "wall_s_timed_region": t_wall,
         "e2e": {"value": world * N / (e2e_ms * 1e-3) / 1e6, "unit": "Msymbols/s", "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h},
+                "d2h_bytes_per_step": d2h, "pipeline_buffers": NB,
+                "serial_value": world * N / (e2e_serial_ms * 1e-3) / 1e6},
         "roofline": {"kernel": plan["kernel"], "lanes": plan["lanes"], "cluster": plan["cluster"],
                      "bound": "alu", "achieved": achieved, "peak": alu_peak,
                      "unit": "Tops/s (FP32 lane ops)", "frac": achieved / alu_peak,
