@@ -38,7 +38,7 @@ FP32_LANES_PER_SM = 128
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of
 # the decoder the plan names, from the ncu captures summarised under
 # profiles/; valid for each kernel as captured there (null otherwise).
-DECODE_TRAFFIC_BYTES = {"fgmm_dec_ws_kernel/16/4": 10791168}   # kernel / lanes / cluster
+DECODE_TRAFFIC_BYTES = {"fgmm_dec_ws_kernel/16/4/16": 10793472}   # "kernel/lanes/cluster/round0": bytes per launch
 
 
 def parse():
@@ -590,9 +590,10 @@ def run_fgmm(args):
                 "d2h_bytes_per_step": d2h, "pipeline_buffers": NB,
                 "serial_value": world * N / (e2e_serial_ms * 1e-3) / 1e6},
         "roofline": {"kernel": plan["kernel"], "lanes": plan["lanes"], "cluster": plan["cluster"],
+                     "round0": plan["round0"],
                      "bound": "alu", "achieved": achieved, "peak": alu_peak,
                      "unit": "Tops/s (FP32 lane ops)", "frac": achieved / alu_peak,
-                     "traffic": DECODE_TRAFFIC_BYTES.get(f'{plan["kernel"]}/{plan["lanes"]}/{plan["cluster"]}'),
+                     "traffic": DECODE_TRAFFIC_BYTES.get(f'{plan["kernel"]}/{plan["lanes"]}/{plan["cluster"]}/{plan["round0"]}'),
                      "peak_source": f"derived: {props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
                                     f"{sm_max:.0f} MHz"},
         "clocks": clk,

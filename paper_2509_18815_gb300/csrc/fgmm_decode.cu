@@ -11,20 +11,21 @@ void decode_config_auto(int64_t nseg, int num_sms, int* lanes, int* cluster, int
     // Enough segments to give every SM several warps: one lane per stream,
     // binary search (least work). Fewer: G lanes per stream, and a cluster of
     // CTAs per segment when the segments leave most SMs idle; the fewer the
-    // segments, the more lanes per stream. With more segments per SM the
-    // issue slots bind, and a 16-point first round (two streams per producer
-    // warp) beats a 32-point one. Measured on GB300 (152 SMs): 1-8 segments
-    // -> 32 lanes x clusters of 8; 16-32 -> 16 lanes x clusters of 4 with 32
-    // first-round points; 48-68 -> 16 lanes x clusters of 8, 16 points;
-    // 100 -> 16 lanes x clusters of 4, 16 points; 152 -> 8 lanes; 200-304 ->
-    // 4 lanes; 608 -> 1 lane.
+    // segments, the more lanes per stream. With 16 lanes per stream a
+    // 16-point first round (two streams per producer warp) halves the
+    // producers' issue slots. Measured on GB300 (152 SMs): 1-8 segments ->
+    // 32 lanes x clusters of 8; 16-32 -> 16 lanes x clusters of 4; 48 -> 16
+    // lanes x clusters of 8; 68-100 -> 16 lanes x clusters of 4; 152 -> 8
+    // lanes; 200-304 -> 4 lanes; 608 -> 1 lane.
     const int64_t sms = num_sms;
     *round0 = 32;
     if (nseg >= 4 * sms) { *lanes = 1; *cluster = 1; return; }
     if (nseg * 16 <= sms) { *lanes = 32; *cluster = 8; return; }
+    *round0 = 16;
     if (nseg * 4 <= sms) { *lanes = 16; *cluster = 4; return; }
-    if (nseg * 2 <= sms) { *lanes = 16; *cluster = 8; *round0 = 16; return; }
-    if (nseg * 3 <= sms * 2) { *lanes = 16; *cluster = 4; *round0 = 16; return; }
+    if (nseg * 8 <= sms * 3) { *lanes = 16; *cluster = 8; return; }
+    if (nseg * 3 <= sms * 2) { *lanes = 16; *cluster = 4; return; }
+    *round0 = 32;
     if (nseg * 4 <= sms * 5) { *lanes = 8; *cluster = 1; return; }
     *lanes = 4;
     *cluster = 1;

@@ -262,39 +262,37 @@ __global__ void __launch_bounds__(32 * (32 / CL / SPW + 32 / CL * R0 / 32))
             const int a = c > 0 ? m.lo + (c * W + R0 - 1) / R0 : m.lo;
             const int b = m.lo + ((min(c, R0 - 1) + 1) * W + R0 - 1) / R0;
             const int L = b - a;   // the symbol lies in [a, b); its L - 1 inner points are evaluated
-            if constexpr (kOneRound) {
+            // inner points a+1 .. b-1: a first round of up to LPS points,
+            // then (only when the interior exceeds the group) rounds of LPS
+            {
                 const bool valid = act && !esc && j < L - 1;
                 const uint32_t q1 = q_at<K>(m, min(a + 1 + j, m.hi + 1));
                 probes += valid;
-                const int c1 = __popc(__ballot_sync(kFull, valid && q1 <= slot) & gmask);
+                int c1 = __popc(__ballot_sync(kFull, valid && q1 <= slot) & gmask);
                 const uint32_t q1a = __shfl_sync(kFull, q1, gbase + (c1 > 0 ? c1 - 1 : 0));
-                const uint32_t q1b = __shfl_sync(kFull, q1, gbase + (c1 < LPS - 1 ? c1 : LPS - 1));
-                if (act && !esc) {
-                    s = a + c1;
-                    start = c1 > 0 ? q1a : qa0;
-                    freq = (c1 < L - 1 ? q1b : qb0) - start;
-                }
-            } else {
-                // rounds of LPS inner points
-                int c1 = 0;
-                uint32_t lastq = qa0, endq = qb0;
-                bool open = act && !esc && L > 1;
-                for (int base = 0; __any_sync(kFull, open); base += LPS) {
-                    const int idx = base + j;
-                    const bool valid = open && idx < L - 1;
-                    const uint32_t q1 = q_at<K>(m, min(a + 1 + idx, m.hi + 1));
-                    probes += valid;
-                    const int cnt = __popc(__ballot_sync(kFull, valid && q1 <= slot) & gmask);
-                    const uint32_t qlo = __shfl_sync(kFull, q1, gbase + (cnt > 0 ? cnt - 1 : 0));
-                    const uint32_t qhi = __shfl_sync(kFull, q1, gbase + (cnt < LPS ? cnt : LPS - 1));
-                    if (open) {
-                        c1 += cnt;
-                        if (cnt > 0) lastq = qlo;
-                        if (cnt < min(LPS, L - 1 - base)) {
-                            endq = qhi;
-                            open = false;
-                        } else if (base + LPS >= L - 1) {
-                            open = false;   // every inner point <= slot: the bracket's end bounds the symbol
+                const uint32_t q1b = __shfl_sync(kFull, q1, gbase + (c1 < LPS ? c1 : LPS - 1));
+                uint32_t lastq = c1 > 0 ? q1a : qa0;
+                uint32_t endq = c1 < min(LPS, L - 1) ? q1b : qb0;
+                if constexpr (!kOneRound) {
+                    // every first-round point <= slot and more inner points left
+                    bool open = act && !esc && c1 == LPS && L - 1 > LPS;
+                    for (int base = LPS; __any_sync(kFull, open); base += LPS) {
+                        const int idx = base + j;
+                        const bool v2 = open && idx < L - 1;
+                        const uint32_t q2 = q_at<K>(m, min(a + 1 + idx, m.hi + 1));
+                        probes += v2;
+                        const int cnt = __popc(__ballot_sync(kFull, v2 && q2 <= slot) & gmask);
+                        const uint32_t qlo = __shfl_sync(kFull, q2, gbase + (cnt > 0 ? cnt - 1 : 0));
+                        const uint32_t qhi = __shfl_sync(kFull, q2, gbase + (cnt < LPS ? cnt : LPS - 1));
+                        if (open) {
+                            c1 += cnt;
+                            if (cnt > 0) lastq = qlo;
+                            if (cnt < min(LPS, L - 1 - base)) {
+                                endq = qhi;
+                                open = false;
+                            } else if (base + LPS >= L - 1) {
+                                open = false;   // every inner point <= slot: the bracket's end bounds the symbol
+                            }
                         }
                     }
                 }

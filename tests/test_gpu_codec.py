@@ -252,7 +252,7 @@ def test_decode_plan_follows_segments_and_options():
     assert codec.decode_plan(many) == {"lanes": 1, "cluster": 1, "round0": 0, "kernel": "fgmm_dec_kernel"}
     assert codec.decode_plan(32) == {"lanes": 32, "cluster": 8, "round0": 32, "kernel": "fgmm_dec_ws_kernel"}
     few = 32 * max(1, sms // 4)
-    assert codec.decode_plan(few) == {"lanes": 16, "cluster": 4, "round0": 32, "kernel": "fgmm_dec_ws_kernel"}
+    assert codec.decode_plan(few) == {"lanes": 16, "cluster": 4, "round0": 16, "kernel": "fgmm_dec_ws_kernel"}
     try:
         _set_lanes(4)
         assert codec.decode_plan(few) == {"lanes": 4, "cluster": 1, "round0": 0, "kernel": "fgmm_dec_coop_kernel"}
@@ -274,8 +274,8 @@ def test_decode_plan_follows_segments_and_options():
         assert codec.decode_plan(few) == {"lanes": 32, "cluster": 1, "round0": 32, "kernel": "fgmm_dec_wide_kernel"}
         _set_lanes(0)
         _set_cluster(0)
-        _set_round0(16)
-        assert codec.decode_plan(few) == {"lanes": 16, "cluster": 4, "round0": 16, "kernel": "fgmm_dec_ws_kernel"}
+        _set_round0(32)
+        assert codec.decode_plan(few) == {"lanes": 16, "cluster": 4, "round0": 32, "kernel": "fgmm_dec_ws_kernel"}
         _set_lanes(8)
         _set_cluster(8)
         assert codec.decode_plan(few) == {"lanes": 8, "cluster": 8, "round0": 32, "kernel": "fgmm_dec_ws_kernel"}
