@@ -295,6 +295,13 @@ fgmm_status fgmm_decode_proposal(fgmm_handle *h, const fgmm_latent *lat, const v
  * automatic; G = 8 and 32 always take 32. The decoded symbols depend on
  * none of these. */
 enum { FGMM_OPT_DECODE_LANES = 1, FGMM_OPT_DECODE_CLUSTER = 2, FGMM_OPT_DECODE_ROUND0 = 3 };
+
+/* Test hook for the bounded waits of the warp-specialised decoder
+ * (FGMM_DEC_WS): stream `value` (0..31) of segment 0 posts no refill flags,
+ * so the other streams' waits run out; the decode then records
+ * FGMM_ERR_TIMEOUT, releases every wait through an abort flag, and returns.
+ * -1 (default) turns it off. The paper has no counterpart. */
+enum { FGMM_OPT_TEST_SILENT_STREAM = 4 };
 fgmm_status fgmm_set_option(fgmm_handle *h, int32_t option, int64_t value);
 
 /* The decoder fgmm_decode would run for S streams (S / 32 segments) under

@@ -623,6 +623,7 @@ fgmm_status fgmm_decode(fgmm_handle* h, const fgmm_latent* lat, const uint16_t* 
     decode_resolve(a.nseg, h->num_sms, h->decode_lanes, h->decode_cluster, h->decode_round0, &lanes, &cluster, &round0,
                    &kernel);
     a.r0 = round0 > 0 ? round0 : 32;
+    a.silent = h->test_silent_stream;
     cudaError_t e = launch_decode(a, lat->K, lat->dtype, lanes, cluster, st);
     return e == cudaSuccess ? FGMM_OK : cuda_fail(h, e, "fgmm_decode launch");
 }
@@ -654,6 +655,10 @@ fgmm_status fgmm_set_option(fgmm_handle* h, int32_t option, int64_t value)
         if (!(value == 0 || value == 1 || value == 2 || value == 4 || value == 8))
             return fail(h, FGMM_ERR_INVALID_ARG, "decode cluster must be 0 (auto), 1, 2, 4 or 8");
         h->decode_cluster = (int)value;
+        return FGMM_OK;
+    case FGMM_OPT_TEST_SILENT_STREAM:
+        if (value < -1 || value > 31) return fail(h, FGMM_ERR_INVALID_ARG, "silent stream must be -1 (off) or 0..31");
+        h->test_silent_stream = (int)value;
         return FGMM_OK;
     case FGMM_OPT_DECODE_ROUND0:
         if (!(value == 0 || value == 16 || value == 32))

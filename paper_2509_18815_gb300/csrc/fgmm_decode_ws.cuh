@@ -52,14 +52,16 @@ __device__ __forceinline__ void store_rank(uint32_t* local, uint32_t r, uint32_t
 // One refill exchange of the segment, called by every lane of every
 // consumer warp. Lane j (< CL) of the group of stream ws posts that stream's
 // flags (bit 0 refill, bit 1 escape) to CTA j. Returns, in lane q, stream
-// q's flags for exchange e.
+// q's flags for exchange e. posts is false only for the stream that the
+// FGMM_OPT_TEST_SILENT_STREAM hook silences, to make the others' waits run
+// out in a test.
 template <int CL>
 __device__ __forceinline__ uint32_t exchange(uint32_t* xflag, uint32_t* abort_flag, uint32_t e, int ws, int j,
-                                             int lane, uint32_t bits, int32_t* err)
+                                             int lane, uint32_t bits, int32_t* err, bool posts)
 {
     uint32_t* slot = xflag + (e & 1u) * 32;
     const uint32_t tag = e & 0x3fffffffu;
-    if (j < CL) store_rank(slot + ws, (uint32_t)j, (tag << 2) | bits);
+    if (posts && j < CL) store_rank(slot + ws, (uint32_t)j, (tag << 2) | bits);
     const volatile uint32_t* vs = slot;
     const volatile uint32_t* va = abort_flag;
     for (uint32_t spin = 0;; ++spin) {
@@ -105,7 +107,7 @@ template <int K, typename T, int CL, int SPW, int R0>
 __global__ void __launch_bounds__(32 * (32 / CL / SPW + 32 / CL * R0 / 32))
     fgmm_dec_ws_kernel(const T* __restrict__ params, int64_t N, int32_t S, int64_t T_steps,
                        const uint16_t* __restrict__ words, int64_t n_words, const int64_t* __restrict__ offsets,
-                       int32_t* __restrict__ out, int32_t* err, unsigned long long* stats, int mode)
+                       int32_t* __restrict__ out, int32_t* err, unsigned long long* stats, int mode, int silent)
 {
     constexpr int SPC = 32 / CL;              // streams per CTA
     constexpr int LPS = 32 / SPW;             // consumer lanes per stream
@@ -138,6 +140,7 @@ __global__ void __launch_bounds__(32 * (32 / CL / SPW + 32 / CL * R0 / 32))
     const uint32_t gmask = LPS == 32 ? kFull : (((1u << LPS) - 1u) << gbase);
     const int ptid = tid - 32 * CW;                   // producer thread index
     const int64_t g = blockIdx.x / CL;
+    const bool posts = !(g == 0 && ws == silent);
     const int64_t beg = offsets[g], end = offsets[g + 1];
     if (!(beg >= 0 && end <= n_words && end - beg >= 64)) {
         if (tid == 0 && rank == 0) set_error(err, kErrCorrupt);
@@ -312,7 +315,7 @@ __global__ void __launch_bounds__(32 * (32 / CL / SPW + 32 / CL * R0 / 32))
             const bool need = act && x < kL;
             const uint32_t below = bit - 1u;
             const uint32_t f =
-                exchange<CL>(xflag, abort_flag, e++, ws, j, lane, (need ? 1u : 0u) | (esc ? 2u : 0u), err);
+                exchange<CL>(xflag, abort_flag, e++, ws, j, lane, (need ? 1u : 0u) | (esc ? 2u : 0u), err, posts);
             const uint32_t M = __ballot_sync(kFull, f & 1u), E = __ballot_sync(kFull, f & 2u);
             ws_refill(x, need, M, below, wsrc, wbase, ptr, beg, bad);
             if (E) {   // the same in every stream of the segment
@@ -320,12 +323,12 @@ __global__ void __launch_bounds__(32 * (32 / CL / SPW + 32 / CL * R0 / 32))
                 if (esc) { hi16 = x & 0xffffu; x >>= 16; }
                 const bool n2 = esc && x < kL;
                 const uint32_t M2 =
-                    __ballot_sync(kFull, exchange<CL>(xflag, abort_flag, e++, ws, j, lane, n2 ? 1u : 0u, err) & 1u);
+                    __ballot_sync(kFull, exchange<CL>(xflag, abort_flag, e++, ws, j, lane, n2 ? 1u : 0u, err, posts) & 1u);
                 ws_refill(x, n2, M2, below, wsrc, wbase, ptr, beg, bad);
                 if (esc) { lo16 = x & 0xffffu; x >>= 16; }
                 const bool n3 = esc && x < kL;
                 const uint32_t M3 =
-                    __ballot_sync(kFull, exchange<CL>(xflag, abort_flag, e++, ws, j, lane, n3 ? 1u : 0u, err) & 1u);
+                    __ballot_sync(kFull, exchange<CL>(xflag, abort_flag, e++, ws, j, lane, n3 ? 1u : 0u, err, posts) & 1u);
                 ws_refill(x, n3, M3, below, wsrc, wbase, ptr, beg, bad);
                 if (esc) s = (int32_t)((hi16 << 16) | lo16);
             }
@@ -380,7 +383,7 @@ cudaError_t launch_ws(const DecodeArgs& a, cudaStream_t st)
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, kern, static_cast<const T*>(a.params), a.N, a.S, a.T, a.words, a.n_words,
-                              a.offsets, a.out, a.err, a.stats, mode);
+                              a.offsets, a.out, a.err, a.stats, mode, a.silent);
 }
 
 template <int K, typename T, int SPW, int R0>

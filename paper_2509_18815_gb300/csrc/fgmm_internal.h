@@ -20,6 +20,7 @@ struct fgmm_handle {
     int decode_lanes = 0;              // 0 = automatic; else lanes per stream (1, 2, 4, 8, 16, 32)
     int decode_cluster = 0;            // 0 = automatic; else CTAs per segment (1, 2, 4, 8)
     int decode_round0 = 0;             // 0 = automatic; else first-round points of the ws decoder (16, 32)
+    int test_silent_stream = -1;       // test hook: a stream of segment 0 that posts no refill flags
     std::string last_error;
 };
 
@@ -84,6 +85,7 @@ struct DecodeArgs {
     int32_t* err;
     unsigned long long* stats;
     int r0 = 32;                       // first-round points of the warp-specialised decoder
+    int silent = -1;                   // test hook: stream of segment 0 that posts no refill flags
 };
 void decode_config_auto(int64_t nseg, int num_sms, int* lanes, int* cluster, int* round0);
 // Warp-specialised decoder for fp32 / bf16 parameters: CL CTAs per segment,

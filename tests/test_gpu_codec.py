@@ -326,6 +326,39 @@ def test_decode_round0_widths_give_identical_symbols(case, CL, R0):
     np.testing.assert_array_equal(out, s)
 
 
+@pytest.mark.parametrize("G,CL", [(16, 4), (32, 8)])
+def test_decode_wait_times_out_and_recovers(G, CL):
+    """A stream that never posts its refill flags makes the other streams'
+    bounded waits run out: the warp-specialised decoder records
+    FGMM_ERR_TIMEOUT, every wait is released through the abort flag, the
+    kernel returns, and the next decode on the same context is exact. Four
+    steps of one segment bound the time even if the abort did not spread."""
+    codec = _codec()
+    from paper_2509_18815_gb300 import _abi
+    from paper_2509_18815_gb300._abi import FGMM_ERR_TIMEOUT, FgmmError
+    lat = synth.make_latent(1, 1, 128, 3, seed=506)
+    dp, ds = dev_params(lat.params), dev_i32(lat.symbols)
+    words, off = codec.encode(dp, ds, 32)
+    h = codec.handle()
+    try:
+        _set_lanes(G)
+        _set_cluster(CL)
+        assert codec.decode_plan(32)["kernel"] == "fgmm_dec_ws_kernel"
+        h.check(_abi.fgmm_set_option(h.ptr, _abi.FGMM_OPT_TEST_SILENT_STREAM, 5))
+        with pytest.raises(FgmmError) as e:
+            codec.decode(dp, words, off, 32)
+        assert e.value.status == FGMM_ERR_TIMEOUT
+        h.check(_abi.fgmm_set_option(h.ptr, _abi.FGMM_OPT_TEST_SILENT_STREAM, -1))
+        out = codec.decode(dp, words, off, 32).cpu().numpy()
+    finally:
+        h.check(_abi.fgmm_set_option(h.ptr, _abi.FGMM_OPT_TEST_SILENT_STREAM, -1))
+        _set_lanes(0)
+        _set_cluster(0)
+    np.testing.assert_array_equal(out, lat.symbols)
+    with pytest.raises(FgmmError):
+        h.check(_abi.fgmm_set_option(h.ptr, _abi.FGMM_OPT_TEST_SILENT_STREAM, 32))
+
+
 @pytest.mark.parametrize("G,CL", [(1, 1), (8, 1), (32, 1), (8, 4), (8, 8), (16, 2), (32, 8)])
 def test_decode_lanes_report_corruption(G, CL):
     codec = _codec()
