@@ -198,35 +198,79 @@ def batch_case(dev, h, out, name, lats, alu_peak_tops, hbm_gbs, reps=5, max_over
 
 
 def throughput_workloads(dev, alu_peak_tops, hbm_gbs, reps=5):
-    """Large workloads where the GPU can be filled: one 320x64x96 latent and a
-    batch of 64 uneven latents (both K = 3, autotuned stream counts, one
-    persistent launch per direction replayed from a CUDA graph), and the
-    learned proposal on 16 latents with scales up to 64. Inputs exceed L2."""
+    """Larger workloads: one 320x64x96 latent (K = 3 and 4, fp32 and bf16
+    parameters, autotuned stream count, FP64 rate audit), a batch of 64
+    uneven K = 3 latents (one persistent launch per direction replayed from a
+    CUDA graph), and the learned proposal on 16 latents with scales up to
+    64. Inputs exceed L2 or L2 is flushed between runs."""
     import numpy as np
     import torch
     from paper_2509_18815_gb300 import _abi, codec, synth
     h = codec.handle(dev)
     out = {}
 
-    # one latent: autotuned S, single-latent encode / decode (automatic
-    # decoder configuration)
+    # one latent of 320 x 64 x 96: autotuned S, single-latent encode / decode
+    # (automatic decoder configuration), K = 3 and 4, fp32 and bf16
+    # parameters, with the FP64 rate audit and the roofline fractions
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    for K3, bf16 in [(3, False), (4, False), (3, True), (4, True)]:
+        lat3 = synth.make_latent(320, 64, 96, K3, 1003)
+        if bf16:
+            dp3 = torch.from_numpy(synth.to_bf16_bits(lat3.params).view(np.int16)).to(dev).view(torch.bfloat16)
+        else:
+            dp3 = torch.from_numpy(lat3.params).to(dev)
+        ds3 = torch.from_numpy(lat3.symbols).to(dev)
+        S3 = codec.autotune([lat3.N], h=h)[0]
+        w3, o3 = codec.encode(dp3, ds3, S3, h=h)
+        out3 = torch.empty(lat3.N, dtype=torch.int32, device=dev)
+        codec.decode(dp3, w3, o3, S3, h=h, out=out3)
+        assert torch.equal(out3, ds3)
+        # binary-search CDF evaluations (one lane per stream) for the roofline
+        h.check(_abi.fgmm_set_option(h.ptr, _abi.FGMM_OPT_DECODE_LANES, 1))
+        codec.stats_enable(True, h); codec.stats_read(h)
+        codec.decode(dp3, w3, o3, S3, h=h, out=out3)
+        evals3, _ = codec.stats_read(h)
+        codec.stats_enable(False, h)
+        h.check(_abi.fgmm_set_option(h.ptr, _abi.FGMM_OPT_DECODE_LANES, 0))
+        te3 = _events_ms(lambda: codec.encode(dp3, ds3, S3, h=h, sync=False), reps, flush)
+        td3 = _events_ms(lambda: codec.decode(dp3, w3, o3, S3, h=h, out=out3, sync=False), reps, flush)
+        ideal3, coded3, maxerr3, nesc3 = codec.rate_audit(dp3, ds3, h)
+        N3 = lat3.N
+        ops_eval = 32 * K3 + 7
+        bytes_sym = 3 * K3 * (2 if bf16 else 4) + 4 + 16.0 * w3.numel() / N3 / 8.0
+        out[f"latent_320x64x96_k{K3}_{'bf16' if bf16 else 'fp32'}"] = {
+            "symbols": N3, "S": S3, "segments": S3 // 32, "decoder": codec.decode_plan(S3, h=h),
+            "encode_msym_s": N3 / te3 / 1e3, "decode_msym_s": N3 / td3 / 1e3, "ms_encode": te3, "ms_decode": td3,
+            "overhead_pct": 100.0 * (coded3 / ideal3 - 1.0), "max_cdf_err": maxerr3, "escapes": nesc3,
+            "container_overhead_pct": 100.0 * (16.0 * w3.numel() / coded3 - 1.0),
+            "encode_roofline": {"hbm_frac": N3 * bytes_sym / (te3 * 1e-3) / 1e9 / hbm_gbs,
+                                "alu_frac": 2 * N3 * ops_eval / (te3 * 1e-3) / 1e12 / alu_peak_tops},
+            "decode_roofline": {"alu_frac": evals3 * ops_eval / (td3 * 1e-3) / 1e12 / alu_peak_tops,
+                                "cdf_evals_per_symbol": evals3 / N3},
+        }
+        del dp3, ds3, w3, o3, out3
+    # the autotuner's trade-off on the K = 3 fp32 latent: a looser bound on
+    # the container overhead buys more streams
     lat3 = synth.make_latent(320, 64, 96, 3, 1003)
     dp3 = torch.from_numpy(lat3.params).to(dev)
     ds3 = torch.from_numpy(lat3.symbols).to(dev)
-    S3 = codec.autotune([lat3.N], h=h)[0]
-    w3, o3 = codec.encode(dp3, ds3, S3, h=h)
-    out3 = torch.empty(lat3.N, dtype=torch.int32, device=dev)
-    codec.decode(dp3, w3, o3, S3, h=h, out=out3)
-    assert torch.equal(out3, ds3)
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    te3 = _events_ms(lambda: codec.encode(dp3, ds3, S3, h=h, sync=False), reps, flush)
-    td3 = _events_ms(lambda: codec.decode(dp3, w3, o3, S3, h=h, out=out3, sync=False), reps, flush)
-    coded3 = codec.rate_audit(dp3, ds3, h)[1]
-    out["latent_320x64x96_k3"] = {"symbols": lat3.N, "S": S3, "segments": S3 // 32,
-                                  "encode_msym_s": lat3.N / te3 / 1e3, "decode_msym_s": lat3.N / td3 / 1e3,
-                                  "ms_encode": te3, "ms_decode": td3,
-                                  "container_overhead_pct": 100.0 * (16.0 * w3.numel() / coded3 - 1.0)}
-    del dp3, ds3, w3, o3, out3, flush
+    ideal3, _, _, _ = codec.rate_audit(dp3, ds3, h)
+    trade = []
+    for ovh in (0.01, 0.03, 0.1, 0.3):
+        S3 = codec.autotune([lat3.N], max_overhead=ovh, h=h)[0]
+        w3, o3 = codec.encode(dp3, ds3, S3, h=h)
+        out3 = torch.empty(lat3.N, dtype=torch.int32, device=dev)
+        codec.decode(dp3, w3, o3, S3, h=h, out=out3)
+        assert torch.equal(out3, ds3)
+        te3 = _events_ms(lambda: codec.encode(dp3, ds3, S3, h=h, sync=False), reps, flush)
+        td3 = _events_ms(lambda: codec.decode(dp3, w3, o3, S3, h=h, out=out3, sync=False), reps, flush)
+        trade.append({"max_overhead": ovh, "S": S3, "decoder": codec.decode_plan(S3, h=h),
+                      "bits_per_symbol": 16.0 * w3.numel() / lat3.N,
+                      "total_overhead_pct": 100.0 * (16.0 * w3.numel() / ideal3 - 1.0),
+                      "encode_msym_s": lat3.N / te3 / 1e3, "decode_msym_s": lat3.N / td3 / 1e3})
+        del w3, o3, out3
+    out["latent_320x64x96_k3_fp32_streams_tradeoff"] = trade
+    del dp3, ds3, flush
     shapes = synth.batch_shapes(64, seed=1004)
     batch_case(dev, h, out, "batch64_uneven_k3",
                [synth.make_latent(C, H, W, 3, 1004 + i) for i, (C, H, W) in enumerate(shapes)], alu_peak_tops,
