@@ -9,6 +9,7 @@ only compiles it with gcc and marshals numpy arrays through ctypes.
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes
 import os
 import subprocess
@@ -24,6 +25,7 @@ _lock = threading.Lock()
 _lib = None
 
 OK, INVALID, BAD_PARAMS, CAPACITY, CORRUPT = 0, 1, 2, 3, 4
+PHI_AS, PHI_LOGISTIC, PHI_POLYA = 0, 1, 2
 
 
 def build(force: bool = False) -> str:
@@ -73,6 +75,12 @@ def _load():
         lib.or_p64.argtypes = [P, ctypes.c_int, I64, I64, I32]
         lib.or_rate_audit.restype = ctypes.c_int
         lib.or_rate_audit.argtypes = [P, ctypes.c_int, I64, P, P]
+        lib.or_phi_v.restype = ctypes.c_float
+        lib.or_phi_v.argtypes = [ctypes.c_float, ctypes.c_int]
+        lib.or_phi_v_many.argtypes = [P, P, I64, ctypes.c_int]
+        lib.or_phi_v_grid_sweep.argtypes = [I64, I64, I64, ctypes.c_int, P]
+        lib.or_set_phi.restype = ctypes.c_int
+        lib.or_set_phi.argtypes = [ctypes.c_int]
         _lib = lib
         return lib
 
@@ -111,6 +119,34 @@ def phi_grid_sweep(i0: int, i1: int, err_stride: int = 1):
     out = np.zeros(3, dtype=np.float64)
     _load().or_phi_grid_sweep(i0, i1, err_stride, _p(out))
     return int(out[0]), float(out[1]), float(out[2])
+
+
+def phi_v(z, v: int) -> np.ndarray:
+    """Phi-hat of approximation v (PHI_AS, PHI_LOGISTIC, PHI_POLYA)."""
+    z = np.ascontiguousarray(z, dtype=np.float32)
+    out = np.empty_like(z)
+    _load().or_phi_v_many(_p(z), _p(out), z.size, v)
+    return out
+
+
+def phi_v_grid_sweep(i0: int, i1: int, err_stride: int, v: int):
+    """(decreases on the grid, max error vs v's formula in FP64, its z,
+    max error vs Phi, its z) over grid points i0 .. i1."""
+    out = np.zeros(5, dtype=np.float64)
+    _load().or_phi_v_grid_sweep(i0, i1, err_stride, v, _p(out))
+    return int(out[0]), float(out[1]), float(out[2]), float(out[3]), float(out[4])
+
+
+@contextlib.contextmanager
+def approximation(v: int):
+    """Codes (freqs, table, encode, decode, rate audit) with approximation v
+    inside the block; A&S again afterwards."""
+    if _load().or_set_phi(v) != OK:
+        raise ValueError(f"unknown approximation {v}")
+    try:
+        yield
+    finally:
+        _load().or_set_phi(PHI_AS)
 
 
 def mixcdf(params, n: int, b: float) -> float:

@@ -11,7 +11,9 @@
  *   - symbol s owns the mixture-CDF interval [F(s-1/2), F(s+1/2)), the
  *     per-symbol mass of the CDF table of Sec. II-C, Eqs. 4-5;
  *   - Phi is approximated by Abramowitz & Stegun 26.2.17 (Sec. III-B, Eq. 8)
- *     evaluated in FP32;
+ *     evaluated in FP32, or (selected by or_set_phi) by the logistic or the
+ *     Polya approximation (Sec. III-B), for the comparison of Sec. V,
+ *     Table II;
  *   - the CDF is quantised to 16-bit rANS frequencies on the fly for the one
  *     symbol being coded (Sec. III-A), coded with rANS (Sec. II-B, Eq. 3),
  *     and decoded by binary search over the same quantised CDF (Sec. III-A);
@@ -45,12 +47,16 @@
 #define OR_CAPACITY 3
 #define OR_CORRUPT 4
 
+#define OR_PHI_AS 0
+#define OR_PHI_LOGISTIC 1
+#define OR_PHI_POLYA 2
+
 /* ---------------------------------------------------------------------
- * exp(a) for a in [-72, 0] in FP32, written from the Cody-Waite method:
+ * exp(a) for a in [-72, 21] in FP32, written from the Cody-Waite method:
  * a = k ln2 + r with k = rint(a / ln2), ln2 split in a high part with a
  * short mantissa and a low part, |r| <= ln2/2; exp(r) by its Taylor series
  * to degree 7 (truncation < 2^-27 relative); scale by 2^k through the
- * exponent field (the result stays normal for a >= -72).
+ * exponent field (the result stays normal for -72 <= a <= 21).
  * ------------------------------------------------------------------- */
 float or_exp(float a)
 {
@@ -113,6 +119,60 @@ float or_phi(float z)
 }
 
 /* ---------------------------------------------------------------------
+ * The other two approximations of Sec. III-B, on the same clamp and grid:
+ * each returns the lower tail q = Phi-hat(-x) for x = |z| >= 0, and
+ * Phi-hat(z) = z >= 0 ? 1 - q : q.
+ *
+ * Logistic (Sec. III-B): Phi(x) ~ 1 / (1 + exp(-1.702 x)), so
+ *   q = 1 / (1 + exp(1.702 x)),
+ * one correctly rounded reciprocal of a non-decreasing quantity.
+ *
+ * Polya (Sec. III-B): Phi(x) ~ (1 + sqrt(1 - exp(-2 x^2 / pi))) / 2 for
+ * x >= 0. The paper prints exp(-x^2) inside the root; Polya's (1949) form
+ * has the factor 2/pi, which the approximation needs to stay within 0.003
+ * of Phi; that form is the reading taken here. The tail is evaluated
+ * without cancellation as
+ *   q = (1 - sqrt(1 - e)) / 2 = (e / 2) * (1 / (1 + sqrt(1 - e))),
+ *   e = exp(max(-(2/pi) x^2, -72)),
+ * a product of a non-increasing and a non-increasing factor.
+ * Both are monotone on the grid when exp is (checked exhaustively).
+ * ------------------------------------------------------------------- */
+static float logistic_tail(float x)
+{
+    float E = or_exp(1.702f * x);
+    return 1.0f / (1.0f + E);
+}
+
+static float polya_tail(float x)
+{
+    const float two_over_pi = 0x1.45f306p-1f;   /* float(2/pi) */
+    float a = fmaxf(-(two_over_pi * (x * x)), -72.0f);
+    float e = or_exp(a);
+    float s = sqrtf(1.0f - e);
+    return (0.5f * e) * (1.0f / (1.0f + s));
+}
+
+float or_phi_v(float z, int v)
+{
+    if (v == OR_PHI_AS) return or_phi(z);
+    float zc = fminf(fmaxf(z, -OR_ZC), OR_ZC);
+    float zs = rintf(zc * 0x1p22f) * 0x1p-22f;
+    float x = fabsf(zs);
+    float q = v == OR_PHI_LOGISTIC ? logistic_tail(x) : polya_tail(x);
+    return zs >= 0.0f ? 1.0f - q : q;
+}
+
+/* The approximation used by the coding functions below (A&S by default). */
+static int g_phi = OR_PHI_AS;
+
+int or_set_phi(int v)
+{
+    if (v < OR_PHI_AS || v > OR_PHI_POLYA) return OR_INVALID;
+    g_phi = v;
+    return OR_OK;
+}
+
+/* ---------------------------------------------------------------------
  * One symbol's mixture parameters, read from the planar layout
  * params[(c*K + k)*N + n], c = 0 (w), 1 (mu), 2 (sigma).
  * ------------------------------------------------------------------- */
@@ -157,7 +217,7 @@ float or_mixcdf_one(const or_mix *m, float b)
         float sp = sig_floor(m->sig[k]);
         float inv = 1.0f / sp;
         float z = (b - m->mu[k]) * inv;
-        acc = fmaf(m->w[k], or_phi(z), acc);
+        acc = fmaf(m->w[k], or_phi_v(z, g_phi), acc);
     }
     return acc;
 }
@@ -249,6 +309,42 @@ void or_phi_grid_sweep(int64_t i0, int64_t i1, int64_t err_stride, double *out)
     out[0] = viol;
     out[1] = maxerr;
     out[2] = zmax;
+}
+
+/* The sweep of or_phi_grid_sweep for approximation v, against v's own
+ * formula in FP64 (out[1], out[2]) and against Phi (out[3], out[4]):
+ * out[0] = decreases between consecutive grid points in [i0, i1]. */
+void or_phi_v_grid_sweep(int64_t i0, int64_t i1, int64_t err_stride, int v, double *out)
+{
+    double viol = 0.0, maxf = 0.0, zf = 0.0, maxg = 0.0, zg = 0.0;
+    float prev = or_phi_v((float)i0 * 0x1p-22f, v);
+    for (int64_t i = i0; i <= i1; ++i) {
+        float z = (float)i * 0x1p-22f;
+        float val = or_phi_v(z, v);
+        if (val < prev) viol += 1.0;
+        prev = val;
+        if (err_stride > 0 && (i - i0) % err_stride == 0) {
+            double x = (double)z, f;
+            if (v == OR_PHI_LOGISTIC) f = 1.0 / (1.0 + exp(-1.702 * x));
+            else if (v == OR_PHI_POLYA) {
+                double r = sqrt(1.0 - exp(-2.0 * x * x / 3.14159265358979323846));
+                f = x >= 0.0 ? 0.5 * (1.0 + r) : 0.5 * (1.0 - r);
+            } else f = 0.5 * erfc(-x / sqrt(2.0));
+            double ef = fabs((double)val - f), eg = fabs((double)val - 0.5 * erfc(-x / sqrt(2.0)));
+            if (ef > maxf) { maxf = ef; zf = x; }
+            if (eg > maxg) { maxg = eg; zg = x; }
+        }
+    }
+    out[0] = viol;
+    out[1] = maxf;
+    out[2] = zf;
+    out[3] = maxg;
+    out[4] = zg;
+}
+
+void or_phi_v_many(const float *z, float *out, int64_t n, int v)
+{
+    for (int64_t i = 0; i < n; ++i) out[i] = or_phi_v(z[i], v);
 }
 
 /* Grid sweep that returns the values themselves (for CPU/GPU bit checks). */
