@@ -302,6 +302,22 @@ enum { FGMM_OPT_DECODE_LANES = 1, FGMM_OPT_DECODE_CLUSTER = 2, FGMM_OPT_DECODE_R
  * FGMM_ERR_TIMEOUT, releases every wait through an abort flag, and returns.
  * -1 (default) turns it off. The paper has no counterpart. */
 enum { FGMM_OPT_TEST_SILENT_STREAM = 4 };
+
+/* FGMM_OPT_PHI selects the approximation of the Gaussian CDF in the coded
+ * quantised CDF (Sec. III-B; the comparison of Sec. V, Table II):
+ *   FGMM_PHI_AS        Abramowitz & Stegun 26.2.17 (default);
+ *   FGMM_PHI_LOGISTIC  1 / (1 + exp(-1.702 z));
+ *   FGMM_PHI_POLYA     (1 + sqrt(1 - exp(-2 z^2 / pi))) / 2 for z >= 0
+ *                      (Polya's form; mirrored for z < 0).
+ * All three are evaluated in FP32 on the clamp |z| <= 12 and the grid
+ * 2^-22 with a fixed operation order, so encoder and decoder agree bit for
+ * bit. A stream must be decoded with the approximation it was encoded
+ * with. Honoured by fgmm_phi, fgmm_phi_grid, fgmm_freqs, fgmm_encode,
+ * fgmm_decode (which then runs FGMM_DEC_LANE) and fgmm_rate_audit; the
+ * table coder, batches, the proposal and fgmm_encode_noalloc take A&S only
+ * and return FGMM_ERR_INVALID_ARG otherwise. */
+enum { FGMM_OPT_PHI = 5 };
+enum { FGMM_PHI_AS = 0, FGMM_PHI_LOGISTIC = 1, FGMM_PHI_POLYA = 2 };
 fgmm_status fgmm_set_option(fgmm_handle *h, int32_t option, int64_t value);
 
 /* The decoder fgmm_decode would run for S streams (S / 32 segments) under

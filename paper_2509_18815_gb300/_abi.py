@@ -29,6 +29,8 @@ FGMM_OPT_DECODE_LANES = 1
 FGMM_OPT_DECODE_CLUSTER = 2
 FGMM_OPT_DECODE_ROUND0 = 3
 FGMM_OPT_TEST_SILENT_STREAM = 4
+FGMM_OPT_PHI = 5
+FGMM_PHI_AS, FGMM_PHI_LOGISTIC, FGMM_PHI_POLYA = 0, 1, 2
 FGMM_DEC_LANE, FGMM_DEC_COOP, FGMM_DEC_WIDE, FGMM_DEC_WS = 0, 1, 2, 3
 DECODE_KERNELS = {FGMM_DEC_LANE: "fgmm_dec_kernel", FGMM_DEC_COOP: "fgmm_dec_coop_kernel",
                   FGMM_DEC_WIDE: "fgmm_dec_wide_kernel", FGMM_DEC_WS: "fgmm_dec_ws_kernel"}

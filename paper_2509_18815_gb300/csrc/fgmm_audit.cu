@@ -49,7 +49,7 @@ struct AuditPart {
     double ideal, coded, maxerr, nesc;
 };
 
-template <int K, typename T>
+template <int K, typename T, int PHI>
 __global__ void __launch_bounds__(kAuditThreads) fgmm_audit_kernel(const T* __restrict__ params, int64_t N,
                                                                    const int32_t* __restrict__ sym,
                                                                    AuditPart* __restrict__ parts, int32_t* err)
@@ -67,7 +67,7 @@ __global__ void __launch_bounds__(kAuditThreads) fgmm_audit_kernel(const T* __re
         }
         const int32_t s = __ldg(sym + n);
         uint32_t st, fr;
-        interval_of<K>(m, s, st, fr);
+        interval_of<K, PHI>(m, s, st, fr);
         const bool esc = st + fr == kM;
         // FP64 mass of the symbol under the exact mixture
         double p = 0.0;
@@ -83,10 +83,10 @@ __global__ void __launch_bounds__(kAuditThreads) fgmm_audit_kernel(const T* __re
         nesc += esc ? 1.0 : 0.0;
         // CDF error at the evaluated boundaries (j - 1/2)
         int j0 = esc ? m.hi + 1 : s + 1;
-        const double e0 = fabs((double)mix_cdf<K>(m, j0) - mix_cdf64<K>(w, mu, sp, (double)j0 - 0.5));
+        const double e0 = fabs((double)mix_cdf<K, PHI>(m, j0) - mix_cdf64<K>(w, mu, sp, (double)j0 - 0.5));
         maxerr = fmax(maxerr, e0);
         if (!esc && s > m.lo) {
-            const double e1 = fabs((double)mix_cdf<K>(m, s) - mix_cdf64<K>(w, mu, sp, (double)s - 0.5));
+            const double e1 = fabs((double)mix_cdf<K, PHI>(m, s) - mix_cdf64<K>(w, mu, sp, (double)s - 0.5));
             maxerr = fmax(maxerr, e1);
         }
     }
@@ -130,24 +130,32 @@ __global__ void __launch_bounds__(kAuditThreads) fgmm_audit_reduce_kernel(const 
     }
 }
 
-template <int K, typename T>
+template <int K, typename T, int PHI>
 void launch_audit_kt(const fgmm_latent* lat, const int32_t* sym, AuditPart* parts, int nblocks, int32_t* err,
                      cudaStream_t st)
 {
-    fgmm_audit_kernel<K, T><<<nblocks, kAuditThreads, 0, st>>>(static_cast<const T*>(lat->params), lat->N, sym, parts,
-                                                               err);
+    fgmm_audit_kernel<K, T, PHI><<<nblocks, kAuditThreads, 0, st>>>(static_cast<const T*>(lat->params), lat->N, sym,
+                                                                    parts, err);
 }
 
-template <typename T>
+template <typename T, int PHI>
 void launch_audit_t(const fgmm_latent* lat, const int32_t* sym, AuditPart* parts, int nblocks, int32_t* err,
                     cudaStream_t st)
 {
     switch (lat->K) {
-    case 1: launch_audit_kt<1, T>(lat, sym, parts, nblocks, err, st); break;
-    case 2: launch_audit_kt<2, T>(lat, sym, parts, nblocks, err, st); break;
-    case 3: launch_audit_kt<3, T>(lat, sym, parts, nblocks, err, st); break;
-    default: launch_audit_kt<4, T>(lat, sym, parts, nblocks, err, st); break;
+    case 1: launch_audit_kt<1, T, PHI>(lat, sym, parts, nblocks, err, st); break;
+    case 2: launch_audit_kt<2, T, PHI>(lat, sym, parts, nblocks, err, st); break;
+    case 3: launch_audit_kt<3, T, PHI>(lat, sym, parts, nblocks, err, st); break;
+    default: launch_audit_kt<4, T, PHI>(lat, sym, parts, nblocks, err, st); break;
     }
+}
+
+template <int PHI>
+void launch_audit_phi(const fgmm_latent* lat, const int32_t* sym, AuditPart* parts, int nblocks, int32_t* err,
+                      cudaStream_t st)
+{
+    if (lat->dtype == FGMM_DTYPE_BF16) launch_audit_t<__nv_bfloat16, PHI>(lat, sym, parts, nblocks, err, st);
+    else launch_audit_t<float, PHI>(lat, sym, parts, nblocks, err, st);
 }
 
 }  // namespace
@@ -165,8 +173,9 @@ extern "C" fgmm_status fgmm_rate_audit(fgmm_handle* h, const fgmm_latent* lat, c
     s = ws_reserve(h, sizeof(AuditPart) * (size_t)nb, st);
     if (s != FGMM_OK) return s;
     AuditPart* parts = static_cast<AuditPart*>(h->ws);
-    if (lat->dtype == FGMM_DTYPE_BF16) launch_audit_t<__nv_bfloat16>(lat, symbols, parts, (int)nb, h->d_err, st);
-    else launch_audit_t<float>(lat, symbols, parts, (int)nb, h->d_err, st);
+    if (h->phi == kPhiLogistic) launch_audit_phi<kPhiLogistic>(lat, symbols, parts, (int)nb, h->d_err, st);
+    else if (h->phi == kPhiPolya) launch_audit_phi<kPhiPolya>(lat, symbols, parts, (int)nb, h->d_err, st);
+    else launch_audit_phi<kPhiAS>(lat, symbols, parts, (int)nb, h->d_err, st);
     fgmm_audit_reduce_kernel<<<1, kAuditThreads, 0, st>>>(parts, (int)nb, out);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? FGMM_OK : cuda_fail(h, e, "fgmm_rate_audit launch");

@@ -336,6 +336,7 @@ fgmm_status fgmm_batch_create(fgmm_handle* h, const fgmm_batch_latent* lats, int
     if (!h || !out || n < 0 || (n > 0 && !lats) || !offsets || !n_words_out || words_cap < 0 ||
         (words_cap > 0 && !words))
         return fail(h, FGMM_ERR_INVALID_ARG, "fgmm_batch_create: bad arguments");
+    if (h->phi != FGMM_PHI_AS) return fail(h, FGMM_ERR_INVALID_ARG, "batches take FGMM_PHI_AS only");
     *out = nullptr;
     std::vector<int32_t> S(n);
     std::vector<int64_t> Ns(n);

@@ -31,10 +31,11 @@ constexpr uint32_t kFull = 0xffffffffu;
 // ---------------------------------------------------------------------------
 // Phi-hat evaluation (tests and sweeps).
 // ---------------------------------------------------------------------------
+template <int PHI>
 __global__ void phi_kernel(const float* __restrict__ z, float* __restrict__ out, int64_t n)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        out[i] = phi_hat(z[i]);
+        out[i] = phi_hat<PHI>(z[i]);
 }
 
 // Exhaustive check of recip() against __frcp_rn over [2^-125, 2^125]
@@ -74,16 +75,17 @@ __global__ void self_check_div_kernel(unsigned long long* bad)
     atomicAdd(bad, nb);
 }
 
+template <int PHI>
 __global__ void phi_grid_kernel(int64_t i0, float* __restrict__ out, int64_t n)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        out[i] = phi_hat(__fmul_rn((float)(i0 + i), 0x1p-22f));
+        out[i] = phi_hat<PHI>(__fmul_rn((float)(i0 + i), 0x1p-22f));
 }
 
 // ---------------------------------------------------------------------------
 // 1. Intervals: sf[n] = start | freq << 16.
 // ---------------------------------------------------------------------------
-template <int K, typename T>
+template <int K, typename T, int PHI>
 __global__ void __launch_bounds__(256) fgmm_interval_kernel(const T* __restrict__ params, int64_t N,
                                                             const int32_t* __restrict__ sym,
                                                             uint32_t* __restrict__ sf, int32_t* err)
@@ -92,7 +94,7 @@ __global__ void __launch_bounds__(256) fgmm_interval_kernel(const T* __restrict_
         Mix<K> m;
         if (!load_mix<K>(params, N, n, m)) set_error(err, kErrBadParams);
         uint32_t st, fr;
-        interval_of<K>(m, __ldg(sym + n), st, fr);
+        interval_of<K, PHI>(m, __ldg(sym + n), st, fr);
         sf[n] = st | (fr << 16);
     }
 }
@@ -302,33 +304,43 @@ inline int grid_for(int64_t n, int threads, int max_blocks)
     return (int)b;
 }
 
-template <int K, typename T>
+template <int K, typename T, int PHI>
 void launch_interval(const fgmm_latent* lat, const int32_t* sym, uint32_t* sf, int32_t* err, int sms,
                      cudaStream_t st)
 {
     if (lat->N == 0) return;
     const int threads = 256;
-    fgmm_interval_kernel<K, T><<<grid_for(lat->N, threads, sms * 16), threads, 0, st>>>(
+    fgmm_interval_kernel<K, T, PHI><<<grid_for(lat->N, threads, sms * 16), threads, 0, st>>>(
         static_cast<const T*>(lat->params), lat->N, sym, sf, err);
 }
 
-template <typename T>
+template <typename T, int PHI>
 void dispatch_interval(const fgmm_latent* lat, const int32_t* sym, uint32_t* sf, int32_t* err, int sms,
                        cudaStream_t st)
 {
     switch (lat->K) {
-    case 1: launch_interval<1, T>(lat, sym, sf, err, sms, st); break;
-    case 2: launch_interval<2, T>(lat, sym, sf, err, sms, st); break;
-    case 3: launch_interval<3, T>(lat, sym, sf, err, sms, st); break;
-    default: launch_interval<4, T>(lat, sym, sf, err, sms, st); break;
+    case 1: launch_interval<1, T, PHI>(lat, sym, sf, err, sms, st); break;
+    case 2: launch_interval<2, T, PHI>(lat, sym, sf, err, sms, st); break;
+    case 3: launch_interval<3, T, PHI>(lat, sym, sf, err, sms, st); break;
+    default: launch_interval<4, T, PHI>(lat, sym, sf, err, sms, st); break;
     }
 }
 
-void launch_interval_any(const fgmm_latent* lat, const int32_t* sym, uint32_t* sf, int32_t* err, int sms,
+template <int PHI>
+void launch_interval_phi(const fgmm_latent* lat, const int32_t* sym, uint32_t* sf, int32_t* err, int sms,
                          cudaStream_t st)
 {
-    if (lat->dtype == FGMM_DTYPE_BF16) dispatch_interval<__nv_bfloat16>(lat, sym, sf, err, sms, st);
-    else dispatch_interval<float>(lat, sym, sf, err, sms, st);
+    if (lat->dtype == FGMM_DTYPE_BF16) dispatch_interval<__nv_bfloat16, PHI>(lat, sym, sf, err, sms, st);
+    else dispatch_interval<float, PHI>(lat, sym, sf, err, sms, st);
+}
+
+// Intervals with approximation phi (kPhiAS, kPhiLogistic, kPhiPolya).
+void launch_interval_any(const fgmm_latent* lat, const int32_t* sym, uint32_t* sf, int32_t* err, int sms,
+                         cudaStream_t st, int phi = kPhiAS)
+{
+    if (phi == kPhiLogistic) launch_interval_phi<kPhiLogistic>(lat, sym, sf, err, sms, st);
+    else if (phi == kPhiPolya) launch_interval_phi<kPhiPolya>(lat, sym, sf, err, sms, st);
+    else launch_interval_phi<kPhiAS>(lat, sym, sf, err, sms, st);
 }
 
 // Warps per block for the per-segment kernels: one warp per block while the
@@ -527,7 +539,10 @@ fgmm_status fgmm_phi(fgmm_handle* h, const float* z, float* out, int64_t n, void
     if (n < 0 || (n > 0 && (!z || !out))) return fail(h, FGMM_ERR_INVALID_ARG, "fgmm_phi: bad arguments");
     if (n == 0) return FGMM_OK;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    phi_kernel<<<grid_for(n, 256, h->num_sms * 16), 256, 0, st>>>(z, out, n);
+    const int g = grid_for(n, 256, h->num_sms * 16);
+    if (h->phi == kPhiLogistic) phi_kernel<kPhiLogistic><<<g, 256, 0, st>>>(z, out, n);
+    else if (h->phi == kPhiPolya) phi_kernel<kPhiPolya><<<g, 256, 0, st>>>(z, out, n);
+    else phi_kernel<kPhiAS><<<g, 256, 0, st>>>(z, out, n);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? FGMM_OK : cuda_fail(h, e, "fgmm_phi launch");
 }
@@ -539,7 +554,10 @@ fgmm_status fgmm_phi_grid(fgmm_handle* h, int64_t i0, float* out, int64_t n, voi
         return fail(h, FGMM_ERR_INVALID_ARG, "fgmm_phi_grid: bad arguments");
     if (n == 0) return FGMM_OK;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    phi_grid_kernel<<<grid_for(n, 256, h->num_sms * 16), 256, 0, st>>>(i0, out, n);
+    const int g = grid_for(n, 256, h->num_sms * 16);
+    if (h->phi == kPhiLogistic) phi_grid_kernel<kPhiLogistic><<<g, 256, 0, st>>>(i0, out, n);
+    else if (h->phi == kPhiPolya) phi_grid_kernel<kPhiPolya><<<g, 256, 0, st>>>(i0, out, n);
+    else phi_grid_kernel<kPhiAS><<<g, 256, 0, st>>>(i0, out, n);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? FGMM_OK : cuda_fail(h, e, "fgmm_phi_grid launch");
 }
@@ -568,7 +586,7 @@ fgmm_status fgmm_freqs(fgmm_handle* h, const fgmm_latent* lat, const int32_t* sy
     if (s != FGMM_OK) return s;
     if (lat->N > 0 && (!symbols || !sf)) return fail(h, FGMM_ERR_INVALID_ARG, "fgmm_freqs: NULL buffer");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    launch_interval_any(lat, symbols, sf, h->d_err, h->num_sms, st);
+    launch_interval_any(lat, symbols, sf, h->d_err, h->num_sms, st, h->phi);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? FGMM_OK : cuda_fail(h, e, "fgmm_freqs launch");
 }
@@ -592,7 +610,7 @@ fgmm_status fgmm_encode(fgmm_handle* h, const fgmm_latent* lat, const int32_t* s
     EncodeWs ws;
     s = encode_reserve(h, lat->N, S, st, &ws);
     if (s != FGMM_OK) return s;
-    launch_interval_any(lat, symbols, ws.sf, h->d_err, h->num_sms, st);
+    launch_interval_any(lat, symbols, ws.sf, h->d_err, h->num_sms, st, h->phi);
     encode_from_intervals(ws, symbols, lat->N, S, words, words_cap, offsets, n_words_out, h->d_err, h->num_sms, st);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? FGMM_OK : cuda_fail(h, e, "fgmm_encode launch");
@@ -620,9 +638,10 @@ fgmm_status fgmm_decode(fgmm_handle* h, const fgmm_latent* lat, const uint16_t* 
     a.err = h->d_err;
     a.stats = h->stats_on ? h->d_stats : nullptr;
     int lanes = 1, cluster = 1, round0 = 0, kernel = 0;
-    decode_resolve(a.nseg, h->num_sms, h->decode_lanes, h->decode_cluster, h->decode_round0, &lanes, &cluster, &round0,
-                   &kernel);
+    decode_resolve(a.nseg, h->num_sms, h->decode_lanes, h->decode_cluster, h->decode_round0, h->phi, &lanes,
+                   &cluster, &round0, &kernel);
     a.r0 = round0 > 0 ? round0 : 32;
+    a.phi = h->phi;
     a.silent = h->test_silent_stream;
     cudaError_t e = launch_decode(a, lat->K, lat->dtype, lanes, cluster, st);
     return e == cudaSuccess ? FGMM_OK : cuda_fail(h, e, "fgmm_decode launch");
@@ -633,8 +652,8 @@ fgmm_status fgmm_decode_plan(fgmm_handle* h, int32_t S, int32_t* out)
     if (!h || !out) return fail(h, FGMM_ERR_INVALID_ARG, "fgmm_decode_plan: NULL argument");
     if (S <= 0 || S % 32 != 0) return fail(h, FGMM_ERR_INVALID_ARG, "S must be a positive multiple of 32");
     int lanes = 1, cluster = 1, round0 = 0, kernel = 0;
-    decode_resolve(S / 32, h->num_sms, h->decode_lanes, h->decode_cluster, h->decode_round0, &lanes, &cluster,
-                   &round0, &kernel);
+    decode_resolve(S / 32, h->num_sms, h->decode_lanes, h->decode_cluster, h->decode_round0, h->phi, &lanes,
+                   &cluster, &round0, &kernel);
     out[0] = lanes;
     out[1] = cluster;
     out[2] = kernel;
@@ -655,6 +674,11 @@ fgmm_status fgmm_set_option(fgmm_handle* h, int32_t option, int64_t value)
         if (!(value == 0 || value == 1 || value == 2 || value == 4 || value == 8))
             return fail(h, FGMM_ERR_INVALID_ARG, "decode cluster must be 0 (auto), 1, 2, 4 or 8");
         h->decode_cluster = (int)value;
+        return FGMM_OK;
+    case FGMM_OPT_PHI:
+        if (!(value == FGMM_PHI_AS || value == FGMM_PHI_LOGISTIC || value == FGMM_PHI_POLYA))
+            return fail(h, FGMM_ERR_INVALID_ARG, "approximation must be FGMM_PHI_AS, _LOGISTIC or _POLYA");
+        h->phi = (int)value;
         return FGMM_OK;
     case FGMM_OPT_TEST_SILENT_STREAM:
         if (value < -1 || value > 31) return fail(h, FGMM_ERR_INVALID_ARG, "silent stream must be -1 (off) or 0..31");

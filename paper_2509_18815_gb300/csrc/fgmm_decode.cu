@@ -31,9 +31,16 @@ void decode_config_auto(int64_t nseg, int num_sms, int* lanes, int* cluster, int
     *cluster = 1;
 }
 
-void decode_resolve(int64_t nseg, int num_sms, int opt_lanes, int opt_cluster, int opt_round0, int* lanes,
+void decode_resolve(int64_t nseg, int num_sms, int opt_lanes, int opt_cluster, int opt_round0, int phi, int* lanes,
                     int* cluster, int* round0, int* kernel)
 {
+    if (phi != FGMM_PHI_AS) {   // the other approximations run on the lane decoder only
+        *lanes = 1;
+        *cluster = 1;
+        *round0 = 0;
+        *kernel = FGMM_DEC_LANE;
+        return;
+    }
     int G = 1, CL = 1, R0 = 32;
     decode_config_auto(nseg, num_sms, &G, &CL, &R0);
     if (opt_lanes > 0) {

@@ -44,7 +44,7 @@ constexpr uint32_t kFull = 0xffffffffu;
 // ---------------------------------------------------------------------------
 // G = 1: binary search, one lane per stream.
 // ---------------------------------------------------------------------------
-template <int K, typename T>
+template <int K, typename T, int PHI>
 __global__ void __launch_bounds__(32) fgmm_dec_kernel(const T* __restrict__ params, int64_t N, int32_t S,
                                                        int64_t T_steps, const uint16_t* __restrict__ words,
                                                        int64_t n_words, const int64_t* __restrict__ offsets,
@@ -58,7 +58,7 @@ __global__ void __launch_bounds__(32) fgmm_dec_kernel(const T* __restrict__ para
         if ((threadIdx.x & 31) == 0) set_error(err, kErrCorrupt);
         return;
     }
-    dec_segment<K, T>(params, N, S, T_steps, g, words, beg, end, out, err, stats);
+    dec_segment<K, T, PHI>(params, N, S, T_steps, g, words, beg, end, out, err, stats);
 }
 
 // ---------------------------------------------------------------------------
@@ -717,9 +717,10 @@ cudaError_t launch_k(const DecodeArgs& a, int G, int CL, cudaStream_t st)
     default: {
         const int threads = 32;   // one warp (segment) per block: segments spread over all SMs
         const int64_t blocks = (a.nseg * 32 + threads - 1) / threads;
-        fgmm_dec_kernel<K, T><<<(unsigned)blocks, threads, 0, st>>>(static_cast<const T*>(a.params), a.N, a.S, a.T,
-                                                                    a.words, a.n_words, a.offsets, a.nseg, a.out,
-                                                                    a.err, a.stats);
+        auto kern = a.phi == kPhiLogistic ? fgmm_dec_kernel<K, T, kPhiLogistic>
+                    : (a.phi == kPhiPolya ? fgmm_dec_kernel<K, T, kPhiPolya> : fgmm_dec_kernel<K, T, kPhiAS>);
+        kern<<<(unsigned)blocks, threads, 0, st>>>(static_cast<const T*>(a.params), a.N, a.S, a.T, a.words, a.n_words,
+                                                   a.offsets, a.nseg, a.out, a.err, a.stats);
         return cudaGetLastError();
     }
     }

@@ -115,9 +115,41 @@ __device__ __forceinline__ float phi_hat_s(float zs)
     return zs >= 0.0f ? __fsub_rn(1.0f, q) : q;
 }
 
+// The other two approximations of Sec. III-B (Sec. V, Table II), on the
+// same clamp, grid and mirror; each gives the lower tail q = Phi-hat(-x):
+//   logistic: Phi(x) ~ 1 / (1 + exp(-1.702 x)),   q = 1 / (1 + exp(1.702 x));
+//   Polya:    Phi(x) ~ (1 + sqrt(1 - exp(-2 x^2 / pi))) / 2 (Polya's form,
+//             with the factor 2/pi), q = (e/2) (1 / (1 + sqrt(1 - e))),
+//             e = exp(max(-(2/pi) x^2, -72)).
+// With x = r 2^-22 the constants are scaled by powers of two (1.702 2^-22,
+// 2/pi 2^-44), which changes no rounding. Both are monotone on the grid.
+enum { kPhiAS = 0, kPhiLogistic = 1, kPhiPolya = 2 };
+
+template <int PHI>
+__device__ __forceinline__ float phi_hat_v(float zs)
+{
+    if constexpr (PHI == kPhiAS) {
+        return phi_hat_s(zs);
+    } else {
+        const float r = rintf(fminf(fabsf(zs), 0x1.8p25f));   // |z| 2^22 on the grid, clamp 12
+        float q;
+        if constexpr (PHI == kPhiLogistic) {
+            const float E = exp_cw(__fmul_rn(0x1.b3b646p-22f, r));   // fp32(1.702) 2^-22
+            q = recip(__fadd_rn(1.0f, E));
+        } else {
+            const float a = fmaxf(-__fmul_rn(0x1.45f306p-45f, __fmul_rn(r, r)), -72.0f);   // fp32(2/pi) 2^-44
+            const float e = exp_cw(a);
+            const float sq = __fsqrt_rn(__fsub_rn(1.0f, e));
+            q = __fmul_rn(__fmul_rn(0.5f, e), recip(__fadd_rn(1.0f, sq)));
+        }
+        return zs >= 0.0f ? __fsub_rn(1.0f, q) : q;
+    }
+}
+
 // Phi-hat(z) for any z: z * 2^22 is exact (or overflows to +-inf, which the
 // clamp maps to 12 as it does z).
-__device__ __forceinline__ float phi_hat(float z) { return phi_hat_s(__fmul_rn(z, 0x1p22f)); }
+template <int PHI = kPhiAS>
+__device__ __forceinline__ float phi_hat(float z) { return phi_hat_v<PHI>(__fmul_rn(z, 0x1p22f)); }
 
 // Parameter loads from the planar [3][K][N] layout.
 __device__ __forceinline__ float load_param(const float* p, int64_t i) { return __ldg(p + i); }
@@ -178,7 +210,7 @@ __device__ __forceinline__ bool load_mix(const T* params, int64_t N, int64_t n, 
 }
 
 // F-hat(j - 1/2) = sum_k w_k Phi-hat((b - mu_k) / sigma'_k), k ascending.
-template <int K>
+template <int K, int PHI = kPhiAS>
 __device__ __forceinline__ float mix_cdf(const Mix<K>& m, int j)
 {
     const float b = __fsub_rn((float)j, 0.5f);
@@ -186,32 +218,32 @@ __device__ __forceinline__ float mix_cdf(const Mix<K>& m, int j)
 #pragma unroll
     for (int k = 0; k < K; ++k) {
         const float zs = __fmul_rn(__fsub_rn(b, m.mu[k]), m.isg[k]);   // z 2^22
-        acc = __fmaf_rn(m.w[k], phi_hat_s(zs), acc);
+        acc = __fmaf_rn(m.w[k], phi_hat_v<PHI>(zs), acc);
     }
     return acc;
 }
 
 // Quantised CDF Q(j) for lo < j <= hi+1: (j - lo) + floor(T' min(F-hat, 1)).
 // Q(lo) = 0 is not evaluated.
-template <int K>
+template <int K, int PHI = kPhiAS>
 __device__ __forceinline__ uint32_t q_at(const Mix<K>& m, int j)
 {
-    const float v = fminf(mix_cdf<K>(m, j), 1.0f);
+    const float v = fminf(mix_cdf<K, PHI>(m, j), 1.0f);
     return (uint32_t)(j - m.lo) + __float2uint_rd(__fmul_rn(m.tp, v));   // floor of a value >= 0
 }
 
 // The rANS interval of symbol s. Escape (s outside [lo, hi]) gets
 // [Q(hi+1), 2^16); an interval is an escape iff start + freq == 2^16.
-template <int K>
+template <int K, int PHI = kPhiAS>
 __device__ __forceinline__ void interval_of(const Mix<K>& m, int32_t s, uint32_t& start, uint32_t& freq)
 {
     if (s >= m.lo && s <= m.hi) {
-        const uint32_t a = (s == m.lo) ? 0u : q_at<K>(m, s);
-        const uint32_t b = q_at<K>(m, s + 1);
+        const uint32_t a = (s == m.lo) ? 0u : q_at<K, PHI>(m, s);
+        const uint32_t b = q_at<K, PHI>(m, s + 1);
         start = a;
         freq = b - a;
     } else {
-        const uint32_t e = q_at<K>(m, m.hi + 1);
+        const uint32_t e = q_at<K, PHI>(m, m.hi + 1);
         start = e;
         freq = kM - e;
     }
@@ -223,7 +255,7 @@ __device__ __forceinline__ void interval_of(const Mix<K>& m, int32_t s, uint32_t
 // escape interval (never evaluated), so landing on hi + 1 means escape and no
 // separate escape test is needed. Returns true for the escape slot.
 // `probes` counts CDF evaluations (ceil or floor of log2(W + 1)).
-template <int K>
+template <int K, int PHI = kPhiAS>
 __device__ __forceinline__ bool search_slot(const Mix<K>& m, uint32_t slot, int32_t& s, uint32_t& start,
                                             uint32_t& freq, int& probes)
 {
@@ -231,7 +263,7 @@ __device__ __forceinline__ bool search_slot(const Mix<K>& m, uint32_t slot, int3
     uint32_t qa = 0, qb = kM;
     while (b - a > 1) {
         const int mid = a + ((b - a) >> 1);
-        const uint32_t qm = q_at<K>(m, mid);
+        const uint32_t qm = q_at<K, PHI>(m, mid);
         ++probes;
         if (qm <= slot) { a = mid; qa = qm; }
         else { b = mid; qb = qm; }

@@ -21,6 +21,7 @@ struct fgmm_handle {
     int decode_cluster = 0;            // 0 = automatic; else CTAs per segment (1, 2, 4, 8)
     int decode_round0 = 0;             // 0 = automatic; else first-round points of the ws decoder (16, 32)
     int test_silent_stream = -1;       // test hook: a stream of segment 0 that posts no refill flags
+    int phi = 0;                       // Phi approximation (FGMM_PHI_*)
     std::string last_error;
 };
 
@@ -86,6 +87,7 @@ struct DecodeArgs {
     unsigned long long* stats;
     int r0 = 32;                       // first-round points of the warp-specialised decoder
     int silent = -1;                   // test hook: stream of segment 0 that posts no refill flags
+    int phi = 0;                       // Phi approximation (FGMM_PHI_*); non-A&S only on the lane decoder
 };
 void decode_config_auto(int64_t nseg, int num_sms, int* lanes, int* cluster, int* round0);
 // Warp-specialised decoder for fp32 / bf16 parameters: CL CTAs per segment,
@@ -94,7 +96,7 @@ cudaError_t launch_ws_f32(const DecodeArgs& a, int K, int CL, int SPW, cudaStrea
 cudaError_t launch_ws_bf16(const DecodeArgs& a, int K, int CL, int SPW, cudaStream_t st);
 // Final decoder choice: automatic plan, then the handle's options, then the
 // limits of each kernel (clusters only with G >= 2, at most 4 below G = 32).
-void decode_resolve(int64_t nseg, int num_sms, int opt_lanes, int opt_cluster, int opt_round0, int* lanes,
+void decode_resolve(int64_t nseg, int num_sms, int opt_lanes, int opt_cluster, int opt_round0, int phi, int* lanes,
                     int* cluster, int* round0, int* kernel);
 cudaError_t launch_decode(const DecodeArgs& a, int K, int dtype, int lanes, int cluster, cudaStream_t st);
 

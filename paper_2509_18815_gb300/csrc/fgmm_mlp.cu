@@ -561,6 +561,7 @@ fgmm_status fgmm_mlp_data(fgmm_handle* h, const fgmm_latent* lat, const int32_t*
     fgmm_status s = check_latent(h, lat);
     if (s != FGMM_OK) return s;
     if (lat->K != 3) return fail(h, FGMM_ERR_INVALID_ARG, "the proposal network takes K = 3 mixtures");
+    if (h->phi != FGMM_PHI_AS) return fail(h, FGMM_ERR_INVALID_ARG, "the proposal path takes FGMM_PHI_AS only");
     if (lat->N > 0 && (!symbols || !uniforms || !X || !target))
         return fail(h, FGMM_ERR_INVALID_ARG, "fgmm_mlp_data: NULL buffer");
     if (lat->N == 0) return FGMM_OK;
@@ -647,6 +648,7 @@ fgmm_status fgmm_decode_proposal(fgmm_handle* h, const fgmm_latent* lat, const v
     fgmm_status s = check_latent(h, lat);
     if (s != FGMM_OK) return s;
     if (lat->K != 3) return fail(h, FGMM_ERR_INVALID_ARG, "the proposal network takes K = 3 mixtures");
+    if (h->phi != FGMM_PHI_AS) return fail(h, FGMM_ERR_INVALID_ARG, "the proposal path takes FGMM_PHI_AS only");
     if (S <= 0 || S % 32 != 0) return fail(h, FGMM_ERR_INVALID_ARG, "S must be a positive multiple of 32");
     if (!packed || !offsets || n_words < 0 || (n_words > 0 && !words) || (lat->N > 0 && !symbols_out))
         return fail(h, FGMM_ERR_INVALID_ARG, "fgmm_decode_proposal: NULL buffer");

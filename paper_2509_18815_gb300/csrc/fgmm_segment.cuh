@@ -144,7 +144,7 @@ __device__ __forceinline__ void enc_segment_fused(const T* __restrict__ params, 
 }
 
 // Decode of segment g whose words are words[beg, end). Symbols go to out[n].
-template <int K, typename T>
+template <int K, typename T, int PHI = kPhiAS>
 __device__ __forceinline__ void dec_segment(const T* __restrict__ params, int64_t N, int32_t S, int64_t T_steps,
                                             int64_t g, const uint16_t* __restrict__ words, int64_t beg, int64_t end,
                                             int32_t* __restrict__ out, int32_t* err, unsigned long long* stats)
@@ -173,7 +173,7 @@ __device__ __forceinline__ void dec_segment(const T* __restrict__ params, int64_
             badp |= !mix_from_params<K>(cur, m);
             const uint32_t slot = x & 0xffffu;
             uint32_t st, fr;
-            esc = search_slot<K>(m, slot, s, st, fr, probes);
+            esc = search_slot<K, PHI>(m, slot, s, st, fr, probes);
             x = fr * (x >> 16) + slot - st;
         }
         refill_warp(x, act, words, ptr, beg, bad, lt);

@@ -170,6 +170,7 @@ fgmm_status fgmm_table_build(fgmm_handle* h, const fgmm_latent* lat, uint16_t* t
 {
     fgmm_status s = check_latent(h, lat);
     if (s != FGMM_OK) return s;
+    if (h->phi != FGMM_PHI_AS) return fail(h, FGMM_ERR_INVALID_ARG, "the table coder takes FGMM_PHI_AS only");
     if (lat->N > 0 && !table) return fail(h, FGMM_ERR_INVALID_ARG, "fgmm_table_build: NULL table");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     launch_build(lat, table, h->d_err, h->num_sms, st);
@@ -183,6 +184,7 @@ fgmm_status fgmm_table_encode(fgmm_handle* h, const fgmm_latent* lat, const int3
 {
     fgmm_status s = check_latent(h, lat);
     if (s != FGMM_OK) return s;
+    if (h->phi != FGMM_PHI_AS) return fail(h, FGMM_ERR_INVALID_ARG, "the table coder takes FGMM_PHI_AS only");
     if (S <= 0 || S % 32 != 0) return fail(h, FGMM_ERR_INVALID_ARG, "S must be a positive multiple of 32");
     if (!offsets || !n_words_out || words_cap < 0 || (words_cap > 0 && !words) ||
         (lat->N > 0 && (!symbols || !table)))
@@ -207,6 +209,7 @@ fgmm_status fgmm_table_decode(fgmm_handle* h, const fgmm_latent* lat, uint16_t* 
 {
     fgmm_status s = check_latent(h, lat);
     if (s != FGMM_OK) return s;
+    if (h->phi != FGMM_PHI_AS) return fail(h, FGMM_ERR_INVALID_ARG, "the table coder takes FGMM_PHI_AS only");
     if (S <= 0 || S % 32 != 0) return fail(h, FGMM_ERR_INVALID_ARG, "S must be a positive multiple of 32");
     if (!offsets || n_words < 0 || (n_words > 0 && !words) || (lat->N > 0 && (!symbols_out || !table)))
         return fail(h, FGMM_ERR_INVALID_ARG, "fgmm_table_decode: NULL buffer");
