@@ -478,6 +478,48 @@ def run_fgmm(args):
     ms_tenc, ms_tdec = statistics.median(te), statistics.median(td)
     del table
 
+    # Sec. V, Table II on this latent: the three approximations of Phi, each
+    # coding with its own quantised CDF; time with the lane decoder (the one
+    # decoder every approximation runs on), rate against the FP64 mixture
+    phi_rows = {}
+    words_v = torch.empty(cap, dtype=torch.int16, device=dev)
+    off_v = torch.empty(S // 32 + 1, dtype=torch.int64, device=dev)
+    tot_v = torch.empty(1, dtype=torch.int64, device=dev)
+    out_v = torch.empty(N, dtype=torch.int32, device=dev)
+    for name, v in (("a_and_s", _abi.FGMM_PHI_AS), ("logistic", _abi.FGMM_PHI_LOGISTIC),
+                    ("polya", _abi.FGMM_PHI_POLYA)):
+        h.check(_abi.fgmm_set_option(h.ptr, _abi.FGMM_OPT_PHI, v))
+        h.check(_abi.fgmm_set_option(h.ptr, _abi.FGMM_OPT_DECODE_LANES, 1))
+
+        def venc():
+            h.check(_abi.fgmm_encode(h.ptr, L, ds.data_ptr(), S, words_v.data_ptr(), cap, off_v.data_ptr(),
+                                     tot_v.data_ptr(), sptr))
+
+        def vdec():
+            h.check(_abi.fgmm_decode(h.ptr, L, words_v.data_ptr(), cap, off_v.data_ptr(), S, out_v.data_ptr(), sptr))
+
+        venc(); vdec(); h.sync()
+        assert torch.equal(out_v, ds), name
+        te_v, td_v = [], []
+        for i in range(tsteps + 2):
+            flush.fill_(i & 0xff)
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e0.record(stream); venc(); e1.record(stream); vdec(); e2.record(stream)
+            torch.cuda.synchronize()
+            if i >= 2:
+                te_v.append(e0.elapsed_time(e1)); td_v.append(e1.elapsed_time(e2))
+        h.sync()
+        aud_v = torch.empty(4, dtype=torch.float64, device=dev)
+        h.check(_abi.fgmm_rate_audit(h.ptr, L, ds.data_ptr(), aud_v.data_ptr(), sptr))
+        h.sync()
+        iv, cv, ev, _ = aud_v.cpu().tolist()
+        phi_rows[name] = {"ms_encode": statistics.median(te_v), "ms_decode_lane": statistics.median(td_v),
+                          "bits_per_symbol": cv / N, "overhead_pct": 100.0 * (cv / iv - 1.0), "max_cdf_err": ev}
+    phi_rows["exact_fp64_bits_per_symbol"] = iv / N
+    h.check(_abi.fgmm_set_option(h.ptr, _abi.FGMM_OPT_PHI, _abi.FGMM_PHI_AS))
+    h.check(_abi.fgmm_set_option(h.ptr, _abi.FGMM_OPT_DECODE_LANES, args.decode_lanes))
+    del words_v, off_v, tot_v, out_v
+
     # rate: FP64 audit on the GPU
     aud = torch.empty(4, dtype=torch.float64, device=dev)
     h.check(_abi.fgmm_rate_audit(h.ptr, L, ds.data_ptr(), aud.data_ptr(), sptr))
@@ -624,6 +666,7 @@ def run_fgmm(args):
                         "ms_encode": ms_tenc, "ms_decode": ms_tdec, "table_mb": N * 512 * 2 / 1e6,
                         "encode_speedup_table_free": ms_tenc / ms_enc, "decode_speedup_table_free": ms_tdec / ms_dec,
                         "stream_identical": True},
+        "phi_approximations": phi_rows,
         "rate": {"ideal_bits_per_symbol": ideal_bits / N, "coded_bits_per_symbol": coded_bits / N,
                  "overhead_pct": 100.0 * (coded_bits / ideal_bits - 1.0),
                  "container_overhead_pct": 100.0 * (16.0 * n_words / coded_bits - 1.0),
