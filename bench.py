@@ -293,18 +293,19 @@ def throughput_workloads(dev, alu_peak_tops, hbm_gbs, reps=5):
     del X, t
     lats = [synth.make_latent(320, 64, 96, 3, seed=1105 + i, sigma_max=64.0) for i in range(16)]
     S_all = codec.autotune([l.N for l in lats], h=h)
-    res = {"plain": [0.0, 0, 0, 0], "proposal": [0.0, 0, 0, 0]}
+    res = {"plain": [0.0, 0, 0, 0], "proposal": [0.0, 0, 0, 0], "analytic": [0.0, 0, 0, 0]}
     for l, S in zip(lats, S_all):
         dp = torch.from_numpy(l.params).to(dev)
         ds = torch.from_numpy(l.symbols).to(dev)
         words, off = codec.encode(dp, ds, S, h=h)
         o = torch.empty(l.N, dtype=torch.int32, device=dev)
-        for kind in ("plain", "proposal"):
+        for kind in ("plain", "proposal", "analytic"):
             if kind == "plain":
                 h.check(_abi.fgmm_set_option(h.ptr, _abi.FGMM_OPT_DECODE_LANES, 1))
                 fn = lambda: codec.decode(dp, words, off, S, h=h, out=o, sync=False)
             else:
-                fn = lambda: codec.decode_proposal(dp, words, off, S, P, h=h, out=o, sync=False)
+                Pk = P if kind == "proposal" else None
+                fn = lambda: codec.decode_proposal(dp, words, off, S, Pk, h=h, out=o, sync=False)
             codec.stats_enable(True, h); codec.stats_read(h)
             fn(); h.sync()
             ev, nd, hits = codec.stats_read(h, with_hits=True)
@@ -321,6 +322,9 @@ def throughput_workloads(dev, alu_peak_tops, hbm_gbs, reps=5):
         "plain_cdf_evals_per_symbol": res["plain"][1] / res["plain"][2],
         "proposal_cdf_evals_per_symbol": res["proposal"][1] / res["proposal"][2],
         "proposal_hit_rate": res["proposal"][3] / res["proposal"][2],
+        "analytic_decode_msym_s": res["analytic"][2] / res["analytic"][0] / 1e3,
+        "analytic_cdf_evals_per_symbol": res["analytic"][1] / res["analytic"][2],
+        "analytic_hit_rate": res["analytic"][3] / res["analytic"][2],
         "streams_per_latent": S_all[0],
     }
     return out

@@ -278,7 +278,10 @@ fgmm_status fgmm_mlp_pack(fgmm_handle *h, const float *theta, void *packed, void
 fgmm_status fgmm_mlp_forward(fgmm_handle *h, const float *X, int64_t B, const void *packed, float *y, void *stream);
 
 /* fgmm_decode with the proposal (K = 3 latents); same arguments plus the
- * packed network. */
+ * packed network. packed == NULL selects the analytic proposal instead: the
+ * inverse of the logistic approximation of Phi (Sec. III-B) on the
+ * component of largest weight, mu + sigma' ln(u / (1 - u)) / 1.702 with
+ * u = (slot + 1/2) / 2^16 -- a comparison point for the network. */
 fgmm_status fgmm_decode_proposal(fgmm_handle *h, const fgmm_latent *lat, const void *packed, const uint16_t *words,
                                  int64_t n_words, const int64_t *offsets, int32_t S, int32_t *symbols_out,
                                  void *stream);

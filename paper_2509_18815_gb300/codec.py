@@ -411,13 +411,16 @@ def mlp_forward(X, packed, h: Handle | None = None):
 
 
 def decode_proposal(params, words, offsets, S, packed, h: Handle | None = None, out=None, sync: bool = True):
+    """Proposal-bracketed decode; packed=None uses the analytic proposal (the
+    logistic inverse on the dominant component) instead of the network."""
     h = h or handle(params.device)
     lat = latent(params)
     if out is None:
         out = torch.empty(lat.N, dtype=torch.int32, device=params.device)
     words = words.contiguous()
     offsets = offsets.to(torch.int64).contiguous()
-    h.check(_abi.fgmm_decode_proposal(h.ptr, ctypes.byref(lat), _ptr(packed), _ptr(words), words.numel(),
+    h.check(_abi.fgmm_decode_proposal(h.ptr, ctypes.byref(lat), _ptr(packed) if packed is not None else None,
+                                      _ptr(words), words.numel(),
                                       _ptr(offsets), S, _ptr(out), _stream()))
     if sync:
         h.sync()

@@ -386,9 +386,12 @@ __global__ void __launch_bounds__(128) mlp_forward_kernel(const float* __restric
 }
 
 // ---------------------------------------------------------------------------
-// Proposal-bracketed decoder (K = 3), one warp per segment.
+// Proposal-bracketed decoder (K = 3), one warp per segment. The guess comes
+// from the network, or (ANALYTIC) from the inverse of the logistic
+// approximation of Phi (Sec. III-B) on the component of largest weight:
+// mu + sigma' ln(u / (1 - u)) / 1.702, u = (slot + 1/2) / 2^16.
 // ---------------------------------------------------------------------------
-template <typename T>
+template <typename T, bool ANALYTIC>
 __global__ void __launch_bounds__(32) fgmm_dec_prop_kernel(const T* __restrict__ params, int64_t N, int32_t S,
                                                             int64_t T_steps, const uint16_t* __restrict__ words,
                                                             int64_t n_words, const int64_t* __restrict__ offsets,
@@ -398,9 +401,11 @@ __global__ void __launch_bounds__(32) fgmm_dec_prop_kernel(const T* __restrict__
 {
     __shared__ MlpPacked P;
     __shared__ uint32_t xs[1][32 * 12];
-    for (int i = threadIdx.x; i < (int)(sizeof(MlpPacked) / 4); i += blockDim.x)
-        reinterpret_cast<uint32_t*>(&P)[i] = reinterpret_cast<const uint32_t*>(Pg)[i];
-    __syncthreads();
+    if constexpr (!ANALYTIC) {
+        for (int i = threadIdx.x; i < (int)(sizeof(MlpPacked) / 4); i += blockDim.x)
+            reinterpret_cast<uint32_t*>(&P)[i] = reinterpret_cast<const uint32_t*>(Pg)[i];
+        __syncthreads();
+    }
     const int wib = 0;
     const int64_t g = blockIdx.x;   // one warp (segment) per block: segments spread over all SMs
     const int lane = threadIdx.x & 31;
@@ -430,14 +435,23 @@ __global__ void __launch_bounds__(32) fgmm_dec_prop_kernel(const T* __restrict__
             mix_from_params<3>(cur, m);
         }
         const uint32_t slot = x & 0xffffu;
-        float f[kIn], m0, s0;
-        features<true>(&cur.v[0], &cur.v[3], &cur.v[6], slot, f, m0, s0);
-        const float yv = mlp_warp_forward(&P, f, xs[wib]);   // all lanes take part
+        float guess;
+        if constexpr (ANALYTIC) {
+            int kd = cur.v[1] > cur.v[0] ? 1 : 0;
+            kd = cur.v[2] > cur.v[kd] ? 2 : kd;
+            const float u = ((float)slot + 0.5f) * 0x1p-16f;
+            guess = cur.v[3 + kd] + fmaxf(cur.v[6 + kd], kSigmaMin) * (__logf(__fdividef(u, 1.0f - u)) * (1.0f / 1.702f));
+        } else {
+            float f[kIn], m0, s0;
+            features<true>(&cur.v[0], &cur.v[3], &cur.v[6], slot, f, m0, s0);
+            const float yv = mlp_warp_forward(&P, f, xs[wib]);   // all lanes take part
+            guess = fmaf(s0, yv, m0);
+        }
         int32_t s = 0;
         bool esc = false;
         if (act_l) {
             ++decoded;
-            float gf = rintf(fmaf(s0, yv, m0));
+            float gf = rintf(guess);
             gf = isfinite(gf) ? fminf(fmaxf(gf, (float)m.lo), (float)m.hi) : (float)m.lo;
             const int gi = (int)gf;
             const uint32_t qg = gi == m.lo ? 0u : q_at<3>(m, gi);
@@ -650,21 +664,22 @@ fgmm_status fgmm_decode_proposal(fgmm_handle* h, const fgmm_latent* lat, const v
     if (lat->K != 3) return fail(h, FGMM_ERR_INVALID_ARG, "the proposal network takes K = 3 mixtures");
     if (h->phi != FGMM_PHI_AS) return fail(h, FGMM_ERR_INVALID_ARG, "the proposal path takes FGMM_PHI_AS only");
     if (S <= 0 || S % 32 != 0) return fail(h, FGMM_ERR_INVALID_ARG, "S must be a positive multiple of 32");
-    if (!packed || !offsets || n_words < 0 || (n_words > 0 && !words) || (lat->N > 0 && !symbols_out))
+    if (!offsets || n_words < 0 || (n_words > 0 && !words) || (lat->N > 0 && !symbols_out))
         return fail(h, FGMM_ERR_INVALID_ARG, "fgmm_decode_proposal: NULL buffer");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int64_t nseg = S / 32, T = steps_of(lat->N, S);
     const int64_t blocks = nseg;
     unsigned long long* stats = h->stats_on ? h->d_stats : nullptr;
     const MlpPacked* P = static_cast<const MlpPacked*>(packed);
-    if (lat->dtype == FGMM_DTYPE_BF16)
-        fgmm_dec_prop_kernel<__nv_bfloat16><<<(unsigned)blocks, 32, 0, st>>>(
-            static_cast<const __nv_bfloat16*>(lat->params), lat->N, S, T, words, n_words, offsets, nseg, P,
-            symbols_out, h->d_err, stats);
-    else
-        fgmm_dec_prop_kernel<float><<<(unsigned)blocks, 32, 0, st>>>(static_cast<const float*>(lat->params), lat->N,
-                                                                       S, T, words, n_words, offsets, nseg, P,
-                                                                       symbols_out, h->d_err, stats);
+    if (lat->dtype == FGMM_DTYPE_BF16) {
+        auto kern = P ? fgmm_dec_prop_kernel<__nv_bfloat16, false> : fgmm_dec_prop_kernel<__nv_bfloat16, true>;
+        kern<<<(unsigned)blocks, 32, 0, st>>>(static_cast<const __nv_bfloat16*>(lat->params), lat->N, S, T, words,
+                                              n_words, offsets, nseg, P, symbols_out, h->d_err, stats);
+    } else {
+        auto kern = P ? fgmm_dec_prop_kernel<float, false> : fgmm_dec_prop_kernel<float, true>;
+        kern<<<(unsigned)blocks, 32, 0, st>>>(static_cast<const float*>(lat->params), lat->N, S, T, words, n_words,
+                                              offsets, nseg, P, symbols_out, h->d_err, stats);
+    }
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? FGMM_OK : cuda_fail(h, e, "fgmm_decode_proposal launch");
 }

@@ -132,6 +132,36 @@ def test_proposal_decode_is_exact_for_any_weights(kind):
         np.testing.assert_array_equal(out, lat.symbols)
 
 
+def test_analytic_proposal_decodes_exactly_and_saves_evaluations():
+    """The analytic proposal (packed network absent: logistic inverse on the
+    dominant component) decodes exactly, also with escapes, and needs fewer
+    CDF evaluations per symbol than plain binary search on latents with
+    scales up to 64."""
+    codec = _codec()
+    from paper_2509_18815_gb300 import _abi
+    lat = synth.make_latent(16, 32, 32, 3, seed=906, sigma_max=64.0, escape_stress=0.003)
+    dp, ds = dev_params(lat.params), dev_i32(lat.symbols)
+    for S in (32, 256):
+        words, off = codec.encode(dp, ds, S)
+        np.testing.assert_array_equal(codec.decode_proposal(dp, words, off, S, None).cpu().numpy(), lat.symbols)
+    h = codec.handle()
+    codec.stats_enable(True)
+    codec.stats_read(with_hits=True)
+    h.check(_abi.fgmm_set_option(h.ptr, _abi.FGMM_OPT_DECODE_LANES, 1))
+    try:
+        codec.decode(dp, words, off, 256)
+    finally:
+        h.check(_abi.fgmm_set_option(h.ptr, _abi.FGMM_OPT_DECODE_LANES, 0))
+    ev_plain, n_plain, _ = codec.stats_read(with_hits=True)
+    codec.decode_proposal(dp, words, off, 256, None)
+    ev_an, n_an, hits = codec.stats_read(with_hits=True)
+    codec.stats_enable(False)
+    assert n_plain == n_an == lat.N
+    print(f"plain {ev_plain / n_plain:.3f} evals/sym; analytic {ev_an / n_an:.3f} evals/sym, "
+          f"hit rate {hits / n_an:.3f}")
+    assert ev_an < ev_plain
+
+
 def test_proposal_reports_corruption():
     codec = _codec()
     from paper_2509_18815_gb300._abi import FGMM_ERR_CORRUPT, FgmmError
