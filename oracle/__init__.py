@@ -81,6 +81,9 @@ def _load():
         lib.or_phi_v_grid_sweep.argtypes = [I64, I64, I64, ctypes.c_int, P]
         lib.or_set_phi.restype = ctypes.c_int
         lib.or_set_phi.argtypes = [ctypes.c_int]
+        lib.or_gsm_levels.argtypes = [P]
+        lib.or_gsm_transform.restype = ctypes.c_int
+        lib.or_gsm_transform.argtypes = [P, I64, P, P, P, P]
         _lib = lib
         return lib
 
@@ -147,6 +150,30 @@ def approximation(v: int):
         yield
     finally:
         _load().or_set_phi(PHI_AS)
+
+
+def gsm_levels() -> np.ndarray:
+    """The 64 scale levels of the Gaussian single model (fp32)."""
+    out = np.empty(64, np.float32)
+    _load().or_gsm_levels(_p(out))
+    return out
+
+
+def gsm_transform(params, symbols):
+    """GSM parameters [3, 1, N] (w ignored) and symbols -> (K = 1 parameters
+    (1, 0, level), residuals y - rint(mu), level indices): the GSM coder is
+    the K = 1 coder on these."""
+    p = _params(params)
+    assert p.shape[1] == 1, "the Gaussian single model has K = 1"
+    N = p.shape[2]
+    s = np.ascontiguousarray(symbols, dtype=np.int32)
+    po = np.empty_like(p)
+    r = np.empty(N, np.int32)
+    li = np.empty(N, np.int32)
+    st = _load().or_gsm_transform(_p(p), N, _p(s), _p(po), _p(r), _p(li))
+    if st != OK:
+        raise ValueError(f"oracle gsm status {st}")
+    return po, r, li
 
 
 def mixcdf(params, n: int, b: float) -> float:
