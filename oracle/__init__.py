@@ -82,8 +82,8 @@ def _load():
         lib.or_set_phi.restype = ctypes.c_int
         lib.or_set_phi.argtypes = [ctypes.c_int]
         lib.or_gsm_levels.argtypes = [P]
-        lib.or_gsm_transform.restype = ctypes.c_int
-        lib.or_gsm_transform.argtypes = [P, I64, P, P, P, P]
+        lib.or_gsm_params.restype = ctypes.c_int
+        lib.or_gsm_params.argtypes = [P, ctypes.c_int, P, I64, P, P]
         _lib = lib
         return lib
 
@@ -159,21 +159,20 @@ def gsm_levels() -> np.ndarray:
     return out
 
 
-def gsm_transform(params, symbols):
-    """GSM parameters [3, 1, N] (w ignored) and symbols -> (K = 1 parameters
-    (1, 0, level), residuals y - rint(mu), level indices): the GSM coder is
-    the K = 1 coder on these."""
-    p = _params(params)
-    assert p.shape[1] == 1, "the Gaussian single model has K = 1"
-    N = p.shape[2]
-    s = np.ascontiguousarray(symbols, dtype=np.int32)
-    po = np.empty_like(p)
-    r = np.empty(N, np.int32)
+def gsm_params(scales, levels=None):
+    """Scales [N] -> (K = 1 parameters [3, 1, N] = (1, 0, level of the
+    scale), level indices). The GSM coder codes the residual symbols with
+    the K = 1 coder on these parameters. levels default to gsm_levels()."""
+    sg = np.ascontiguousarray(scales, dtype=np.float32).ravel()
+    lv = gsm_levels() if levels is None else np.ascontiguousarray(levels, dtype=np.float32)
+    assert 1 <= lv.size <= 64
+    N = sg.size
+    po = np.empty((3, 1, N), np.float32)
     li = np.empty(N, np.int32)
-    st = _load().or_gsm_transform(_p(p), N, _p(s), _p(po), _p(r), _p(li))
+    st = _load().or_gsm_params(_p(lv), lv.size, _p(sg), N, _p(po), _p(li))
     if st != OK:
         raise ValueError(f"oracle gsm status {st}")
-    return po, r, li
+    return po, li
 
 
 def mixcdf(params, n: int, b: float) -> float:

@@ -681,17 +681,18 @@ int or_rate_audit(const float *params, int K, int64_t N, const int32_t *sym, dou
 
 /* ---------------------------------------------------------------------
  * Gaussian single model with pre-built tables (the scheme of Sec. II-C
- * that the paper attributes to CompressAI, its GSM anchor): symbol y with
- * mean mu and scale sigma is shifted by the mean and its scale is
- * quantised to one of 64 levels spaced evenly in log between 0.11 and 256,
- * so that only 64 CDF tables exist and can be built ahead of time.
- * Readings: the shift is by the integer m = rint(mu) (mu clamped to
- * +-2^24) so that r = y - m is an integer and y = r + m is exact (both mod
- * 2^32); the level is the smallest one >= sigma (the last one above 256);
- * level i = float(exp(ln 0.11 + i (ln 256 - ln 0.11) / 63)) in FP64; each
- * level's table is this coder's quantised CDF of N(0, level). The GSM coder
- * is then exactly this file's K = 1 coder on w = 1, mu = 0, sigma = level,
- * symbol r: or_gsm_transform produces those parameters and symbols.
+ * that the paper attributes to CompressAI, its GSM anchor). The quantiser
+ * shifts the latent by its mean, so the coder receives the integer
+ * residual q and only the scale sigma: q is coded with N(0, sigma). The
+ * scale is quantised to one of a fixed set of levels (by default 64 spaced
+ * evenly in log between 0.11 and 256), so only one CDF table per level
+ * exists and all can be built ahead of time.
+ * Readings: the level of sigma is the smallest level >= sigma among the
+ * first L - 1, else the last; default level i = float(exp(ln 0.11 +
+ * i (ln 256 - ln 0.11) / 63)) in FP64; each level's table is this coder's
+ * quantised CDF of N(0, level) (the same window, escape and 0.11 scale
+ * floor). The GSM coder is then exactly this file's K = 1 coder on w = 1,
+ * mu = 0, sigma = level: or_gsm_params produces those parameters.
  * ------------------------------------------------------------------- */
 void or_gsm_levels(float *lv)
 {
@@ -699,32 +700,20 @@ void or_gsm_levels(float *lv)
     for (int i = 0; i < 64; ++i) lv[i] = (float)exp(a + (b - a) * (double)i / 63.0);
 }
 
-static int gsm_level(const float *lv, float sigma)
+/* Scales sigma[N] and levels lv[L] -> K = 1 parameters [3][1][N] =
+ * (1, 0, level) and level indices (level_idx may be NULL). Returns
+ * OR_BAD_PARAMS for a scale that is not finite and > 0. */
+int or_gsm_params(const float *lv, int L, const float *sigma, int64_t N, float *params_out, int32_t *level_idx)
 {
-    for (int i = 0; i < 63; ++i)
-        if (sigma <= lv[i]) return i;
-    return 63;
-}
-
-/* params [3][1][N] (w ignored) and symbols y -> K = 1 parameters
- * (1, 0, level) and residuals r = y - rint(mu); level_idx[n] receives the
- * level. Returns OR_BAD_PARAMS for a non-finite mean or a scale that is not
- * finite and > 0. */
-int or_gsm_transform(const float *params, int64_t N, const int32_t *sym, float *params_out, int32_t *r_out,
-                     int32_t *level_idx)
-{
-    float lv[64];
-    or_gsm_levels(lv);
     for (int64_t n = 0; n < N; ++n) {
-        float mu = params[1 * N + n], sg = params[2 * N + n];
-        if (!isfinite(mu) || !isfinite(sg) || !(sg > 0.0f)) return OR_BAD_PARAMS;
-        float mc = fminf(fmaxf(mu, -16777216.0f), 16777216.0f);
-        int32_t m = (int32_t)rintf(mc);
-        int i = gsm_level(lv, sg);
+        const float sg = sigma[n];
+        if (!isfinite(sg) || !(sg > 0.0f)) return OR_BAD_PARAMS;
+        int i = L - 1;
+        for (int j = 0; j < L - 1; ++j)
+            if (sg <= lv[j]) { i = j; break; }
         params_out[0 * N + n] = 1.0f;
         params_out[1 * N + n] = 0.0f;
         params_out[2 * N + n] = lv[i];
-        r_out[n] = (int32_t)((uint32_t)sym[n] - (uint32_t)m);
         if (level_idx) level_idx[n] = i;
     }
     return OR_OK;

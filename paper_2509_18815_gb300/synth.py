@@ -18,6 +18,11 @@ which needs trained weights and images that are not available):
            the CompressAI scale table the paper describes in Sec. II-B)
   symbol = round-half-even(mu_c + sigma_c * N(0, 1)), c ~ Categorical(w)
 No clipping: values outside the coder's window are legal (escape path).
+
+The Gaussian single model's coder receives the quantiser's mean-shifted
+residual and the scale only (Sec. II-C); its inputs (make_gsm_latent) are
+  sigma  = exp(U[ln 0.11, ln sigma_max])
+  q      = round-half-even(sigma * N(0, 1))   (= round(y - mu), y ~ N(mu, sigma))
 """
 from __future__ import annotations
 
@@ -78,6 +83,36 @@ def make_latent(C: int, H: int, W: int, K: int, seed: int,
         sym[m] = np.where(pick, big, near).astype(np.int32)
     params = np.stack([w, mu, sigma], axis=0)
     return Latent(params=np.ascontiguousarray(params), symbols=sym, shape=(C, H, W), seed=seed)
+
+
+@dataclass
+class GsmLatent:
+    scales: np.ndarray      # float32 [N]
+    symbols: np.ndarray     # int32 [N], the mean-shifted residuals q
+    shape: tuple
+    seed: int
+
+    @property
+    def N(self) -> int:
+        return int(self.symbols.shape[0])
+
+
+def make_gsm_latent(C: int, H: int, W: int, seed: int, sigma_max: float = 16.0,
+                    escape_stress: float = 0.0) -> GsmLatent:
+    """Inputs of the Gaussian single model's coder: scales and residuals
+    (module docstring). escape_stress as in make_latent."""
+    rng = np.random.default_rng(seed)
+    N = C * H * W
+    sigma = np.exp(rng.uniform(math.log(SIGMA_MIN), math.log(sigma_max), N)).astype(np.float32)
+    q = np.rint(sigma.astype(np.float64) * rng.standard_normal(N)).astype(np.int64).astype(np.int32)
+    if escape_stress > 0.0 and N > 0:
+        m = rng.random(N) < escape_stress
+        nsel = int(m.sum())
+        big = rng.integers(-2**31, 2**31 - 1, nsel, dtype=np.int64, endpoint=True)
+        near = rng.integers(256, 4000, nsel) * rng.choice([-1, 1], nsel)
+        pick = rng.random(nsel) < 0.5
+        q[m] = np.where(pick, big, near).astype(np.int32)
+    return GsmLatent(scales=sigma, symbols=q, shape=(C, H, W), seed=seed)
 
 
 def to_bf16_bits(x: np.ndarray) -> np.ndarray:
