@@ -167,6 +167,62 @@ fgmm_status fgmm_table_decode(fgmm_handle *h, const fgmm_latent *lat, uint16_t *
                               int64_t n_words, const int64_t *offsets, int32_t S, int32_t *symbols_out,
                               void *stream);
 
+/* ---- Gaussian single model with pre-built tables (Sec. II-C) ------------
+ * The scheme that makes the GSM cheap: the quantiser has already shifted
+ * each latent by its mean, so the coder receives the integer residual q and
+ * the scale sigma only and codes q with N(0, sigma); sigma is quantised to
+ * the smallest of L increasing levels at or above it (the last level above
+ * them all; by default 64 levels spaced evenly in log between 0.11 and 256),
+ * so one quantised-CDF row per level, built once, serves every symbol.
+ * A level's row is this library's quantised CDF of N(0, level) (K = 1, same
+ * window, escape slot and 0.11 scale floor, the handle's FGMM_OPT_PHI at
+ * build time), so a GSM stream is byte-identical to fgmm_encode of the K = 1
+ * parameters (w, mu, sigma) = (1, 0, level of sigma); the stream format is
+ * fgmm_encode's.
+ *
+ * Tables: a device blob of fgmm_gsm_tables_bytes() bytes, 16-byte aligned,
+ * caller-owned, written by fgmm_gsm_build and read-only afterwards:
+ *   [0, 512)        int32 L at byte 0, float levels[64] at byte 16;
+ *   [512, 66048)    uint16 rows[64][512], rows[l][j + 255] =
+ *                   Q_l(clamp(j, lo_l, hi_l + 1)), 0 left of the window;
+ *   [66048, 198144) uint32 pairs buckets[64][258]: for b in [0, 256],
+ *                   J = the largest j in [0, 510] with rows[l][j] <= 256 b,
+ *                   bucket = (J | rows[l][J] << 16, rows[l][J + 1]); entry
+ *                   257 is 0. The decoder's slot index.
+ * Scales: device fp32 or bf16 [N] (dtype FGMM_DTYPE_*); a scale must be
+ * finite and > 0 (else FGMM_ERR_BAD_PARAMS through fgmm_sync_status). */
+
+/* Bytes of the tables blob (host-only). */
+int64_t fgmm_gsm_tables_bytes(void);
+
+/* The 64 default levels, float(exp(ln 0.11 + i (ln 256 - ln 0.11) / 63))
+ * for i = 0..63 computed in double; out is host float[64]. */
+void fgmm_gsm_default_levels(float *out);
+
+/* Builds the tables of L (1..64) levels given in host memory (finite, > 0,
+ * strictly increasing; else FGMM_ERR_INVALID_ARG) into `tables`. */
+fgmm_status fgmm_gsm_build(fgmm_handle *h, const float *levels, int32_t L, void *tables, void *stream);
+
+/* Per-symbol intervals start | freq << 16 into device uint32 sf[N] (as
+ * fgmm_freqs for the K = 1 parameters above). */
+fgmm_status fgmm_gsm_freqs(fgmm_handle *h, int32_t dtype, int64_t N, const void *scales, const int32_t *symbols,
+                           const void *tables, uint32_t *sf, void *stream);
+
+/* Encodes residuals symbols[N] (device int32) with their scales; other
+ * arguments and the output as fgmm_encode. */
+fgmm_status fgmm_gsm_encode(fgmm_handle *h, int32_t dtype, int64_t N, const void *scales, const int32_t *symbols,
+                            int32_t S, const void *tables, uint16_t *words, int64_t words_cap, int64_t *offsets,
+                            int64_t *n_words_out, void *stream);
+
+/* Decodes N residuals into device int32 symbols_out[N]; arguments and
+ * errors as fgmm_decode, except that `words` must be 8-byte aligned
+ * (FGMM_ERR_INVALID_ARG otherwise). The decoder stages the tables in shared memory
+ * (cp.async.bulk on an mbarrier whose wait is bounded: FGMM_ERR_TIMEOUT if
+ * it gives up) and runs one lane per stream. */
+fgmm_status fgmm_gsm_decode(fgmm_handle *h, int32_t dtype, int64_t N, const void *scales, const void *tables,
+                            const uint16_t *words, int64_t n_words, const int64_t *offsets, int32_t S,
+                            int32_t *symbols_out, void *stream);
+
 /* ---- FP64 rate audit (Sec. V "no approximation" reference) --------------
  * For a latent and its symbols, computes in FP64 on the GPU:
  *   out[0] = sum over symbols of -log2 p64(s), p64 the exact mixture mass of

@@ -76,6 +76,12 @@ SIGNATURES = {
     "fgmm_table_encode": (I32, [P, LATP, P, I32, P, P, I64, P, P, P]),
     "fgmm_table_decode": (I32, [P, LATP, P, P, I64, P, I32, P, P]),
     "fgmm_rate_audit": (I32, [P, LATP, P, P, P]),
+    "fgmm_gsm_tables_bytes": (I64, []),
+    "fgmm_gsm_default_levels": (None, [P]),
+    "fgmm_gsm_build": (I32, [P, P, I32, P, P]),
+    "fgmm_gsm_freqs": (I32, [P, I32, I64, P, P, P, P, P]),
+    "fgmm_gsm_encode": (I32, [P, I32, I64, P, P, I32, P, P, I64, P, P, P]),
+    "fgmm_gsm_decode": (I32, [P, I32, I64, P, P, P, I64, P, I32, P, P]),
     "fgmm_autotune": (I32, [P, P, I32, ctypes.c_double, ctypes.c_double, P]),
     "fgmm_batch_create": (I32, [P, P, I32, P, P, I64, P, P, ctypes.POINTER(P)]),
     "fgmm_batch_destroy": (None, [P]),

@@ -9,6 +9,8 @@ from __future__ import annotations
 import ctypes
 import threading
 
+import numpy as np
+
 import torch
 
 from . import _abi
@@ -223,6 +225,83 @@ def table_decode(params, words, offsets, S, table=None, h: Handle | None = None,
     offsets = offsets.to(torch.int64).contiguous()
     h.check(_abi.fgmm_table_decode(h.ptr, ctypes.byref(lat), _ptr(table), _ptr(words), words.numel(), _ptr(offsets),
                                    S, _ptr(out), _stream()))
+    if sync:
+        h.sync()
+    return out
+
+
+# ---- Gaussian single model with pre-built tables (Sec. II-C) ----
+
+def gsm_default_levels() -> np.ndarray:
+    """The 64 default scale levels (log-even in [0.11, 256]), float32."""
+    out = np.empty(64, np.float32)
+    _abi.fgmm_gsm_default_levels(out.ctypes.data_as(ctypes.c_void_p))
+    return out
+
+
+def gsm_build(levels=None, device="cuda", h: Handle | None = None) -> torch.Tensor:
+    """Tables blob (uint8 device tensor) for the given increasing levels
+    (default: the 64 default levels)."""
+    h = h or handle(device)
+    lv = gsm_default_levels() if levels is None else np.ascontiguousarray(levels, dtype=np.float32)
+    blob = torch.empty(int(_abi.fgmm_gsm_tables_bytes()), dtype=torch.uint8, device=device)
+    h.check(_abi.fgmm_gsm_build(h.ptr, lv.ctypes.data_as(ctypes.c_void_p), int(lv.size), _ptr(blob), _stream()))
+    h.sync()
+    return blob
+
+
+def _scales(scales: torch.Tensor):
+    if scales.dim() != 1 or not scales.is_cuda or not scales.is_contiguous():
+        raise ValueError("scales must be a contiguous 1-D CUDA tensor")
+    if scales.dtype == torch.float32:
+        return _abi.FGMM_DTYPE_F32
+    if scales.dtype == torch.bfloat16:
+        return _abi.FGMM_DTYPE_BF16
+    raise ValueError("scales dtype must be float32 or bfloat16")
+
+
+def gsm_freqs(scales, symbols, tables, h: Handle | None = None) -> torch.Tensor:
+    h = h or handle(scales.device)
+    dt = _scales(scales)
+    sym = symbols.to(torch.int32).contiguous()
+    sf = torch.empty(scales.numel(), dtype=torch.int32, device=scales.device)
+    h.check(_abi.fgmm_gsm_freqs(h.ptr, dt, scales.numel(), _ptr(scales), _ptr(sym), _ptr(tables), _ptr(sf),
+                                _stream()))
+    h.sync()
+    return sf
+
+
+def gsm_encode(scales, symbols, S: int, tables, h: Handle | None = None, sync: bool = True):
+    """Encode residuals with their scales. Returns (words, offsets) as encode()."""
+    h = h or handle(scales.device)
+    dt = _scales(scales)
+    N = scales.numel()
+    sym = symbols.to(torch.int32).contiguous()
+    cap = encode_bound_words(N, S)
+    if cap < 0:
+        raise ValueError("S must be a positive multiple of 32")
+    words = torch.empty(max(cap, 1), dtype=torch.int16, device=scales.device)
+    offsets = torch.empty(S // 32 + 1, dtype=torch.int64, device=scales.device)
+    total = torch.empty(1, dtype=torch.int64, device=scales.device)
+    h.check(_abi.fgmm_gsm_encode(h.ptr, dt, N, _ptr(scales), _ptr(sym), S, _ptr(tables), _ptr(words), cap,
+                                 _ptr(offsets), _ptr(total), _stream()))
+    if not sync:
+        return words, offsets, total
+    h.sync()
+    return words[: int(total.item())], offsets
+
+
+def gsm_decode(scales, words, offsets, S: int, tables, h: Handle | None = None, out=None, sync: bool = True):
+    """Decode residuals; returns int32 [N]."""
+    h = h or handle(scales.device)
+    dt = _scales(scales)
+    N = scales.numel()
+    words = words.contiguous()
+    offsets = offsets.to(torch.int64).contiguous()
+    if out is None:
+        out = torch.empty(N, dtype=torch.int32, device=scales.device)
+    h.check(_abi.fgmm_gsm_decode(h.ptr, dt, N, _ptr(scales), _ptr(tables), _ptr(words), words.numel(),
+                                 _ptr(offsets), S, _ptr(out), _stream()))
     if sync:
         h.sync()
     return out
