@@ -207,27 +207,41 @@ __device__ __forceinline__ void wring_issue(uint16_t* ring, const uint16_t* __re
     asm volatile("cp.async.commit_group;\n" ::: "memory");
 }
 
-// refill_warp with the words read from the ring.
+// refill_warp with the words read from the ring, without branches: every
+// lane reads a slot (an index inside the ring), the lanes that refill keep it.
 __device__ __forceinline__ void refill_ring(uint32_t& x, bool part, const uint16_t* ring, int64_t& ptr, int64_t beg,
                                             bool& bad, uint32_t lt)
 {
     const bool need = part && x < kL;
     const uint32_t m = __ballot_sync(kFull, need);
-    if (m) {
-        const int c = __popc(m);
-        if (need) {
-            const int64_t idx = ptr - c + __popc(m & lt);
-            uint32_t w = 0;
-            if (idx >= beg) w = ring[(int)(idx & (kWRing - 1))];
-            else bad = true;
-            x = (x << 16) | w;
-        }
-        ptr -= c;
-    }
+    const int64_t idx = ptr - __popc(m) + __popc(m & lt);
+    const uint32_t w = ring[(int)(idx & (kWRing - 1))];
+    const bool ok = idx >= beg;
+    bad |= need && !ok;
+    x = need ? (x << 16) | (ok ? w : 0u) : x;
+    ptr -= __popc(m);
 }
 
+// Level of every symbol's scale (uint8), and the scale check, ahead of the
+// decoder: the search over the levels leaves the decoder's serial chain.
 template <typename T>
-__global__ void __launch_bounds__(1024, 1) fgmm_gsm_dec_kernel(const T* __restrict__ scales, int64_t N, int32_t S,
+__global__ void __launch_bounds__(256) fgmm_gsm_level_kernel(const T* __restrict__ scales, int64_t N,
+                                                             const unsigned char* __restrict__ blob,
+                                                             uint8_t* __restrict__ lev, int32_t* err)
+{
+    __shared__ float lvp[kLmax];
+    if (threadIdx.x < kLmax) load_levels(blob, lvp, threadIdx.x);
+    __syncthreads();
+    bool bad = false;
+    for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x) {
+        const float sg = load_param(scales, n);
+        bad |= !scale_ok(sg);
+        lev[n] = (uint8_t)level_of(lvp, sg);
+    }
+    if (bad) set_error(err, kErrBadParams);
+}
+
+__global__ void __launch_bounds__(1024, 1) fgmm_gsm_dec_kernel(const uint8_t* __restrict__ lev, int64_t N, int32_t S,
                                                                int64_t T_steps, const unsigned char* __restrict__ blob,
                                                                const uint16_t* __restrict__ words, int64_t n_words,
                                                                const int64_t* __restrict__ offsets, int64_t nseg,
@@ -235,7 +249,6 @@ __global__ void __launch_bounds__(1024, 1) fgmm_gsm_dec_kernel(const T* __restri
 {
     extern __shared__ __align__(16) unsigned char sm[];
     __shared__ __align__(8) unsigned long long mbar_s;
-    float* lvp = reinterpret_cast<float*>(sm);                         // header slot reused for the search table
     const uint16_t* srow = reinterpret_cast<const uint16_t*>(sm + kRowsOff);
     const uint2* sbkt = reinterpret_cast<const uint2*>(sm + kBktOff);
     const uint32_t mbar = (uint32_t)__cvta_generic_to_shared(&mbar_s);
@@ -255,8 +268,6 @@ __global__ void __launch_bounds__(1024, 1) fgmm_gsm_dec_kernel(const T* __restri
             "l"(blob + kRowsOff), "r"(bytes), "r"(mbar)
             : "memory");
     }
-    for (int i = threadIdx.x; i < kLmax; i += blockDim.x) load_levels(blob, lvp, i);   // blocks of 32 threads too
-    __syncthreads();
     if (!mbar_wait(mbar, 0, kWaitLimit)) {
         if (threadIdx.x == 0) set_error(err, kErrTimeout);
         mbar_wait(mbar, 0, kWaitLimit);   // let the copy land before the block leaves
@@ -284,31 +295,25 @@ __global__ void __launch_bounds__(1024, 1) fgmm_gsm_dec_kernel(const T* __restri
         __syncwarp();
         int64_t ready = fill;
         int pending = 0;
-        bool bad = false, badp = false;
+        bool bad = false;
         const int64_t n0 = g * 32 + lane;
         // steps of this lane's stream with a symbol: t < tn
         const int64_t tn = n0 < N ? (N - n0 + S - 1) / S : 0;
-        const T* sp = scales + n0;
+        const uint8_t* lp = lev + n0;
         int32_t* op = out + n0;
-        // scales of steps t .. t + kRing - 1 in registers: the load of step
-        // t + kRing is issued at step t, kRing - 1 steps before its level
-        // is needed, which covers the latency of a load from DRAM
-        float ring_s[kRing];
+        // levels of steps t .. t + kRing - 1 in registers, each loaded
+        // kRing steps before it is used
+        uint32_t lring[kRing];
 #pragma unroll
-        for (int k = 0; k < kRing; ++k) ring_s[k] = k < tn ? load_param(sp, (int64_t)k * S) : 1.0f;
-        int lvl = level_of(lvp, ring_s[0]);
-        badp |= tn > 0 && !scale_ok(ring_s[0]);
+        for (int k = 0; k < kRing; ++k) lring[k] = k < tn ? (uint32_t)__ldg(lp + (int64_t)k * S) : 0u;
         for (int64_t t0 = 0; t0 < T_steps; t0 += kRing) {
 #pragma unroll
             for (int k = 0; k < kRing; ++k) {
                 const int64_t t = t0 + k;
                 if (t >= T_steps) break;
                 const bool act = t < tn;
-                // next step's level, off the state chain
-                const float sg_n = ring_s[(k + 1) % kRing];
-                const int lvl_n = level_of(lvp, sg_n);
-                badp |= t + 1 < tn && !scale_ok(sg_n);
-                ring_s[k] = t + kRing < tn ? load_param(sp, (t + kRing) * S) : 1.0f;
+                const int lvl = (int)min(lring[k], (uint32_t)(kLmax - 1));
+                lring[k] = t + kRing < tn ? (uint32_t)__ldg(lp + (t + kRing) * S) : 0u;
                 // words: issue the next chunk once its slots are consumed;
                 // wait only if this step could read below what has landed
                 if (ptr - fill <= kWRing - kWChunk && fill > beg) {
@@ -329,35 +334,35 @@ __global__ void __launch_bounds__(1024, 1) fgmm_gsm_dec_kernel(const T* __restri
                     }
                     __syncwarp();
                 }
-                int32_t s = 0;
-                bool esc = false;
-                if (act) {
-                    const uint32_t slot = x & 0xffffu;
-                    const uint2* bk = sbkt + lvl * kBktStride + (slot >> 8);
-                    const uint2 P = bk[0], Pn = bk[1];
-                    // clamped so that a blob that was never built still
-                    // reads inside its row
-                    int j0 = min((int)(P.x & 0xffffu), kRow - 2);
-                    int j1 = min(max((int)(Pn.x & 0xffffu) + 1, j0 + 1), kRow - 1);
-                    uint32_t qa = P.x >> 16, qb = Pn.y;
-                    esc = slot >= qb;
-                    if (esc) {
-                        qa = qb;
-                        qb = kM;
-                    } else {
-                        const uint16_t* row = srow + lvl * kRow;
-                        while (j1 - j0 > 1) {
-                            const int mid = (j0 + j1) >> 1;
-                            const uint32_t qm = row[mid];
-                            if (qm <= slot) { j0 = mid; qa = qm; }
-                            else { j1 = mid; qb = qm; }
-                        }
-                        s = j0 - kYmax;
+                // the bucket pair decides most slots; the row search runs
+                // only for lanes whose bucket holds more than one boundary
+                const uint32_t slot = x & 0xffffu;
+                const uint2* bk = sbkt + lvl * kBktStride + (slot >> 8);
+                const uint2 P = bk[0], Pn = bk[1];
+                // clamped so that a blob that was never built still reads
+                // inside its row
+                int j0 = min((int)(P.x & 0xffffu), kRow - 2);
+                int j1 = min(max((int)(Pn.x & 0xffffu) + 1, j0 + 1), kRow - 1);
+                uint32_t qa = P.x >> 16, qb = Pn.y;
+                const bool esc = act && slot >= qb;
+                bool srch = act && !esc && j1 - j0 > 1;
+                if (__any_sync(kFull, srch)) {
+                    const uint16_t* row = srow + lvl * kRow;
+                    while (srch) {
+                        const int mid = (j0 + j1) >> 1;
+                        const uint32_t qm = row[mid];
+                        if (qm <= slot) { j0 = mid; qa = qm; }
+                        else { j1 = mid; qb = qm; }
+                        srch = j1 - j0 > 1;
                     }
-                    x = (qb - qa) * (x >> 16) + slot - qa;
                 }
+                const uint32_t st = esc ? qb : qa;
+                const uint32_t fr = esc ? kM - qb : qb - qa;
+                const uint32_t xn = fr * (x >> 16) + slot - st;
+                x = act ? xn : x;
+                int32_t s = j0 - kYmax;
                 refill_ring(x, act, ring, ptr, beg, bad, lt);
-                if (__ballot_sync(kFull, esc)) {
+                if (__any_sync(kFull, esc)) {
                     uint32_t hi16 = 0, lo16 = 0;
                     if (esc) { hi16 = x & 0xffffu; x >>= 16; }
                     refill_ring(x, esc, ring, ptr, beg, bad, lt);
@@ -366,14 +371,12 @@ __global__ void __launch_bounds__(1024, 1) fgmm_gsm_dec_kernel(const T* __restri
                     if (esc) s = (int32_t)((hi16 << 16) | lo16);
                 }
                 if (act) op[t * S] = s;
-                lvl = lvl_n;
             }
         }
         asm volatile("cp.async.wait_group 0;\n" ::: "memory");   // the ring is reused by the next segment
         __syncwarp();
         const bool fail = bad || x != kL || ptr != beg;
         if (__ballot_sync(kFull, fail) && lane == 0) set_error(err, kErrCorrupt);
-        if (__ballot_sync(kFull, badp) && lane == 0) set_error(err, kErrBadParams);
     }
 }
 
@@ -397,21 +400,30 @@ void launch_interval_any(int32_t dtype, const void* scales, int64_t N, const int
 // Decoder grid: one CTA per SM at most (the staged tables take ~194 KB of
 // shared memory), ceil(nseg / SMs) warps per CTA up to 32, warps looping
 // over segments beyond that.
-template <typename T>
-cudaError_t launch_dec(const void* scales, int64_t N, int32_t S, const unsigned char* blob, const uint16_t* words,
-                       int64_t n_words, const int64_t* offsets, int32_t* out, int32_t* err, int sms, cudaStream_t st)
+cudaError_t launch_dec(int32_t dtype, const void* scales, int64_t N, int32_t S, const unsigned char* blob,
+                       uint8_t* lev, const uint16_t* words, int64_t n_words, const int64_t* offsets, int32_t* out,
+                       int32_t* err, int sms, cudaStream_t st)
 {
+    if (N > 0) {
+        const int64_t blocks = (N + 255) / 256 < (int64_t)sms * 16 ? (N + 255) / 256 : (int64_t)sms * 16;
+        if (dtype == FGMM_DTYPE_BF16)
+            fgmm_gsm_level_kernel<__nv_bfloat16><<<(unsigned)blocks, 256, 0, st>>>(
+                static_cast<const __nv_bfloat16*>(scales), N, blob, lev, err);
+        else
+            fgmm_gsm_level_kernel<float><<<(unsigned)blocks, 256, 0, st>>>(static_cast<const float*>(scales), N,
+                                                                            blob, lev, err);
+    }
     const int64_t nseg = S / 32;
     int64_t wpb = (nseg + sms - 1) / sms;
     if (wpb > 32) wpb = 32;
     int64_t grid = (nseg + wpb - 1) / wpb;
     if (grid > sms) grid = sms;
     const size_t smem = kDecSmem + (size_t)wpb * kWRing * sizeof(uint16_t);
-    cudaError_t e = cudaFuncSetAttribute(fgmm_gsm_dec_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(fgmm_gsm_dec_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)(kDecSmem + 32 * kWRing * sizeof(uint16_t)));
     if (e != cudaSuccess) return e;
-    fgmm_gsm_dec_kernel<T><<<(unsigned)grid, (unsigned)(wpb * 32), smem, st>>>(
-        static_cast<const T*>(scales), N, S, steps_of(N, S), blob, words, n_words, offsets, nseg, out, err);
+    fgmm_gsm_dec_kernel<<<(unsigned)grid, (unsigned)(wpb * 32), smem, st>>>(lev, N, S, steps_of(N, S), blob, words,
+                                                                             n_words, offsets, nseg, out, err);
     return cudaGetLastError();
 }
 
@@ -508,12 +520,12 @@ fgmm_status fgmm_gsm_decode(fgmm_handle* h, int32_t dtype, int64_t N, const void
     if (n_words > 0 && (reinterpret_cast<uintptr_t>(words) & 7u) != 0)
         return fail(h, FGMM_ERR_INVALID_ARG, "fgmm_gsm_decode: words must be 8-byte aligned");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const unsigned char* blob = static_cast<const unsigned char*>(tables);
-    cudaError_t e = dtype == FGMM_DTYPE_BF16
-                        ? launch_dec<__nv_bfloat16>(scales, N, S, blob, words, n_words, offsets, symbols_out,
-                                                    h->d_err, h->num_sms, st)
-                        : launch_dec<float>(scales, N, S, blob, words, n_words, offsets, symbols_out, h->d_err,
-                                            h->num_sms, st);
+    // workspace: one level byte per symbol
+    s = ws_reserve(h, (size_t)(N > 0 ? N : 1), st);
+    if (s != FGMM_OK) return s;
+    cudaError_t e = launch_dec(dtype, scales, N, S, static_cast<const unsigned char*>(tables),
+                               static_cast<uint8_t*>(h->ws), words, n_words, offsets, symbols_out, h->d_err,
+                               h->num_sms, st);
     return e == cudaSuccess ? FGMM_OK : cuda_fail(h, e, "fgmm_gsm_decode launch");
 }
 
