@@ -197,6 +197,53 @@ def batch_case(dev, h, out, name, lats, alu_peak_tops, hbm_gbs, reps=5, max_over
     del params, syms
 
 
+def gsm_case(dev, h, flush, reps):
+    """Gaussian single model with 64 pre-built level tables (Sec. II-C)
+    against the table-free coder on the same residuals with the exact scale
+    (K = 1), on a 320x64x96 latent of residuals: time per direction (the
+    decoder includes its level pre-pass), and rate against the FP64 ideal of
+    the exact scale."""
+    import numpy as np
+    import torch
+    from paper_2509_18815_gb300 import codec, synth
+    lat = synth.make_gsm_latent(320, 64, 96, seed=1003)
+    N = lat.N
+    dsg = torch.from_numpy(lat.scales).to(dev)
+    dq = torch.from_numpy(lat.symbols).to(dev)
+    exact = torch.stack([torch.ones_like(dsg), torch.zeros_like(dsg), dsg])[:, None, :].contiguous()
+    blob = codec.gsm_build(device=dev, h=h)
+    t_build = _events_ms(lambda: codec.gsm_build(device=dev, h=h), reps)
+    ideal, coded_k1, _, _ = codec.rate_audit(exact, dq, h)
+    sf = codec.gsm_freqs(dsg, dq, blob, h).to(torch.int64) & 0xffffffff
+    fr = (sf >> 16).to(torch.float64)
+    esc = ((sf & 0xffff) + (sf >> 16)) == 65536
+    coded_gsm = float((16.0 - torch.log2(fr)).sum().item()) + 32.0 * int(esc.sum().item())
+    res = {"symbols": N, "levels": 64, "tables_bytes": blob.numel(), "ms_build_tables": t_build,
+           "ideal_bits_per_symbol": ideal / N,
+           "gsm_overhead_pct": 100.0 * (coded_gsm / ideal - 1.0),
+           "table_free_k1_overhead_pct": 100.0 * (coded_k1 / ideal - 1.0), "by_streams": []}
+    out = torch.empty(N, dtype=torch.int32, device=dev)
+    for S in (1024, codec.autotune([N], bits_per_symbol=ideal / N, h=h)[0], 16384):
+        w, o = codec.gsm_encode(dsg, dq, S, blob, h=h)
+        codec.gsm_decode(dsg, w, o, S, blob, h=h, out=out)
+        assert torch.equal(out, dq)
+        te = _events_ms(lambda: codec.gsm_encode(dsg, dq, S, blob, h=h, sync=False), reps, flush)
+        td = _events_ms(lambda: codec.gsm_decode(dsg, w, o, S, blob, h=h, out=out, sync=False), reps, flush)
+        w1, o1 = codec.encode(exact, dq, S, h=h)
+        codec.decode(exact, w1, o1, S, h=h, out=out)
+        assert torch.equal(out, dq)
+        te1 = _events_ms(lambda: codec.encode(exact, dq, S, h=h, sync=False), reps, flush)
+        td1 = _events_ms(lambda: codec.decode(exact, w1, o1, S, h=h, out=out, sync=False), reps, flush)
+        res["by_streams"].append({
+            "S": S, "gsm": {"encode_msym_s": N / te / 1e3, "decode_msym_s": N / td / 1e3, "ms_encode": te,
+                            "ms_decode": td, "bits_per_symbol": 16.0 * w.numel() / N},
+            "table_free_k1": {"encode_msym_s": N / te1 / 1e3, "decode_msym_s": N / td1 / 1e3, "ms_encode": te1,
+                              "ms_decode": td1, "bits_per_symbol": 16.0 * w1.numel() / N,
+                              "decoder": codec.decode_plan(S, h=h)}})
+        del w, o, w1, o1
+    return res
+
+
 def throughput_workloads(dev, alu_peak_tops, hbm_gbs, reps=5):
     """Larger workloads: one 320x64x96 latent (K = 3 and 4, fp32 and bf16
     parameters, autotuned stream count, FP64 rate audit), a batch of 64
@@ -270,7 +317,9 @@ def throughput_workloads(dev, alu_peak_tops, hbm_gbs, reps=5):
                       "encode_msym_s": lat3.N / te3 / 1e3, "decode_msym_s": lat3.N / td3 / 1e3})
         del w3, o3, out3
     out["latent_320x64x96_k3_fp32_streams_tradeoff"] = trade
-    del dp3, ds3, flush
+    del dp3, ds3
+    out["gsm_320x64x96"] = gsm_case(dev, h, flush, reps)
+    del flush
     shapes = synth.batch_shapes(64, seed=1004)
     batch_case(dev, h, out, "batch64_uneven_k3",
                [synth.make_latent(C, H, W, 3, 1004 + i) for i, (C, H, W) in enumerate(shapes)], alu_peak_tops,
