@@ -84,6 +84,9 @@ def _load():
         lib.or_gsm_levels.argtypes = [P]
         lib.or_gsm_params.restype = ctypes.c_int
         lib.or_gsm_params.argtypes = [P, ctypes.c_int, P, I64, P, P]
+        lib.or_ckbd_split.argtypes = [ctypes.c_int, I64, I64, I64, P, P, P, P, P, P]
+        lib.or_ckbd_merge.argtypes = [I64, I64, I64, P, P, P]
+        lib.or_ckbd_context.argtypes = [ctypes.c_int, I64, I64, I64, P, P, P]
         _lib = lib
         return lib
 
@@ -258,3 +261,72 @@ def rate_audit(params, symbols):
     if st != OK:
         raise ValueError(f"oracle audit status {st}")
     return float(out[0]), float(out[1]), float(out[2]), int(out[3])
+
+
+# ---- checkerboard two-pass coding (anchors h + w even, then the rest) ----
+
+def ckbd_counts(shape):
+    """(anchors, non-anchors) of a C x H x W latent."""
+    C, H, W = shape
+    na = C * ((H * W + 1) // 2)
+    return na, C * H * W - na
+
+
+def ckbd_split(params, y, shape):
+    """-> (anchor params [3, K, Na], anchor symbols, non-anchor params,
+    non-anchor symbols), each list channel by channel in raster order."""
+    p = _params(params)
+    K = p.shape[1]
+    C, H, W = shape
+    assert p.shape[2] == C * H * W
+    na, nn = ckbd_counts(shape)
+    yy = None if y is None else np.ascontiguousarray(y, dtype=np.int32)
+    pa, pn = np.empty((3, K, na), np.float32), np.empty((3, K, nn), np.float32)
+    ya, yn = np.zeros(na, np.int32), np.zeros(nn, np.int32)
+    _load().or_ckbd_split(K, C, H, W, _p(p), None if yy is None else _p(yy), _p(pa), _p(ya), _p(pn), _p(yn))
+    return pa, ya, pn, yn
+
+
+def ckbd_merge(ya, yn, shape):
+    C, H, W = shape
+    y = np.zeros(C * H * W, np.int32)
+    a = np.ascontiguousarray(ya, dtype=np.int32)
+    b = None if yn is None else np.ascontiguousarray(yn, dtype=np.int32)
+    _load().or_ckbd_merge(C, H, W, _p(a), None if b is None else _p(b), _p(y))
+    return y
+
+
+def ckbd_context(params, y, shape):
+    """The fixed stand-in context model: non-anchor parameters [3, K, Nn]
+    from the hyperprior parameters and the anchors of y."""
+    p = _params(params)
+    C, H, W = shape
+    _, nn = ckbd_counts(shape)
+    yy = np.ascontiguousarray(y, dtype=np.int32)
+    pn = np.empty((3, p.shape[1], nn), np.float32)
+    _load().or_ckbd_context(p.shape[1], C, H, W, _p(p), _p(yy), _p(pn))
+    return pn
+
+
+def ckbd_encode(params, y, shape, Sa: int, Sn: int):
+    """Two-pass encode: anchors with the hyperprior's parameters, then the
+    non-anchors with the context's. -> ((words, offsets) anchors, (words,
+    offsets) non-anchors)."""
+    pa, ya, _, yn = ckbd_split(params, y, shape)
+    pn = ckbd_context(params, y, shape)
+    return encode(pa, ya, Sa), encode(pn, yn, Sn)
+
+
+def ckbd_decode(params, first, second, shape, Sa: int, Sn: int):
+    """Two-pass decode: the anchors, then the context from them, then the
+    non-anchors. -> (y, status)."""
+    pa, _, _, _ = ckbd_split(params, None, shape)
+    ya, st = decode(pa, first[0], first[1], Sa)
+    if st != OK:
+        return None, st
+    y = ckbd_merge(ya, None, shape)
+    pn = ckbd_context(params, y, shape)
+    yn, st = decode(pn, second[0], second[1], Sn)
+    if st != OK:
+        return None, st
+    return ckbd_merge(ya, yn, shape), OK

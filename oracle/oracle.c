@@ -718,3 +718,93 @@ int or_gsm_params(const float *lv, int L, const float *sigma, int64_t N, float *
     }
     return OR_OK;
 }
+
+/* ---------------------------------------------------------------------
+ * Checkerboard two-pass coding (the context model of the paper's codecs,
+ * Sec. IV-A): in every channel of a C x H x W latent the positions with
+ * h + w even are anchors, coded first with the hyperprior's parameters;
+ * the others are coded second, with parameters that a context model
+ * computes from the decoded anchors around them. Anchors and non-anchors
+ * are each listed channel by channel in raster order.
+ *
+ * The trained context network is not available; a fixed stand-in takes its
+ * place, defined here and nowhere in the paper: for a non-anchor with
+ * in-bounds 4-neighbours (all anchors) of symbol sum ctx (64-bit integer)
+ * and count cnt, each component keeps its weight, moves its mean toward the
+ * neighbours, m_k = fmaf(-cnt, mu_k, (float)ctx), mu'_k = fmaf(0.125, m_k,
+ * mu_k), and narrows its scale, sigma'_k = 0.75 sigma_k (each one FP32
+ * rounding, in this order).
+ * ------------------------------------------------------------------- */
+static int64_t ckbd_count(int64_t C, int64_t H, int64_t W, int anchor)
+{
+    int64_t n = 0;
+    for (int64_t h = 0; h < H; ++h)
+        for (int64_t w = 0; w < W; ++w)
+            if ((((h + w) & 1) == 0) == (anchor != 0)) ++n;
+    return C * n;
+}
+
+/* params [3][K][N] and y[N] -> anchor and non-anchor parameters and
+ * symbols; any output may be NULL. */
+void or_ckbd_split(int K, int64_t C, int64_t H, int64_t W, const float *params, const int32_t *y, float *params_a,
+                   int32_t *y_a, float *params_n, int32_t *y_n)
+{
+    const int64_t N = C * H * W, Na = ckbd_count(C, H, W, 1), Nn = N - Na;
+    int64_t ia = 0, in = 0;
+    for (int64_t c = 0; c < C; ++c)
+        for (int64_t h = 0; h < H; ++h)
+            for (int64_t w = 0; w < W; ++w) {
+                const int64_t n = (c * H + h) * W + w;
+                const int anchor = ((h + w) & 1) == 0;
+                float *po = anchor ? params_a : params_n;
+                int32_t *yo = anchor ? y_a : y_n;
+                const int64_t i = anchor ? ia++ : in++, M = anchor ? Na : Nn;
+                if (po)
+                    for (int r = 0; r < 3 * K; ++r) po[r * M + i] = params[r * N + n];
+                if (yo && y) yo[i] = y[n];
+            }
+}
+
+/* Anchor and non-anchor symbols -> y[N] (y_n may be NULL: anchors only). */
+void or_ckbd_merge(int64_t C, int64_t H, int64_t W, const int32_t *y_a, const int32_t *y_n, int32_t *y)
+{
+    int64_t ia = 0, in = 0;
+    for (int64_t c = 0; c < C; ++c)
+        for (int64_t h = 0; h < H; ++h)
+            for (int64_t w = 0; w < W; ++w) {
+                const int64_t n = (c * H + h) * W + w;
+                if (((h + w) & 1) == 0) y[n] = y_a[ia++];
+                else if (y_n) y[n] = y_n[in++];
+                else ++in;
+            }
+}
+
+/* Stand-in context: hyperprior params [3][K][N] and y[N] (anchors read) ->
+ * non-anchor parameters [3][K][Nn]. */
+void or_ckbd_context(int K, int64_t C, int64_t H, int64_t W, const float *params, const int32_t *y, float *params_n)
+{
+    const int64_t N = C * H * W, Nn = N - ckbd_count(C, H, W, 1);
+    int64_t in = 0;
+    for (int64_t c = 0; c < C; ++c)
+        for (int64_t h = 0; h < H; ++h)
+            for (int64_t w = 0; w < W; ++w) {
+                if (((h + w) & 1) == 0) continue;
+                const int64_t n = (c * H + h) * W + w;
+                int64_t ctx = 0;
+                int cnt = 0;
+                if (h > 0) { ctx += y[n - W]; ++cnt; }
+                if (h + 1 < H) { ctx += y[n + W]; ++cnt; }
+                if (w > 0) { ctx += y[n - 1]; ++cnt; }
+                if (w + 1 < W) { ctx += y[n + 1]; ++cnt; }
+                for (int k = 0; k < K; ++k) {
+                    const float wk = params[(0 * K + k) * N + n];
+                    const float mu = params[(1 * K + k) * N + n];
+                    const float sg = params[(2 * K + k) * N + n];
+                    const float m = fmaf(-(float)cnt, mu, (float)ctx);
+                    params_n[(0 * K + k) * Nn + in] = wk;
+                    params_n[(1 * K + k) * Nn + in] = fmaf(0.125f, m, mu);
+                    params_n[(2 * K + k) * Nn + in] = sg * 0.75f;
+                }
+                ++in;
+            }
+}

@@ -23,6 +23,13 @@ The Gaussian single model's coder receives the quantiser's mean-shifted
 residual and the scale only (Sec. II-C); its inputs (make_gsm_latent) are
   sigma  = exp(U[ln 0.11, ln sigma_max])
   q      = round-half-even(sigma * N(0, 1))   (= round(y - mu), y ~ N(mu, sigma))
+
+Checkerboard latents (make_ckbd_latent) have the hyperprior parameters
+above for every position; anchors (h + w even) are drawn from them, and
+each non-anchor from the mixture whose means move toward its 4-neighbour
+anchors and whose scales narrow, the way a context model's output does:
+  mu'_k = mu_k + (sum of neighbours - cnt mu_k) / 8,  sigma'_k = 0.75 sigma_k
+(computed here in float64, only to draw the symbols).
 """
 from __future__ import annotations
 
@@ -113,6 +120,36 @@ def make_gsm_latent(C: int, H: int, W: int, seed: int, sigma_max: float = 16.0,
         pick = rng.random(nsel) < 0.5
         q[m] = np.where(pick, big, near).astype(np.int32)
     return GsmLatent(scales=sigma, symbols=q, shape=(C, H, W), seed=seed)
+
+
+def _draw_mixture(rng, w, mu, sigma):
+    K, N = w.shape
+    u = rng.random(N)
+    cw = np.cumsum(w.astype(np.float64), axis=0)
+    comp = np.minimum((u[None, :] > cw).sum(axis=0), K - 1)
+    idx = np.arange(N)
+    y = mu[comp, idx].astype(np.float64) + sigma[comp, idx].astype(np.float64) * rng.standard_normal(N)
+    return np.clip(np.rint(y), -2.0**31, 2.0**31 - 1).astype(np.int64).astype(np.int32)
+
+
+def make_ckbd_latent(C: int, H: int, W: int, K: int, seed: int, sigma_max: float = 16.0) -> Latent:
+    """Hyperprior parameters for all C*H*W positions and symbols whose
+    non-anchors depend on their anchor neighbours (module docstring)."""
+    lat = make_latent(C, H, W, K, seed, sigma_max)
+    rng = np.random.default_rng(seed + 7919)
+    w, mu, sigma = (lat.params[i].astype(np.float64) for i in range(3))
+    y = lat.symbols.astype(np.int64).reshape(C, H, W)
+    hh, ww = np.meshgrid(np.arange(H), np.arange(W), indexing="ij")
+    non = ((hh + ww) & 1) == 1
+    pad = np.pad(y, ((0, 0), (1, 1), (1, 1)))
+    ctx = pad[:, :-2, 1:-1] + pad[:, 2:, 1:-1] + pad[:, 1:-1, :-2] + pad[:, 1:-1, 2:]
+    cnt = ((hh > 0).astype(np.int64) + (hh < H - 1) + (ww > 0) + (ww < W - 1))[None].repeat(C, 0)
+    sel = np.broadcast_to(non, (C, H, W)).reshape(-1)
+    mu2 = mu + (ctx.reshape(-1)[None, :] - cnt.reshape(-1)[None, :] * mu) / 8.0
+    yn = _draw_mixture(rng, w[:, sel], mu2[:, sel], 0.75 * sigma[:, sel])
+    sym = lat.symbols.copy()
+    sym[sel] = yn
+    return Latent(params=lat.params, symbols=sym, shape=(C, H, W), seed=seed)
 
 
 def to_bf16_bits(x: np.ndarray) -> np.ndarray:
