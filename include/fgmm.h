@@ -223,6 +223,41 @@ fgmm_status fgmm_gsm_decode(fgmm_handle *h, int32_t dtype, int64_t N, const void
                             const uint16_t *words, int64_t n_words, const int64_t *offsets, int32_t S,
                             int32_t *symbols_out, void *stream);
 
+/* ---- Checkerboard two-pass coding (the context model, Sec. IV-A) ---------
+ * In every channel of a C x H x W latent (N = C H W, n = (c H + h) W + w)
+ * the positions with h + w even are anchors: pass 1 codes them with the
+ * hyperprior's parameters; pass 2 codes the others with parameters that a
+ * context model computes from the decoded anchors. Anchors (non-anchors)
+ * are listed channel by channel in raster order, C ceil(HW/2) (C floor(HW/2))
+ * of them; each pass is an ordinary latent for fgmm_encode / fgmm_decode.
+ * Decoding: pass 1, fgmm_ckbd_merge of the anchors, the context, pass 2,
+ * fgmm_ckbd_merge of both. */
+
+/* Anchors of a C x H x W latent (host-only; -1 for negative sizes). */
+int64_t fgmm_ckbd_anchors(int64_t C, int64_t H, int64_t W);
+
+/* Gathers the anchors' and non-anchors' parameters ([3][K][Na], [3][K][Nn],
+ * lat's dtype) and symbols (int32) out of lat (N = C H W) and y (device
+ * int32 [N]). Any output may be NULL; y may be NULL when both symbol
+ * outputs are. */
+fgmm_status fgmm_ckbd_split(fgmm_handle *h, const fgmm_latent *lat, int64_t C, int64_t H, int64_t W,
+                            const int32_t *y, void *params_a, int32_t *y_a, void *params_n, int32_t *y_n,
+                            void *stream);
+
+/* Scatters anchor symbols y_a (and non-anchor symbols y_n, unless NULL) into
+ * y (device int32 [N]); positions of a NULL class are left unchanged. */
+fgmm_status fgmm_ckbd_merge(fgmm_handle *h, int64_t C, int64_t H, int64_t W, const int32_t *y_a,
+                            const int32_t *y_n, int32_t *y, void *stream);
+
+/* The stand-in context model (no trained network is available; this fixed
+ * function takes its place): from the hyperprior parameters lat (N = C H W)
+ * and the anchors of y, the non-anchors' parameters params_n (device fp32
+ * [3][K][Nn]): for a non-anchor whose in-bounds 4-neighbours sum to ctx
+ * (64-bit) over cnt of them, w'_k = w_k, mu'_k = fmaf(0.125, fmaf(-cnt, mu_k,
+ * float(ctx)), mu_k), sigma'_k = 0.75 sigma_k (FP32, round to nearest). */
+fgmm_status fgmm_ckbd_context(fgmm_handle *h, const fgmm_latent *lat, int64_t C, int64_t H, int64_t W,
+                              const int32_t *y, float *params_n, void *stream);
+
 /* ---- FP64 rate audit (Sec. V "no approximation" reference) --------------
  * For a latent and its symbols, computes in FP64 on the GPU:
  *   out[0] = sum over symbols of -log2 p64(s), p64 the exact mixture mass of

@@ -76,6 +76,10 @@ SIGNATURES = {
     "fgmm_table_encode": (I32, [P, LATP, P, I32, P, P, I64, P, P, P]),
     "fgmm_table_decode": (I32, [P, LATP, P, P, I64, P, I32, P, P]),
     "fgmm_rate_audit": (I32, [P, LATP, P, P, P]),
+    "fgmm_ckbd_anchors": (I64, [I64, I64, I64]),
+    "fgmm_ckbd_split": (I32, [P, LATP, I64, I64, I64, P, P, P, P, P, P]),
+    "fgmm_ckbd_merge": (I32, [P, I64, I64, I64, P, P, P, P]),
+    "fgmm_ckbd_context": (I32, [P, LATP, I64, I64, I64, P, P, P]),
     "fgmm_gsm_tables_bytes": (I64, []),
     "fgmm_gsm_default_levels": (None, [P]),
     "fgmm_gsm_build": (I32, [P, P, I32, P, P]),

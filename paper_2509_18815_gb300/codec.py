@@ -307,6 +307,74 @@ def gsm_decode(scales, words, offsets, S: int, tables, h: Handle | None = None, 
     return out
 
 
+# ---- checkerboard two-pass coding (anchors h + w even, then the rest) ----
+
+def ckbd_split(params, y, shape, h: Handle | None = None):
+    """-> (anchor params, anchor symbols, non-anchor params, non-anchor
+    symbols); y may be None (parameters only, symbols returned as None)."""
+    h = h or handle(params.device)
+    lat = latent(params)
+    C, H, W = shape
+    na = int(_abi.fgmm_ckbd_anchors(C, H, W))
+    nn = C * H * W - na
+    K = params.shape[1]
+    pa = torch.empty((3, K, na), dtype=params.dtype, device=params.device)
+    pn = torch.empty((3, K, nn), dtype=params.dtype, device=params.device)
+    ya = yn = None
+    if y is not None:
+        y = y.to(torch.int32).contiguous()
+        ya = torch.empty(na, dtype=torch.int32, device=params.device)
+        yn = torch.empty(nn, dtype=torch.int32, device=params.device)
+    h.check(_abi.fgmm_ckbd_split(h.ptr, ctypes.byref(lat), C, H, W, None if y is None else _ptr(y), _ptr(pa),
+                                 None if ya is None else _ptr(ya), _ptr(pn), None if yn is None else _ptr(yn),
+                                 _stream()))
+    return pa, ya, pn, yn
+
+
+def ckbd_merge(ya, yn, shape, y=None, h: Handle | None = None):
+    h = h or handle(ya.device)
+    C, H, W = shape
+    if y is None:
+        y = torch.zeros(C * H * W, dtype=torch.int32, device=ya.device)
+    h.check(_abi.fgmm_ckbd_merge(h.ptr, C, H, W, _ptr(ya), None if yn is None else _ptr(yn), _ptr(y), _stream()))
+    return y
+
+
+def ckbd_context(params, y, shape, out=None, h: Handle | None = None):
+    """The fixed stand-in context model: fp32 non-anchor parameters."""
+    h = h or handle(params.device)
+    lat = latent(params)
+    C, H, W = shape
+    nn = C * H * W - int(_abi.fgmm_ckbd_anchors(C, H, W))
+    if out is None:
+        out = torch.empty((3, params.shape[1], nn), dtype=torch.float32, device=params.device)
+    h.check(_abi.fgmm_ckbd_context(h.ptr, ctypes.byref(lat), C, H, W, _ptr(y), _ptr(out), _stream()))
+    return out
+
+
+def ckbd_encode(params, y, shape, Sa: int, Sn: int, h: Handle | None = None):
+    """Two-pass encode: anchors with the hyperprior's parameters, then the
+    non-anchors with the context's. -> ((words, offsets), (words, offsets))."""
+    h = h or handle(params.device)
+    pa, ya, _, yn = ckbd_split(params, y, shape, h)
+    pn = ckbd_context(params, y.to(torch.int32).contiguous(), shape, h=h)
+    return encode(pa, ya, Sa, h), encode(pn, yn, Sn, h)
+
+
+def ckbd_decode(params, first, second, shape, Sa: int, Sn: int, h: Handle | None = None, sync: bool = True):
+    """Two-pass decode: the anchors, the context from them, the non-anchors."""
+    h = h or handle(params.device)
+    pa, _, _, _ = ckbd_split(params, None, shape, h)
+    ya = decode(pa, first[0], first[1], Sa, h, sync=False)
+    y = ckbd_merge(ya, None, shape, h=h)
+    pn = ckbd_context(params, y, shape, h=h)
+    yn = decode(pn, second[0], second[1], Sn, h, sync=False)
+    ckbd_merge(ya, yn, shape, y=y, h=h)
+    if sync:
+        h.sync()
+    return y
+
+
 def rate_audit(params, symbols, h: Handle | None = None):
     """(ideal_bits, coded_bits, max_cdf_err, n_escape) computed in FP64 on the GPU."""
     h = h or handle(params.device)
