@@ -244,6 +244,41 @@ def gsm_case(dev, h, flush, reps):
     return res
 
 
+def ckbd_case(dev, h, flush, reps):
+    """Checkerboard two-pass coding (anchors, then the non-anchors with the
+    stand-in context's parameters) of the 192x32x48 K = 3 latent with 512
+    streams per pass (288 steps each, as the one-pass headline at 1024):
+    time per direction including split, context and merge, and the rate of
+    both passes against one pass with the hyperprior's parameters."""
+    import torch
+    from paper_2509_18815_gb300 import codec, synth
+    shape = (192, 32, 48)
+    lat = synth.make_ckbd_latent(*shape, 3, seed=1002)
+    N = lat.N
+    dp = torch.from_numpy(lat.params).to(dev)
+    dy = torch.from_numpy(lat.symbols).to(dev)
+    Sa = Sn = 512
+    first, second = codec.ckbd_encode(dp, dy, shape, Sa, Sn, h=h)
+    y = codec.ckbd_decode(dp, first, second, shape, Sa, Sn, h=h)
+    assert torch.equal(y, dy)
+    te = _events_ms(lambda: codec.ckbd_encode(dp, dy, shape, Sa, Sn, h=h), reps, flush)
+    td = _events_ms(lambda: codec.ckbd_decode(dp, first, second, shape, Sa, Sn, h=h, sync=False), reps, flush)
+    w1, o1 = codec.encode(dp, dy, 1024, h=h)
+    out = torch.empty(N, dtype=torch.int32, device=dev)
+    td1 = _events_ms(lambda: codec.decode(dp, w1, o1, 1024, h=h, out=out, sync=False), reps, flush)
+    ideal1, _, _, _ = codec.rate_audit(dp, dy, h)
+    pa, ya, _, yn = codec.ckbd_split(dp, dy, shape, h)
+    pn = codec.ckbd_context(dp, dy, shape, h=h)
+    ia, _, _, _ = codec.rate_audit(pa, ya, h)
+    inn, _, _, _ = codec.rate_audit(pn, yn, h)
+    bits2 = 16.0 * (first[0].numel() + second[0].numel())
+    return {"symbols": N, "S_per_pass": [Sa, Sn], "ms_encode": te, "ms_decode": td,
+            "encode_msym_s": N / te / 1e3, "decode_msym_s": N / td / 1e3, "one_pass_ms_decode": td1,
+            "ideal_bits_per_symbol_one_pass": ideal1 / N, "ideal_bits_per_symbol_two_pass": (ia + inn) / N,
+            "coded_bits_per_symbol_two_pass": bits2 / N,
+            "note": "host-launched sequence of split, two coder passes, context and merges (no graph)"}
+
+
 def throughput_workloads(dev, alu_peak_tops, hbm_gbs, reps=5):
     """Larger workloads: one 320x64x96 latent (K = 3 and 4, fp32 and bf16
     parameters, autotuned stream count, FP64 rate audit), a batch of 64
@@ -319,6 +354,7 @@ def throughput_workloads(dev, alu_peak_tops, hbm_gbs, reps=5):
     out["latent_320x64x96_k3_fp32_streams_tradeoff"] = trade
     del dp3, ds3
     out["gsm_320x64x96"] = gsm_case(dev, h, flush, reps)
+    out["ckbd_192x32x48_k3"] = ckbd_case(dev, h, flush, reps)
     del flush
     shapes = synth.batch_shapes(64, seed=1004)
     batch_case(dev, h, out, "batch64_uneven_k3",
