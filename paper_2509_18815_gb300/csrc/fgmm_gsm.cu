@@ -187,12 +187,13 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, uint32
 
 // Per-warp word ring: the segment's words are consumed downward from the
 // top; a ring of kWRing words in shared memory holds the words at and above
-// `fill` (absolute indices, slot = index mod kWRing), refilled kWChunk words
-// at a time by cp.async (8 bytes per lane) well before they are read. A
-// chunk overwrites the slots of words kWRing above it, which are consumed
-// once ptr - fill <= kWRing - kWChunk. One step reads at most 96 words (32
-// symbols plus two escape chunks each), fewer than kWChunk, so one issue per
-// step keeps up. Pieces outside [0, n_words) are zero-filled, never read.
+// `fill` (slot = absolute index mod kWRing), refilled kWChunk words at a
+// time by cp.async (8 bytes per lane) well before they are read. A chunk
+// overwrites the slots of words kWRing above it, which are consumed once
+// (first unread word + 1) - fill <= kWRing - kWChunk. One step reads at most
+// 96 words (32 symbols plus two escape chunks each), fewer than kWChunk, so
+// one issue per step keeps up. Pieces outside [0, n_words) are zero-filled,
+// never read.
 constexpr int kWRing = 512, kWChunk = 128, kWMaxStep = 96;
 
 __device__ __forceinline__ void wring_issue(uint16_t* ring, const uint16_t* __restrict__ words, int64_t n_words,
@@ -207,21 +208,6 @@ __device__ __forceinline__ void wring_issue(uint16_t* ring, const uint16_t* __re
     asm volatile("cp.async.commit_group;\n" ::: "memory");
 }
 
-// refill_warp with the words read from the ring, without branches: every
-// lane reads a slot (an index inside the ring), the lanes that refill keep it.
-__device__ __forceinline__ void refill_ring(uint32_t& x, bool part, const uint16_t* ring, int64_t& ptr, int64_t beg,
-                                            bool& bad, uint32_t lt)
-{
-    const bool need = part && x < kL;
-    const uint32_t m = __ballot_sync(kFull, need);
-    const int64_t idx = ptr - __popc(m) + __popc(m & lt);
-    const uint32_t w = ring[(int)(idx & (kWRing - 1))];
-    const bool ok = idx >= beg;
-    bad |= need && !ok;
-    x = need ? (x << 16) | (ok ? w : 0u) : x;
-    ptr -= __popc(m);
-}
-
 // Level of every symbol's scale (uint8), and the scale check, ahead of the
 // decoder: the search over the levels leaves the decoder's serial chain.
 template <typename T>
@@ -233,10 +219,22 @@ __global__ void __launch_bounds__(256) fgmm_gsm_level_kernel(const T* __restrict
     if (threadIdx.x < kLmax) load_levels(blob, lvp, threadIdx.x);
     __syncthreads();
     bool bad = false;
-    for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x) {
-        const float sg = load_param(scales, n);
-        bad |= !scale_ok(sg);
-        lev[n] = (uint8_t)level_of(lvp, sg);
+    // four loads in flight per thread before the searches
+    for (int64_t b = blockIdx.x * (int64_t)blockDim.x * 4 + threadIdx.x; b < N; b += (int64_t)gridDim.x * blockDim.x * 4) {
+        float sg[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int64_t n = b + (int64_t)u * blockDim.x;
+            sg[u] = n < N ? load_param(scales, n) : 1.0f;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int64_t n = b + (int64_t)u * blockDim.x;
+            if (n < N) {
+                bad |= !scale_ok(sg[u]);
+                lev[n] = (uint8_t)level_of(lvp, sg[u]);
+            }
+        }
     }
     if (bad) set_error(err, kErrBadParams);
 }
@@ -280,102 +278,121 @@ __global__ void __launch_bounds__(1024, 1) fgmm_gsm_dec_kernel(const uint8_t* __
     uint16_t* ring = reinterpret_cast<uint16_t*>(sm + kBlobBytes) + (threadIdx.x >> 5) * kWRing;
     for (int64_t g = (int64_t)blockIdx.x * wpb + (threadIdx.x >> 5); g < nseg; g += (int64_t)gridDim.x * wpb) {
         const int64_t beg = offsets[g], end = offsets[g + 1];
-        if (!(beg >= 0 && end <= n_words && end - beg >= 64)) {
+        // a stream of fewer than 2^24 steps has fewer than 2^31 words
+        if (!(beg >= 0 && end <= n_words && end - beg >= 64 && end - beg < ((int64_t)1 << 31))) {
             if (lane == 0) set_error(err, kErrCorrupt);
             continue;
         }
         uint32_t x = (uint32_t)__ldg(words + end - 64 + 2 * lane) |
                      ((uint32_t)__ldg(words + end - 63 + 2 * lane) << 16);
-        int64_t ptr = end - 64;
-        // ring: the kWRing words below ptr rounded up to 4, loaded and waited for
-        int64_t fill = ((ptr + 3) & ~(int64_t)3) - kWRing;
+        // word indices relative to beg (32-bit); ring slot (bmod + i) mod kWRing
+        const int bmod = (int)(beg & (kWRing - 1));
+        int rp = (int)(end - 64 - beg);
+        // ring: the kWRing words below rp rounded up to 4 (absolute), loaded and waited for
+        int rf = (int)((((end - 64 + 3) & ~(int64_t)3) - kWRing) - beg);
 #pragma unroll
-        for (int c = 0; c < kWRing / kWChunk; ++c) wring_issue(ring, words, n_words, fill + c * kWChunk, lane);
+        for (int c = 0; c < kWRing / kWChunk; ++c) wring_issue(ring, words, n_words, beg + rf + c * kWChunk, lane);
         asm volatile("cp.async.wait_group 0;\n" ::: "memory");
         __syncwarp();
-        int64_t ready = fill;
+        int rready = rf;
         int pending = 0;
         bool bad = false;
         const int64_t n0 = g * 32 + lane;
         // steps of this lane's stream with a symbol: t < tn
-        const int64_t tn = n0 < N ? (N - n0 + S - 1) / S : 0;
-        const uint8_t* lp = lev + n0;
-        int32_t* op = out + n0;
+        const int tn = n0 < N ? (int)((N - n0 + S - 1) / S) : 0;
+        const int Ts = (int)T_steps;
+        const uint8_t* lnext = lev + n0 + (int64_t)kRing * S;   // level of step t + kRing
+        int32_t* op = out + n0;                                 // symbol of step t
         // levels of steps t .. t + kRing - 1 in registers, each loaded
         // kRing steps before it is used
         uint32_t lring[kRing];
 #pragma unroll
-        for (int k = 0; k < kRing; ++k) lring[k] = k < tn ? (uint32_t)__ldg(lp + (int64_t)k * S) : 0u;
-        for (int64_t t0 = 0; t0 < T_steps; t0 += kRing) {
-#pragma unroll
-            for (int k = 0; k < kRing; ++k) {
-                const int64_t t = t0 + k;
-                if (t >= T_steps) break;
-                const bool act = t < tn;
-                const int lvl = (int)min(lring[k], (uint32_t)(kLmax - 1));
-                lring[k] = t + kRing < tn ? (uint32_t)__ldg(lp + (t + kRing) * S) : 0u;
-                // words: issue the next chunk once its slots are consumed;
-                // wait only if this step could read below what has landed
-                if (ptr - fill <= kWRing - kWChunk && fill > beg) {
-                    fill -= kWChunk;
-                    wring_issue(ring, words, n_words, fill, lane);
-                    ++pending;
-                }
-                if (ptr - kWMaxStep < ready) {
-                    if (pending >= 2) {
-                        asm volatile("cp.async.wait_group 1;\n" ::: "memory");
-                        ready = fill + kWChunk;
-                        pending = 1;
-                    }
-                    if (ptr - kWMaxStep < ready) {
-                        asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-                        ready = fill;
-                        pending = 0;
-                    }
-                    __syncwarp();
-                }
-                // the bucket pair decides most slots; the row search runs
-                // only for lanes whose bucket holds more than one boundary
-                const uint32_t slot = x & 0xffffu;
-                const uint2* bk = sbkt + lvl * kBktStride + (slot >> 8);
-                const uint2 P = bk[0], Pn = bk[1];
-                // clamped so that a blob that was never built still reads
-                // inside its row
-                int j0 = min((int)(P.x & 0xffffu), kRow - 2);
-                int j1 = min(max((int)(Pn.x & 0xffffu) + 1, j0 + 1), kRow - 1);
-                uint32_t qa = P.x >> 16, qb = Pn.y;
-                const bool esc = act && slot >= qb;
-                bool srch = act && !esc && j1 - j0 > 1;
-                if (__any_sync(kFull, srch)) {
-                    const uint16_t* row = srow + lvl * kRow;
-                    while (srch) {
-                        const int mid = (j0 + j1) >> 1;
-                        const uint32_t qm = row[mid];
-                        if (qm <= slot) { j0 = mid; qa = qm; }
-                        else { j1 = mid; qb = qm; }
-                        srch = j1 - j0 > 1;
-                    }
-                }
-                const uint32_t st = esc ? qb : qa;
-                const uint32_t fr = esc ? kM - qb : qb - qa;
-                const uint32_t xn = fr * (x >> 16) + slot - st;
-                x = act ? xn : x;
-                int32_t s = j0 - kYmax;
-                refill_ring(x, act, ring, ptr, beg, bad, lt);
-                if (__any_sync(kFull, esc)) {
-                    uint32_t hi16 = 0, lo16 = 0;
-                    if (esc) { hi16 = x & 0xffffu; x >>= 16; }
-                    refill_ring(x, esc, ring, ptr, beg, bad, lt);
-                    if (esc) { lo16 = x & 0xffffu; x >>= 16; }
-                    refill_ring(x, esc, ring, ptr, beg, bad, lt);
-                    if (esc) s = (int32_t)((hi16 << 16) | lo16);
-                }
-                if (act) op[t * S] = s;
+        for (int k = 0; k < kRing; ++k) lring[k] = k < tn ? (uint32_t)__ldg(lev + n0 + (int64_t)k * S) : 0u;
+        auto refill = [&](bool part) {
+            const bool need = part && x < kL;
+            const uint32_t m = __ballot_sync(kFull, need);
+            const int c = __popc(m);
+            const int i = rp - c + __popc(m & lt);
+            const uint32_t w = ring[(bmod + i) & (kWRing - 1)];
+            bad |= need && i < 0;
+            x = need ? (x << 16) | (i >= 0 ? w : 0u) : x;
+            rp -= c;
+        };
+        auto step = [&](int t, uint32_t& lslot) {
+            const bool act = t < tn;
+            const int lvl = (int)min(lslot, (uint32_t)(kLmax - 1));
+            lslot = t + kRing < tn ? (uint32_t)__ldg(lnext) : 0u;
+            lnext += S;
+            // words: issue the next chunk once its slots are consumed; wait
+            // only if this step could read below what has landed
+            if (rp - rf <= kWRing - kWChunk && rf > 0) {
+                rf -= kWChunk;
+                wring_issue(ring, words, n_words, beg + rf, lane);
+                ++pending;
             }
+            if (rp - kWMaxStep < rready) {
+                if (pending >= 2) {
+                    asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+                    rready = rf + kWChunk;
+                    pending = 1;
+                }
+                if (rp - kWMaxStep < rready) {
+                    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+                    rready = rf;
+                    pending = 0;
+                }
+                __syncwarp();
+            }
+            // the bucket pair decides most slots; the row search runs only
+            // for lanes whose bucket holds more than one boundary
+            const uint32_t slot = x & 0xffffu;
+            const uint2* bk = sbkt + lvl * kBktStride + (slot >> 8);
+            const uint2 P = bk[0], Pn = bk[1];
+            // clamped so that a blob that was never built still reads inside
+            // its row
+            int j0 = min((int)(P.x & 0xffffu), kRow - 2);
+            int j1 = min(max((int)(Pn.x & 0xffffu) + 1, j0 + 1), kRow - 1);
+            uint32_t qa = P.x >> 16, qb = Pn.y;
+            const bool esc = act && slot >= qb;
+            bool srch = act && !esc && j1 - j0 > 1;
+            if (__any_sync(kFull, srch)) {
+                const uint16_t* row = srow + lvl * kRow;
+                while (srch) {
+                    const int mid = (j0 + j1) >> 1;
+                    const uint32_t qm = row[mid];
+                    if (qm <= slot) { j0 = mid; qa = qm; }
+                    else { j1 = mid; qb = qm; }
+                    srch = j1 - j0 > 1;
+                }
+            }
+            const uint32_t st = esc ? qb : qa;
+            const uint32_t fr = esc ? kM - qb : qb - qa;
+            const uint32_t xn = fr * (x >> 16) + slot - st;
+            x = act ? xn : x;
+            int32_t s = j0 - kYmax;
+            refill(act);
+            if (__any_sync(kFull, esc)) {
+                uint32_t hi16 = 0, lo16 = 0;
+                if (esc) { hi16 = x & 0xffffu; x >>= 16; }
+                refill(esc);
+                if (esc) { lo16 = x & 0xffffu; x >>= 16; }
+                refill(esc);
+                if (esc) s = (int32_t)((hi16 << 16) | lo16);
+            }
+            if (act) *op = s;
+            op += S;
+        };
+        int t = 0;
+        for (; t + kRing <= Ts; t += kRing) {
+#pragma unroll
+            for (int k = 0; k < kRing; ++k) step(t + k, lring[k]);
         }
+#pragma unroll
+        for (int k = 0; k < kRing; ++k)
+            if (t + k < Ts) step(t + k, lring[k]);
         asm volatile("cp.async.wait_group 0;\n" ::: "memory");   // the ring is reused by the next segment
         __syncwarp();
-        const bool fail = bad || x != kL || ptr != beg;
+        const bool fail = bad || x != kL || rp != 0;
         if (__ballot_sync(kFull, fail) && lane == 0) set_error(err, kErrCorrupt);
     }
 }
@@ -405,7 +422,7 @@ cudaError_t launch_dec(int32_t dtype, const void* scales, int64_t N, int32_t S, 
                        int32_t* err, int sms, cudaStream_t st)
 {
     if (N > 0) {
-        const int64_t blocks = (N + 255) / 256 < (int64_t)sms * 16 ? (N + 255) / 256 : (int64_t)sms * 16;
+        const int64_t blocks = (N + 1023) / 1024 < (int64_t)sms * 16 ? (N + 1023) / 1024 : (int64_t)sms * 16;
         if (dtype == FGMM_DTYPE_BF16)
             fgmm_gsm_level_kernel<__nv_bfloat16><<<(unsigned)blocks, 256, 0, st>>>(
                 static_cast<const __nv_bfloat16*>(scales), N, blob, lev, err);
@@ -519,6 +536,8 @@ fgmm_status fgmm_gsm_decode(fgmm_handle* h, int32_t dtype, int64_t N, const void
         return fail(h, FGMM_ERR_INVALID_ARG, "fgmm_gsm_decode: NULL buffer");
     if (n_words > 0 && (reinterpret_cast<uintptr_t>(words) & 7u) != 0)
         return fail(h, FGMM_ERR_INVALID_ARG, "fgmm_gsm_decode: words must be 8-byte aligned");
+    if (steps_of(N, S) >= ((int64_t)1 << 24))
+        return fail(h, FGMM_ERR_INVALID_ARG, "fgmm_gsm_decode: at most 2^24 - 1 steps per stream");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     // workspace: one level byte per symbol
     s = ws_reserve(h, (size_t)(N > 0 ? N : 1), st);
