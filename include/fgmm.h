@@ -215,8 +215,9 @@ fgmm_status fgmm_gsm_encode(fgmm_handle *h, int32_t dtype, int64_t N, const void
                             int64_t *n_words_out, void *stream);
 
 /* Decodes N residuals into device int32 symbols_out[N]; arguments and
- * errors as fgmm_decode, except that `words` must be 8-byte aligned
- * (FGMM_ERR_INVALID_ARG otherwise). The decoder stages the tables in shared memory
+ * errors as fgmm_decode, except that `words` must be 8-byte aligned and a
+ * stream may hold at most 2^24 - 1 symbols (ceil(N / S) < 2^24; both
+ * FGMM_ERR_INVALID_ARG otherwise). The decoder stages the tables in shared memory
  * (cp.async.bulk on an mbarrier whose wait is bounded: FGMM_ERR_TIMEOUT if
  * it gives up) and runs one lane per stream. */
 fgmm_status fgmm_gsm_decode(fgmm_handle *h, int32_t dtype, int64_t N, const void *scales, const void *tables,
