@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--no-throughput", action="store_true", help="skip the large-workload section")
     ap.add_argument("--batch-only", type=int, default=0, metavar="N",
                     help="run only the batch case on the first N latents of the 64-latent batch (for profiling)")
+    ap.add_argument("--gsm-only", action="store_true",
+                    help="run only the Gaussian-single-model case (for profiling its decoder)")
     ap.add_argument("--batch-overhead", type=float, default=0.01,
                     help="container-overhead bound given to the stream autotuner in --batch-only mode")
     return ap.parse_args()
@@ -802,10 +804,23 @@ def run_batch_only(args):
     print(json.dumps(out))
 
 
+def run_gsm_only(args):
+    import torch
+    from paper_2509_18815_gb300 import build, codec
+    build.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    h = codec.handle(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    print(json.dumps({"gsm_320x64x96": gsm_case(dev, h, flush, max(args.steps, 1))}))
+
+
 def main():
     args = parse()
     if args.batch_only > 0:
         run_batch_only(args)
+    elif args.gsm_only:
+        run_gsm_only(args)
     elif args.impl == "reference":
         run_reference(args)
     else:
