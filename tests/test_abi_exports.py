@@ -49,3 +49,17 @@ def test_host_only_entry_points(lib_path):
     assert _abi.fgmm_encode_bound_words(33, 32) == 3 * 32 * 2 + 64
     assert _abi.fgmm_encode_bound_words(10, 48) == -1
     assert _abi.fgmm_status_string(4) == b"corrupt or truncated stream"
+
+
+def test_host_only_gsm_and_checkerboard_entry_points(lib_path):
+    import numpy as np
+
+    import oracle
+    from paper_2509_18815_gb300 import _abi
+    assert _abi.fgmm_gsm_tables_bytes() == 198144
+    lv = np.empty(64, np.float32)
+    _abi.fgmm_gsm_default_levels(lv.ctypes.data_as(ctypes.c_void_p))
+    np.testing.assert_array_equal(lv.view(np.uint32), oracle.gsm_levels().view(np.uint32))
+    for shape in [(3, 5, 5), (2, 4, 6), (1, 1, 1), (0, 3, 3), (4, 7, 1)]:
+        assert _abi.fgmm_ckbd_anchors(*shape) == oracle.ckbd_counts(shape)[0]
+    assert _abi.fgmm_ckbd_anchors(-1, 2, 2) == -1
