@@ -47,6 +47,7 @@ constexpr uint32_t kBktBytes = kLmax * kBktStride * 8;                  // 13209
 constexpr uint32_t kBlobBytes = kBktOff + kBktBytes;                    // 198144
 constexpr uint32_t kDecSmem = kBlobBytes;                               // same layout in shared memory
 constexpr uint32_t kWaitLimit = 1u << 22;
+constexpr uint64_t kWaitNs = 1000000000ull;                              // 1 s
 constexpr int kRing = 8;                                                // scale prefetch depth (steps)
 
 struct GsmLevels {
@@ -171,8 +172,19 @@ __global__ void __launch_bounds__(256) fgmm_gsm_interval_kernel(const T* __restr
 // 32-stream segment, one lane per stream, persistent over segments; each
 // warp reads its segment's words through a shared-memory ring.
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Waits for phase `parity` of the mbarrier; gives up after `limit` tries or
+// kWaitNs nanoseconds, whichever comes first (each try may suspend the
+// thread for a hardware-defined time).
 __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, uint32_t limit)
 {
+    const uint64_t t0 = global_ns();
     for (uint32_t i = 0; i < limit; ++i) {
         uint32_t done;
         asm volatile(
@@ -181,6 +193,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, uint32
             : "r"(mbar), "r"(parity)
             : "memory");
         if (done) return true;
+        if (global_ns() - t0 > kWaitNs) return false;
     }
     return false;
 }
