@@ -581,6 +581,53 @@ def run_fgmm(args):
     ms_dec = statistics.mean(ev[i][2].elapsed_time(ev[i][3]) for i in range(args.steps))
     ms_step, ms_enc, ms_dec = max_over_ranks([ms_step, ms_enc, ms_dec], device=dev)
 
+    # service throughput: D steps decoding at once (step i's decode on
+    # stream i mod D, each with its own handle), encode overlapping as above;
+    # per-launch decode time grows as the decodes share SMs
+    concurrency = {}
+    conc_steps = max(R, min(args.steps, 100))
+    hD_all = [hB] + [codec.Handle(dev) for _ in range(2)]
+    sD_all = [sB] + [torch.cuda.Stream(dev) for _ in range(2)]
+    for hx in hD_all[1:]:
+        hx.check(_abi.fgmm_set_option(hx.ptr, _abi.FGMM_OPT_DECODE_LANES, args.decode_lanes))
+    for D in (2, 3):
+        for rep in range(2):   # the first pass grows the new handles' workspaces
+            enc_done = [torch.cuda.Event() for _ in range(conc_steps)]
+            dec_done = [torch.cuda.Event() for _ in range(conc_steps)]
+            dev_ev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(conc_steps)]
+            torch.cuda.synchronize()
+            c0 = torch.cuda.Event(enable_timing=True)
+            c0.record(sA)
+            for sx in sD_all[:D]:
+                sx.wait_event(c0)
+            for i in range(conc_steps):
+                r, sx, hx = i % R, sD_all[i % D], hD_all[i % D]
+                if i >= R:
+                    sA.wait_event(dec_done[i - R])
+                enc_slot(r)
+                enc_done[i].record(sA)
+                sx.wait_event(enc_done[i])
+                dev_ev[i][0].record(sx)
+                hx.check(_abi.fgmm_decode(hx.ptr, ctypes.byref(slot_desc[r]), slot_w[r].data_ptr(), cap,
+                                          slot_o[r].data_ptr(), S, slot_out[r].data_ptr(),
+                                          ctypes.c_void_p(sx.cuda_stream)))
+                dev_ev[i][1].record(sx)
+                dec_done[i].record(sx)
+            ends = []
+            for sx in sD_all[:D]:
+                c1 = torch.cuda.Event(enable_timing=True)
+                c1.record(sx)
+                ends.append(c1)
+            torch.cuda.synchronize()
+        for hx in [h] + hD_all[:D]:
+            hx.sync()
+        for r in range(R):
+            assert torch.equal(slot_out[r], ds), "round trip failed with concurrent decodes"
+        ms_c = max(c0.elapsed_time(c1) for c1 in ends) / conc_steps
+        concurrency[str(D)] = {"value": world * N / (ms_c * 1e-3) / 1e6, "ms_per_step": ms_c,
+                               "ms_decode_launch": statistics.mean(dev_ev[i][0].elapsed_time(dev_ev[i][1])
+                                                                   for i in range(conc_steps))}
+
     # the same steps one after another on one stream, L2 flushed before each
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     ser_steps = max(3, min(args.steps, 50))
@@ -812,6 +859,7 @@ def run_fgmm(args):
         "config": {"workload": WORKLOAD["name"], "symbols": N, "K": K, "S": S, "params": "fp32",
                    "l2": f"inputs larger than L2: {R} rotating buffer sets, {R * slot_bytes / 1e6:.0f} MB",
                    "schedule": "step i+1's encode overlaps step i's decode on a second stream (own handle)"},
+        "concurrent_decodes": concurrency,
         "serial": {"value": world * N / ((ser_enc + ser_dec) * 1e-3) / 1e6, "ms_per_step": ser_enc + ser_dec,
                    "ms_encode": ser_enc, "ms_decode": ser_dec,
                    "l2": "flushed before each step (256 MiB write outside the timed events)"},
