@@ -50,18 +50,26 @@ __device__ __forceinline__ void store_rank(uint32_t* local, uint32_t r, uint32_t
 }
 
 // One refill exchange of the segment, called by every lane of every
-// consumer warp. Lane j (< CL) of the group of stream ws posts that stream's
-// flags (bit 0 refill, bit 1 escape) to CTA j. Returns, in lane q, stream
-// q's flags for exchange e. posts is false only for the stream that the
-// FGMM_OPT_TEST_SILENT_STREAM hook silences, to make the others' waits run
-// out in a test.
+// consumer warp, in two halves so that work can run between them. Post: lane
+// j (< CL) of the group of stream ws posts that stream's flags (bit 0
+// refill, bit 1 escape) to CTA j; posts is false only for the stream that
+// the FGMM_OPT_TEST_SILENT_STREAM hook silences, to make the others' waits
+// run out in a test. Wait: returns, in lane q, stream q's flags for
+// exchange e.
 template <int CL>
-__device__ __forceinline__ uint32_t exchange(uint32_t* xflag, uint32_t* abort_flag, uint32_t e, int ws, int j,
-                                             int lane, uint32_t bits, int32_t* err, bool posts)
+__device__ __forceinline__ void exchange_post(uint32_t* xflag, uint32_t e, int ws, int j, uint32_t bits, bool posts)
 {
     uint32_t* slot = xflag + (e & 1u) * 32;
     const uint32_t tag = e & 0x3fffffffu;
     if (posts && j < CL) store_rank(slot + ws, (uint32_t)j, (tag << 2) | bits);
+}
+
+template <int CL>
+__device__ __forceinline__ uint32_t exchange_wait(uint32_t* xflag, uint32_t* abort_flag, uint32_t e, int lane,
+                                                  int32_t* err)
+{
+    uint32_t* slot = xflag + (e & 1u) * 32;
+    const uint32_t tag = e & 0x3fffffffu;
     const volatile uint32_t* vs = slot;
     const volatile uint32_t* va = abort_flag;
     for (uint32_t spin = 0;; ++spin) {
@@ -74,6 +82,14 @@ __device__ __forceinline__ uint32_t exchange(uint32_t* xflag, uint32_t* abort_fl
             return 0u;
         }
     }
+}
+
+template <int CL>
+__device__ __forceinline__ uint32_t exchange(uint32_t* xflag, uint32_t* abort_flag, uint32_t e, int ws, int j,
+                                             int lane, uint32_t bits, int32_t* err, bool posts)
+{
+    exchange_post<CL>(xflag, e, ws, j, bits, posts);
+    return exchange_wait<CL>(xflag, abort_flag, e, lane, err);
 }
 
 // Refill of one sub-step: M holds the segment's refill bits (stream q at
@@ -309,13 +325,13 @@ __global__ void __launch_bounds__(32 * (32 / CL / SPW + 32 / CL * R0 / 32))
                 x = freq * (x >> 16) + slot - start;
                 decoded += (j == 0);
             }
-            // step t + 1's round (produced two barriers ago) overlaps the
-            // exchange
-            if (t + 1 < T_steps) fetch(t + 1, m, q0);
+            // post this step's flags, then fetch step t + 1's round
+            // (produced two barriers ago) while they travel
             const bool need = act && x < kL;
             const uint32_t below = bit - 1u;
-            const uint32_t f =
-                exchange<CL>(xflag, abort_flag, e++, ws, j, lane, (need ? 1u : 0u) | (esc ? 2u : 0u), err, posts);
+            exchange_post<CL>(xflag, e, ws, j, (need ? 1u : 0u) | (esc ? 2u : 0u), posts);
+            if (t + 1 < T_steps) fetch(t + 1, m, q0);
+            const uint32_t f = exchange_wait<CL>(xflag, abort_flag, e++, lane, err);
             const uint32_t M = __ballot_sync(kFull, f & 1u), E = __ballot_sync(kFull, f & 2u);
             ws_refill(x, need, M, below, wsrc, wbase, ptr, beg, bad);
             if (E) {   // the same in every stream of the segment
