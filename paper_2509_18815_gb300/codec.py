@@ -67,7 +67,23 @@ def _stream(stream=None):
 
 
 def _ptr(t: torch.Tensor):
+    """Device pointer of a CUDA tensor (every pointer the C ABI takes from
+    here is a device pointer; a host tensor is refused, not passed on)."""
+    if t.numel() > 0 and not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
     return ctypes.c_void_p(t.data_ptr() if t.numel() > 0 else 0)
+
+
+def _tables(tables: torch.Tensor) -> torch.Tensor:
+    """A GSM tables blob: a contiguous CUDA tensor of at least
+    fgmm_gsm_tables_bytes() bytes, 16-byte aligned."""
+    if not tables.is_cuda or not tables.is_contiguous():
+        raise ValueError("tables must be a contiguous CUDA tensor")
+    if tables.numel() * tables.element_size() < int(_abi.fgmm_gsm_tables_bytes()):
+        raise ValueError("tables is smaller than fgmm_gsm_tables_bytes()")
+    if tables.data_ptr() % 16:
+        raise ValueError("tables must be 16-byte aligned")
+    return tables
 
 
 def latent(params: torch.Tensor) -> _abi.fgmm_latent:
@@ -265,7 +281,7 @@ def gsm_freqs(scales, symbols, tables, h: Handle | None = None) -> torch.Tensor:
     dt = _scales(scales)
     sym = symbols.to(torch.int32).contiguous()
     sf = torch.empty(scales.numel(), dtype=torch.int32, device=scales.device)
-    h.check(_abi.fgmm_gsm_freqs(h.ptr, dt, scales.numel(), _ptr(scales), _ptr(sym), _ptr(tables), _ptr(sf),
+    h.check(_abi.fgmm_gsm_freqs(h.ptr, dt, scales.numel(), _ptr(scales), _ptr(sym), _ptr(_tables(tables)), _ptr(sf),
                                 _stream()))
     h.sync()
     return sf
@@ -283,7 +299,7 @@ def gsm_encode(scales, symbols, S: int, tables, h: Handle | None = None, sync: b
     words = torch.empty(max(cap, 1), dtype=torch.int16, device=scales.device)
     offsets = torch.empty(S // 32 + 1, dtype=torch.int64, device=scales.device)
     total = torch.empty(1, dtype=torch.int64, device=scales.device)
-    h.check(_abi.fgmm_gsm_encode(h.ptr, dt, N, _ptr(scales), _ptr(sym), S, _ptr(tables), _ptr(words), cap,
+    h.check(_abi.fgmm_gsm_encode(h.ptr, dt, N, _ptr(scales), _ptr(sym), S, _ptr(_tables(tables)), _ptr(words), cap,
                                  _ptr(offsets), _ptr(total), _stream()))
     if not sync:
         return words, offsets, total
@@ -300,7 +316,7 @@ def gsm_decode(scales, words, offsets, S: int, tables, h: Handle | None = None, 
     offsets = offsets.to(torch.int64).contiguous()
     if out is None:
         out = torch.empty(N, dtype=torch.int32, device=scales.device)
-    h.check(_abi.fgmm_gsm_decode(h.ptr, dt, N, _ptr(scales), _ptr(tables), _ptr(words), words.numel(),
+    h.check(_abi.fgmm_gsm_decode(h.ptr, dt, N, _ptr(scales), _ptr(_tables(tables)), _ptr(words), words.numel(),
                                  _ptr(offsets), S, _ptr(out), _stream()))
     if sync:
         h.sync()
@@ -416,7 +432,8 @@ class Batch:
         lats = (_abi.fgmm_batch_latent * max(n, 1))()
         for i, (p, s, d) in enumerate(zip(self.params, self.symbols, self.decoded)):
             base = latent(p)
-            lats[i] = _abi.fgmm_batch_latent(base.K, base.dtype, base.N, base.params, s.data_ptr(), d.data_ptr())
+            lats[i] = _abi.fgmm_batch_latent(base.K, base.dtype, base.N, base.params, _ptr(s).value or 0,
+                                             _ptr(d).value or 0)
         s_arr = None
         if S is not None:
             s_arr = (ctypes.c_int32 * max(n, 1))(*[int(x) for x in S])

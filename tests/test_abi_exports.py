@@ -63,3 +63,16 @@ def test_host_only_gsm_and_checkerboard_entry_points(lib_path):
     for shape in [(3, 5, 5), (2, 4, 6), (1, 1, 1), (0, 3, 3), (4, 7, 1)]:
         assert _abi.fgmm_ckbd_anchors(*shape) == oracle.ckbd_counts(shape)[0]
     assert _abi.fgmm_ckbd_anchors(-1, 2, 2) == -1
+
+
+def test_binding_refuses_host_tensors_before_any_launch():
+    """Every pointer the binding hands to the C ABI is a device pointer: a
+    host tensor is refused in Python, so it never reaches a kernel."""
+    import torch
+
+    from paper_2509_18815_gb300 import codec
+    with pytest.raises(ValueError):
+        codec._ptr(torch.zeros(4, dtype=torch.int32))
+    assert codec._ptr(torch.zeros(0, dtype=torch.int32)).value is None
+    with pytest.raises(ValueError):
+        codec._tables(torch.zeros(198144, dtype=torch.uint8))

@@ -201,6 +201,13 @@ def test_errors_are_reported():
     with pytest.raises(FgmmError) as e:
         codec.gsm_decode(ds, junk, off, 64, blob)
     assert e.value.status == FGMM_ERR_CORRUPT
+    # the binding refuses a blob that is too small or on the host, and host symbols
+    with pytest.raises(ValueError):
+        codec.gsm_decode(ds, words, off, 64, blob[:1000])
+    with pytest.raises(ValueError):
+        codec.gsm_encode(ds, dq, 64, blob.cpu())
+    with pytest.raises(ValueError):
+        codec.gsm_encode(ds, dq.cpu(), 64, blob)
     # a blob that was never built decodes garbage but stays in bounds
     raw = torch.randint(0, 255, (BLOB,), dtype=torch.uint8, device="cuda")
     try:
