@@ -148,7 +148,9 @@ def test_full_size_latent_round_trip_and_sampled_intervals():
     idx = np.random.default_rng(5).choice(lat.N, 20000, replace=False)
     po, _ = oracle.gsm_params(sig_o[idx])
     np.testing.assert_array_equal(host_u32(codec.gsm_freqs(ds, dq, blob))[idx], oracle.freqs(po, lat.symbols[idx]))
-    for S in (1024, 8192, 65536):
+    # 262144 streams: 8192 segments, more than one warp per segment slot of
+    # the grid, so decoder warps loop over segments
+    for S in (1024, 8192, 65536, 262144):
         words, off = codec.gsm_encode(ds, dq, S, blob)
         np.testing.assert_array_equal(codec.gsm_decode(ds, words, off, S, blob).cpu().numpy(), lat.symbols)
 
