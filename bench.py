@@ -893,7 +893,11 @@ def run_fgmm(args):
                      "unit": "Tops/s (FP32 lane ops)", "frac": achieved / alu_peak,
                      "traffic": DECODE_TRAFFIC_BYTES.get(f'{plan["kernel"]}/{plan["lanes"]}/{plan["cluster"]}/{plan["round0"]}'),
                      "peak_source": f"derived: {props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
-                                    f"{sm_max:.0f} MHz"},
+                                    f"{sm_max:.0f} MHz",
+                     # the decode is a chain of dependent steps per stream:
+                     # its time per step at the sampled SM clock
+                     "steps_per_stream": -(-N // S),
+                     "cycles_per_step": ms_dec * 1e-3 * (clk["sm_mhz"] if clk else sm_max) * 1e6 / -(-N // S)},
         "clocks": clk,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
