@@ -134,15 +134,18 @@ def encode_bound_words(N: int, S: int) -> int:
     return int(_abi.fgmm_encode_bound_words(N, S))
 
 
-def encode(params: torch.Tensor, symbols: torch.Tensor, S: int, h: Handle | None = None,
+def encode(params: torch.Tensor, symbols: torch.Tensor, S: int | None = None, h: Handle | None = None,
            words_cap: int | None = None, sync: bool = True):
-    """Encode one latent into S interleaved rANS streams.
+    """Encode one latent into S interleaved rANS streams (S = None: the
+    autotuner's choice for this latent; S = 32 * (len(offsets) - 1)).
 
     Returns (words uint16-as-int16 tensor trimmed to its length, offsets int64
     [S/32 + 1]). With sync=False returns the untrimmed buffer, offsets and the
     device total, without synchronising."""
     h = h or handle(params.device)
     lat = latent(params)
+    if S is None:
+        S = autotune([lat.N], h=h)[0]
     sym = symbols.to(torch.int32).contiguous()
     cap = encode_bound_words(lat.N, S) if words_cap is None else words_cap
     if cap < 0:
@@ -158,13 +161,18 @@ def encode(params: torch.Tensor, symbols: torch.Tensor, S: int, h: Handle | None
     return words[: int(total.item())], offsets
 
 
-def decode(params: torch.Tensor, words: torch.Tensor, offsets: torch.Tensor, S: int,
+def decode(params: torch.Tensor, words: torch.Tensor, offsets: torch.Tensor, S: int | None = None,
            h: Handle | None = None, out: torch.Tensor | None = None, sync: bool = True) -> torch.Tensor:
-    """Decode one latent; returns int32 symbols [N]."""
+    """Decode one latent; returns int32 symbols [N]. S = None takes
+    32 * (len(offsets) - 1)."""
     h = h or handle(params.device)
     lat = latent(params)
     words = words.contiguous()
     offsets = offsets.to(torch.int64).contiguous()
+    if S is None:
+        S = 32 * (offsets.numel() - 1)
+    elif offsets.numel() != S // 32 + 1:
+        raise ValueError("offsets must hold S/32 + 1 entries")
     if out is None:
         out = torch.empty(lat.N, dtype=torch.int32, device=params.device)
     h.check(_abi.fgmm_decode(h.ptr, ctypes.byref(lat), _ptr(words), words.numel(), _ptr(offsets), S, _ptr(out),

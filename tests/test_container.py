@@ -72,3 +72,7 @@ def test_gpu_streams_through_the_container():
     w = torch.from_numpy(c["words"].view(np.int16).copy()).cuda()
     o = torch.from_numpy(c["offsets"]).cuda()
     assert torch.equal(codec.decode(dp, w, o, c["S"]), ds)
+    # S chosen by the autotuner on encode and read from the offsets on decode
+    words, offsets = codec.encode(dp, ds)
+    assert (offsets.numel() - 1) * 32 == codec.autotune([lat.N])[0]
+    assert torch.equal(codec.decode(dp, words, offsets), ds)
