@@ -30,18 +30,67 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOAD = dict(name="latent_192x32x48_k3_s1024", C=192, H=32, W=48, K=3, S=1024, seed=1002)
-# FP32 operations per quantised-CDF evaluation, counted from the definition:
-# per component: z (sub, mul), clamp (2), grid rounding (3), |.|, 1+px (fma),
-# reciprocal, Horner (4 fma), *t, x*x and *-1/2 (2), exp (mul, rint, 2 fma,
-# 7 fma, exponent add), q (mul), mirror (2), weight fma = 32;
-# per evaluation: b = j - 1/2 (2), min(., 1), *T', floor, convert, add (5).
-OPS_PER_COMPONENT = 32
-OPS_PER_EVAL = 7
+# FP32 operations per Phi-hat evaluation, the fixed count of the method's
+# arithmetic (1 division, 5 Horner fmaf, exp ~12, clamp/select/accumulate
+# ~10); a quantised-CDF evaluation takes K of them. The kernels issue more
+# instructions than this (about 34 per component: the reciprocal's Newton
+# step, the grid rounding, the exponent scaling and integer conversions are
+# separate instructions); the roofline numerator counts the method's work,
+# not the instructions.
+OPS_PER_PHI = 28
 FP32_LANES_PER_SM = 128
+# Rotating input sets of the timed loop (more than L2 holds).
+ROTATE_SETS = 16
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of
 # the decoder the plan names, from the ncu captures summarised under
 # profiles/; valid for each kernel as captured there (null otherwise).
 DECODE_TRAFFIC_BYTES = {"fgmm_dec_ws_kernel/16/4/16": 10794240}   # "kernel/lanes/cluster/round0": bytes per launch
+
+
+def ops_per_eval(K: int) -> int:
+    """FP32 operations of one quantised-CDF evaluation (K Phi-hat)."""
+    return OPS_PER_PHI * K
+
+
+def slot_bytes(N: int, K: int, S: int) -> int:
+    """Device bytes of one input/output set of the timed loop: fp32
+    parameters, symbols, the encode bound of words, offsets, decoded
+    symbols."""
+    T = -(-N // S)
+    cap = (S // 32) * (3 * 32 * T + 64)
+    return 3 * K * N * 4 + 4 * N + 2 * cap + 8 * (S // 32 + 1) + 4 * N
+
+
+def workload_config(N: int, K: int, S: int) -> dict:
+    """The config dict both arms print (same workload, same keys)."""
+    return {"workload": WORKLOAD["name"], "symbols": N, "K": K, "S": S, "params": "fp32",
+            "l2": f"inputs larger than L2: {ROTATE_SETS} rotating buffer sets, "
+                  f"{ROTATE_SETS * slot_bytes(N, K, S) / 1e6:.0f} MB"}
+
+
+def host_cpu():
+    """Core count and CPU model of this host."""
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    info = {}
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if ":" in line:
+                k, v = line.split(":", 1)
+                info.setdefault(k.strip(), v.strip())
+    except Exception:
+        pass
+    model = info.get("Model name")
+    if model is None:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.lower().startswith(("model name", "cpu part")):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except Exception:
+            pass
+    return {"nproc": cores, "model": model or "unknown", "vendor": info.get("Vendor ID", "unknown"),
+            "machine": os.uname().machine}
 
 
 def parse():
@@ -131,21 +180,35 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def cpu_baseline(lat, S, budget_s=8.0):
-    """The CPU oracle (single thread, as it stands) on the same latent."""
+def _oracle_round_trips(lat, S, threads, budget_s):
+    """Encode + decode round trips of the whole latent with the oracle on
+    `threads` host threads (segments spread over them), until budget_s has
+    passed; returns (round trips, seconds)."""
     import oracle
     t0 = time.perf_counter()
     reps = 0
     while True:
-        words, offsets = oracle.encode(lat.params, lat.symbols, S)
-        out, st = oracle.decode(lat.params, words, offsets, S)
+        words, offsets = oracle.encode(lat.params, lat.symbols, S, threads=threads)
+        out, st = oracle.decode(lat.params, words, offsets, S, threads=threads)
         assert st == 0
         reps += 1
         if time.perf_counter() - t0 >= budget_s:
             break
-    dt = time.perf_counter() - t0
-    return {"value": reps * lat.N / dt / 1e6, "unit": "Msymbols/s", "cores": 1, "kind": "oracle",
-            "sample": f"{reps} encode+decode round trip(s) of the full {lat.N}-symbol latent, single thread"}
+    return reps, time.perf_counter() - t0
+
+
+def cpu_baseline(lat, S, budget_s=6.0):
+    """The CPU oracle, as it stands, on the same latent: on all host cores
+    (its segments spread over one thread per core) and on one thread."""
+    host = host_cpu()
+    n = host["nproc"]
+    r1, t1 = _oracle_round_trips(lat, S, 1, budget_s)
+    rn, tn = _oracle_round_trips(lat, S, n, budget_s)
+    return {"value": rn * lat.N / tn / 1e6, "unit": "Msymbols/s", "cores": n, "kind": "oracle",
+            "sample": f"{rn} encode+decode round trip(s) of the full {lat.N}-symbol latent, segments over {n} threads",
+            "single_thread": {"value": r1 * lat.N / t1 / 1e6, "unit": "Msymbols/s", "cores": 1,
+                              "sample": f"{r1} round trip(s) of the full latent on one thread"},
+            "host": host}
 
 
 def _events_ms(fn, reps, flush=None):
@@ -162,6 +225,27 @@ def _events_ms(fn, reps, flush=None):
         torch.cuda.synchronize()
         ts.append(a.elapsed_time(b))
     return statistics.median(ts)
+
+
+def measure_alu_peaks(dev, h, reps=5):
+    """Measured FP32 FMA and XU reciprocal throughput of this GPU, in
+    T lane-ops/s: the library's throughput probe (independent instruction
+    chains on every SM) timed with CUDA events on its stream."""
+    import torch
+    from paper_2509_18815_gb300 import _abi, codec
+    sink = torch.zeros(1, dtype=torch.float32, device=dev)
+    res = {}
+    for name, kind, iters in (("fma", _abi.FGMM_PEAK_FMA, 32), ("rcp", _abi.FGMM_PEAK_RCP, 64)):
+        ops = [0.0]
+
+        def run():
+            ops[0] = codec.peak_probe(kind, iters, sink, h)
+
+        for _ in range(3):
+            run()
+        ms = _events_ms(run, reps)
+        res[name] = ops[0] / (ms * 1e-3) / 1e12
+    return res
 
 
 def batch_case(dev, h, out, name, lats, alu_peak_tops, hbm_gbs, reps=5, max_overhead=0.01):
@@ -189,8 +273,8 @@ def batch_case(dev, h, out, name, lats, alu_peak_tops, hbm_gbs, reps=5, max_over
         coded += codec.rate_audit(p_, s_, h)[1]
     b.close()
     bytes_sym = 36.0 + 4.0 + 16.0 * nw / N / 8.0
-    enc_ops = 2 * N * (32 * 3 + 7)
-    dec_ops = evals * (32 * 3 + 7)
+    enc_ops = 2 * N * ops_per_eval(3)
+    dec_ops = evals * ops_per_eval(3)
     out[name] = {
         "symbols": N, "latents": len(lats), "segments": sum(s // 32 for s in b.S),
         "encode_msym_s": N / te / 1e3, "decode_msym_s": N / td / 1e3, "ms_encode": te, "ms_decode": td,
@@ -324,7 +408,7 @@ def throughput_workloads(dev, alu_peak_tops, hbm_gbs, reps=5):
         td3 = _events_ms(lambda: codec.decode(dp3, w3, o3, S3, h=h, out=out3, sync=False), reps, flush)
         ideal3, coded3, maxerr3, nesc3 = codec.rate_audit(dp3, ds3, h)
         N3 = lat3.N
-        ops_eval = 32 * K3 + 7
+        ops_eval = ops_per_eval(K3)
         bytes_sym = 3 * K3 * (2 if bf16 else 4) + 4 + 16.0 * w3.numel() / N3 / 8.0
         out[f"latent_320x64x96_k{K3}_{'bf16' if bf16 else 'fp32'}"] = {
             "symbols": N3, "S": S3, "segments": S3 // 32, "decoder": codec.decode_plan(S3, h=h),
@@ -422,6 +506,9 @@ def throughput_workloads(dev, alu_peak_tops, hbm_gbs, reps=5):
 
 
 def run_reference(args):
+    """The reference arm: the CPU oracle as it stands, on all host cores, one
+    encode + decode of the full headline latent per step; the one-thread
+    figure is reported beside it."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
@@ -430,25 +517,32 @@ def run_reference(args):
     oracle.build()
     lat = synth.make_latent(WORKLOAD["C"], WORKLOAD["H"], WORKLOAD["W"], WORKLOAD["K"], WORKLOAD["seed"])
     S = WORKLOAD["S"]
+    host = host_cpu()
+    threads = host["nproc"]
     for _ in range(args.warmup):
-        w, o = oracle.encode(lat.params, lat.symbols, S)
-        oracle.decode(lat.params, w, o, S)
+        w, o = oracle.encode(lat.params, lat.symbols, S, threads=threads)
+        oracle.decode(lat.params, w, o, S, threads=threads)
     times = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        w, o = oracle.encode(lat.params, lat.symbols, S)
-        out, st = oracle.decode(lat.params, w, o, S)
+        w, o = oracle.encode(lat.params, lat.symbols, S, threads=threads)
+        out, st = oracle.decode(lat.params, w, o, S, threads=threads)
         times.append(time.perf_counter() - t0)
         assert st == 0
     ms = 1e3 * sum(times) / len(times)
     value = lat.N / (ms * 1e-3) / 1e6
+    r1, t1 = _oracle_round_trips(lat, S, 1, 2.0)
     print(json.dumps({
         "impl": "reference", "metric": "encode+decode Msymbols/s (round trip)", "value": value,
         "unit": "Msymbols/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD["name"], "symbols": lat.N, "K": 3, "S": S, "params": "fp32"},
-        "cpu_baseline": {"value": value, "unit": "Msymbols/s", "cores": 1, "kind": "oracle",
-                         "sample": f"each step one encode+decode of the full {lat.N}-symbol latent"},
+        "config": workload_config(lat.N, WORKLOAD["K"], S),
+        "cpu_baseline": {"value": value, "unit": "Msymbols/s", "cores": threads, "kind": "oracle",
+                         "sample": f"each step one encode+decode of the full {lat.N}-symbol latent, "
+                                   f"segments over {threads} threads",
+                         "single_thread": {"value": r1 * lat.N / t1 / 1e6, "unit": "Msymbols/s", "cores": 1,
+                                           "sample": f"{r1} round trip(s) of the full latent on one thread"},
+                         "host": host},
         "e2e": {"value": value, "unit": "Msymbols/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
 
@@ -491,6 +585,7 @@ def run_fgmm(args):
         h.check(_abi.fgmm_decode(h.ptr, L, words.data_ptr(), cap, offsets.data_ptr(), S, out.data_ptr(), sptr))
 
     launches_per_step = 4 + 1   # interval, rANS encode, scan, compaction; decode
+    alu_peaks = measure_alu_peaks(dev, h)
 
     # correctness gate and algorithmic work (CDF evaluations) outside timing
     enc(); dec(); h.sync()
@@ -511,7 +606,7 @@ def run_fgmm(args):
     # Step i+1's encode (stream A, handle h) overlaps step i's decode (stream
     # B, a second handle with its own workspace); the inputs rotate over R
     # buffer sets that together exceed L2, so no step finds its data there.
-    R = 16
+    R = ROTATE_SETS
     hB = codec.Handle(dev)
     hB.check(_abi.fgmm_set_option(hB.ptr, _abi.FGMM_OPT_DECODE_LANES, args.decode_lanes))
     sA, sB = stream, torch.cuda.Stream(dev)
@@ -523,7 +618,8 @@ def run_fgmm(args):
     slot_o = [offsets] + [torch.empty_like(offsets) for _ in range(R - 1)]
     slot_t = [total] + [torch.empty_like(total) for _ in range(R - 1)]
     slot_out = [out] + [torch.empty_like(out) for _ in range(R - 1)]
-    slot_bytes = sum(x[0].numel() * x[0].element_size() for x in (slot_dp, slot_ds, slot_w, slot_o, slot_out))
+    assert sum(x[0].numel() * x[0].element_size() for x in (slot_dp, slot_ds, slot_w, slot_o, slot_out)) == \
+        slot_bytes(N, K, S)
 
     def enc_slot(r):
         h.check(_abi.fgmm_encode(h.ptr, ctypes.byref(slot_desc[r]), slot_ds[r].data_ptr(), S, slot_w[r].data_ptr(),
@@ -843,8 +939,9 @@ def run_fgmm(args):
     props = torch.cuda.get_device_properties(dev)
     peaks = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    alu_peak = props.multi_processor_count * FP32_LANES_PER_SM * sm_max * 1e6 / 1e12   # Tops/s
-    ops = cdf_evals * (OPS_PER_COMPONENT * K + OPS_PER_EVAL)
+    alu_derived = props.multi_processor_count * FP32_LANES_PER_SM * sm_max * 1e6 / 1e12   # Tops/s
+    alu_peak = alu_peaks["fma"]
+    ops = cdf_evals * ops_per_eval(K)
     achieved = ops / (ms_dec * 1e-3) / 1e12
     result = {
         "metric": "encode+decode Msymbols/s (round trip)",
@@ -859,9 +956,8 @@ def run_fgmm(args):
         "vs_baseline": None,
         "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD["name"], "symbols": N, "K": K, "S": S, "params": "fp32",
-                   "l2": f"inputs larger than L2: {R} rotating buffer sets, {R * slot_bytes / 1e6:.0f} MB",
-                   "schedule": "step i+1's encode overlaps step i's decode on a second stream (own handle)"},
+        "config": workload_config(N, K, S),
+        "schedule": "step i+1's encode overlaps step i's decode on a second stream (own handle)",
         "concurrent_decodes": concurrency,
         "serial": {"value": world * N / ((ser_enc + ser_dec) * 1e-3) / 1e6, "ms_per_step": ser_enc + ser_dec,
                    "ms_encode": ser_enc, "ms_decode": ser_dec,
@@ -892,8 +988,14 @@ def run_fgmm(args):
                      "bound": "alu", "achieved": achieved, "peak": alu_peak,
                      "unit": "Tops/s (FP32 lane ops)", "frac": achieved / alu_peak,
                      "traffic": DECODE_TRAFFIC_BYTES.get(f'{plan["kernel"]}/{plan["lanes"]}/{plan["cluster"]}/{plan["round0"]}'),
-                     "peak_source": f"derived: {props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
-                                    f"{sm_max:.0f} MHz",
+                     "peak_source": "measured: FP32 FMA chains on every SM (fgmm_peak_probe), CUDA events",
+                     "peak_derived": alu_derived,
+                     "peak_derived_source": f"{props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
+                                            f"{sm_max:.0f} MHz",
+                     "xu_peak": alu_peaks["rcp"],
+                     "xu_peak_source": "measured: rcp.approx chains on every SM (fgmm_peak_probe)",
+                     "ops_per_cdf_eval": ops_per_eval(K),
+                     "ops_count": f"{OPS_PER_PHI} FP32 operations per Phi-hat x K components per CDF evaluation",
                      # the decode is a chain of dependent steps per stream:
                      # its time per step at the sampled SM clock
                      "steps_per_stream": -(-N // S),
@@ -917,9 +1019,8 @@ def run_batch_only(args):
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
     h = codec.handle(dev)
-    props = torch.cuda.get_device_properties(dev)
     peaks = measured_peaks()
-    alu_peak = props.multi_processor_count * FP32_LANES_PER_SM * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+    alu_peak = measure_alu_peaks(dev, h)["fma"]
     shapes = synth.batch_shapes(64, seed=1004)[: args.batch_only]
     out = {}
     batch_case(dev, h, out, f"batch{len(shapes)}_uneven_k3",

@@ -442,6 +442,20 @@ fgmm_status fgmm_decode_plan(fgmm_handle *h, int32_t S, int32_t out[4]);
 fgmm_status fgmm_stats_enable(fgmm_handle *h, int32_t on);
 fgmm_status fgmm_stats_read(fgmm_handle *h, uint64_t *out, void *stream);
 
+/* Throughput probe for the roofline denominators (a measurement aid; the
+ * paper has no counterpart). Launches, asynchronously on `stream`, a grid of
+ * 4 CTAs of 256 threads per SM in which every thread runs 8 independent
+ * chains of `iters` x 16 steps of one instruction:
+ *   FGMM_PEAK_FMA  fma.rn.f32 (the FP32 pipe the CDF evaluations run on);
+ *   FGMM_PEAK_RCP  rcp.approx.ftz.f32 (the XU pipe the reciprocals use).
+ * *ops_out (host) receives the number of per-lane operations the launch
+ * performs; the caller times the launch (CUDA events on `stream`) and
+ * divides. sink: device float[1], never written in practice (it keeps the
+ * chains from being optimised away). iters >= 1. */
+enum { FGMM_PEAK_FMA = 0, FGMM_PEAK_RCP = 1 };
+fgmm_status fgmm_peak_probe(fgmm_handle *h, int32_t kind, int64_t iters, float *sink, double *ops_out,
+                            void *stream);
+
 /* Size of the fixed device scratch array used by fgmm_encode_noalloc. */
 #define FGMM_NOALLOC_SCRATCH_BYTES (16u << 20)
 

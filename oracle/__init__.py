@@ -37,7 +37,7 @@ def build(force: bool = False) -> str:
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
     cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
-           "-fno-fast-math", "-fno-finite-math-only", "-Wall", "-o", tmp, _SRC, "-lm"]
+           "-fno-fast-math", "-fno-finite-math-only", "-Wall", "-pthread", "-o", tmp, _SRC, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -71,6 +71,10 @@ def _load():
         lib.or_encode.argtypes = [P, ctypes.c_int, I64, P, I32, P, I64, P]
         lib.or_decode.restype = ctypes.c_int
         lib.or_decode.argtypes = [P, ctypes.c_int, I64, P, P, I32, P]
+        lib.or_encode_mt.restype = I64
+        lib.or_encode_mt.argtypes = [P, ctypes.c_int, I64, P, I32, P, I64, P, ctypes.c_int]
+        lib.or_decode_mt.restype = ctypes.c_int
+        lib.or_decode_mt.argtypes = [P, ctypes.c_int, I64, P, P, I32, P, ctypes.c_int]
         lib.or_p64.restype = ctypes.c_double
         lib.or_p64.argtypes = [P, ctypes.c_int, I64, I64, I32]
         lib.or_rate_audit.restype = ctypes.c_int
@@ -219,8 +223,9 @@ def encode_bound_words(N: int, S: int) -> int:
     return (S // 32) * (3 * 32 * T + 64)
 
 
-def encode(params, symbols, S: int):
-    """Returns (words uint16, offsets int64[S/32 + 1])."""
+def encode(params, symbols, S: int, threads: int = 1):
+    """Returns (words uint16, offsets int64[S/32 + 1]). threads > 1 codes
+    the segments on that many host threads (identical output)."""
     p = _params(params)
     s = np.ascontiguousarray(symbols, dtype=np.int32)
     N = p.shape[2]
@@ -228,14 +233,18 @@ def encode(params, symbols, S: int):
     cap = encode_bound_words(N, S)
     words = np.empty(max(cap, 1), np.uint16)
     offsets = np.empty(S // 32 + 1, np.int64)
-    n = _load().or_encode(_p(p), p.shape[1], N, _p(s), S, _p(words), cap, _p(offsets))
+    if threads > 1:
+        n = _load().or_encode_mt(_p(p), p.shape[1], N, _p(s), S, _p(words), cap, _p(offsets), threads)
+    else:
+        n = _load().or_encode(_p(p), p.shape[1], N, _p(s), S, _p(words), cap, _p(offsets))
     if n < 0:
         raise ValueError(f"oracle encode status {-n}")
     return words[:n].copy(), offsets
 
 
-def decode(params, words, offsets, S: int):
-    """Returns (symbols int32[N], status)."""
+def decode(params, words, offsets, S: int, threads: int = 1):
+    """Returns (symbols int32[N], status). threads > 1 decodes the segments
+    on that many host threads (identical output)."""
     p = _params(params)
     w = np.ascontiguousarray(words, dtype=np.uint16)
     if w.size == 0:
@@ -243,7 +252,10 @@ def decode(params, words, offsets, S: int):
     o = np.ascontiguousarray(offsets, dtype=np.int64)
     N = p.shape[2]
     out = np.zeros(N, np.int32)
-    st = _load().or_decode(_p(p), p.shape[1], N, _p(w), _p(o), S, _p(out))
+    if threads > 1:
+        st = _load().or_decode_mt(_p(p), p.shape[1], N, _p(w), _p(o), S, _p(out), threads)
+    else:
+        st = _load().or_decode(_p(p), p.shape[1], N, _p(w), _p(o), S, _p(out))
     return out, st
 
 

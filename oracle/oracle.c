@@ -29,6 +29,7 @@
  * rounding, '/' is correctly rounded.
  */
 #include <math.h>
+#include <pthread.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -439,52 +440,68 @@ static void rans_put(uint32_t *x, uint32_t start, uint32_t freq, uint16_t *buf, 
  * words are appended in ascending lane order. Afterwards each lane appends
  * its final state as (x & 0xFFFF, x >> 16), lanes 0..31. Segments are
  * concatenated in order; offsets[g] is the exclusive prefix sum of segment
- * lengths, offsets[nseg] the total. Returns the total number of words, or a
- * negative status. */
+ * lengths, offsets[nseg] the total.
+ *
+ * encode_segment codes segment g into buf (room for 3 * 32 * T + 64 words)
+ * and returns its length in words; or_encode returns the total number of
+ * words, or a negative status. */
+static int64_t encode_segment(const float *params, int K, int64_t N, const int32_t *sym, int32_t S, int64_t T,
+                              int64_t g, uint16_t *buf)
+{
+    int64_t len = 0;
+    uint32_t x[32];
+    for (int l = 0; l < 32; ++l) x[l] = OR_L;
+    for (int64_t t = T - 1; t >= 0; --t) {
+        uint32_t st[32], fr[32];
+        int esc[32], act[32];
+        for (int l = 0; l < 32; ++l) {
+            int64_t n = t * S + g * 32 + l;
+            act[l] = n < N;
+            esc[l] = 0;
+            if (act[l]) {
+                or_mix m;
+                load_mix(params, K, N, n, &m);
+                esc[l] = interval_of(&m, sym[n], &st[l], &fr[l]);
+            }
+        }
+        for (int l = 0; l < 32; ++l)       /* low chunk of escapes */
+            if (act[l] && esc[l])
+                rans_put(&x[l], (uint32_t)sym[t * S + g * 32 + l] & 0xFFFFu, 1u, buf, &len);
+        for (int l = 0; l < 32; ++l)       /* high chunk of escapes */
+            if (act[l] && esc[l])
+                rans_put(&x[l], (uint32_t)sym[t * S + g * 32 + l] >> 16, 1u, buf, &len);
+        for (int l = 0; l < 32; ++l)       /* main symbol */
+            if (act[l]) rans_put(&x[l], st[l], fr[l], buf, &len);
+    }
+    for (int l = 0; l < 32; ++l) {
+        buf[len++] = (uint16_t)(x[l] & 0xFFFFu);
+        buf[len++] = (uint16_t)(x[l] >> 16);
+    }
+    return len;
+}
+
+static int params_ok(const float *params, int K, int64_t N)
+{
+    for (int64_t n = 0; n < N; ++n) {
+        or_mix m;
+        load_mix(params, K, N, n, &m);
+        if (!mix_ok(&m)) return 0;
+    }
+    return 1;
+}
+
 int64_t or_encode(const float *params, int K, int64_t N, const int32_t *sym, int32_t S,
                   uint16_t *words, int64_t cap, int64_t *offsets)
 {
     if (K < 1 || K > OR_MAXK || N < 0 || S <= 0 || S % 32 != 0) return -OR_INVALID;
-    for (int64_t n = 0; n < N; ++n) {
-        or_mix m;
-        load_mix(params, K, N, n, &m);
-        if (!mix_ok(&m)) return -OR_BAD_PARAMS;
-    }
+    if (!params_ok(params, K, N)) return -OR_BAD_PARAMS;
     int64_t nseg = S / 32;
     int64_t T = (N + S - 1) / S;
     uint16_t *buf = (uint16_t *)malloc(sizeof(uint16_t) * (size_t)(3 * 32 * T + 64));
     if (!buf) return -OR_INVALID;
     int64_t total = 0;
     for (int64_t g = 0; g < nseg; ++g) {
-        int64_t len = 0;
-        uint32_t x[32];
-        for (int l = 0; l < 32; ++l) x[l] = OR_L;
-        for (int64_t t = T - 1; t >= 0; --t) {
-            uint32_t st[32], fr[32];
-            int esc[32], act[32];
-            for (int l = 0; l < 32; ++l) {
-                int64_t n = t * S + g * 32 + l;
-                act[l] = n < N;
-                esc[l] = 0;
-                if (act[l]) {
-                    or_mix m;
-                    load_mix(params, K, N, n, &m);
-                    esc[l] = interval_of(&m, sym[n], &st[l], &fr[l]);
-                }
-            }
-            for (int l = 0; l < 32; ++l)       /* low chunk of escapes */
-                if (act[l] && esc[l])
-                    rans_put(&x[l], (uint32_t)sym[t * S + g * 32 + l] & 0xFFFFu, 1u, buf, &len);
-            for (int l = 0; l < 32; ++l)       /* high chunk of escapes */
-                if (act[l] && esc[l])
-                    rans_put(&x[l], (uint32_t)sym[t * S + g * 32 + l] >> 16, 1u, buf, &len);
-            for (int l = 0; l < 32; ++l)       /* main symbol */
-                if (act[l]) rans_put(&x[l], st[l], fr[l], buf, &len);
-        }
-        for (int l = 0; l < 32; ++l) {
-            buf[len++] = (uint16_t)(x[l] & 0xFFFFu);
-            buf[len++] = (uint16_t)(x[l] >> 16);
-        }
+        int64_t len = encode_segment(params, K, N, sym, S, T, g, buf);
         offsets[g] = total;
         if (total + len > cap) { free(buf); return -OR_CAPACITY; }
         memcpy(words + total, buf, sizeof(uint16_t) * (size_t)len);
@@ -527,75 +544,190 @@ static int search_slot(const or_mix *m, uint32_t slot, int32_t *s, uint32_t *sta
  * rank r among c such lanes takes word [ptr - c + r]. At the end every
  * state must be 2^16 and the read pointer at the segment start, else
  * OR_CORRUPT. */
+static int decode_segment(const float *params, int K, int64_t N, const uint16_t *words, const int64_t *offsets,
+                          int32_t S, int64_t T, int64_t g, int32_t *out)
+{
+    int64_t beg = offsets[g], end = offsets[g + 1];
+    if (end - beg < 64) return OR_CORRUPT;
+    uint32_t x[32];
+    for (int l = 0; l < 32; ++l)
+        x[l] = (uint32_t)words[end - 64 + 2 * l] | ((uint32_t)words[end - 64 + 2 * l + 1] << 16);
+    int64_t ptr = end - 64;
+    int bad = 0;
+    for (int64_t t = 0; t < T && !bad; ++t) {
+        int act[32], esc[32];
+        uint32_t hi16[32];
+        /* main symbol */
+        for (int l = 0; l < 32; ++l) {
+            int64_t n = t * S + g * 32 + l;
+            act[l] = n < N;
+            esc[l] = 0;
+            if (!act[l]) continue;
+            or_mix m;
+            load_mix(params, K, N, n, &m);
+            uint32_t slot = x[l] & 0xFFFFu, st, fr;
+            int32_t s = 0;
+            esc[l] = search_slot(&m, slot, &s, &st, &fr);
+            x[l] = fr * (x[l] >> 16) + slot - st;
+            out[n] = s;
+        }
+        for (int l = 31; l >= 0; --l)
+            if (act[l] && x[l] < OR_L) {
+                if (ptr <= beg) { bad = 1; break; }
+                x[l] = (x[l] << 16) | words[--ptr];
+            }
+        if (bad) break;
+        /* high chunk of escapes */
+        for (int l = 0; l < 32; ++l)
+            if (act[l] && esc[l]) { hi16[l] = x[l] & 0xFFFFu; x[l] >>= 16; }
+        for (int l = 31; l >= 0; --l)
+            if (act[l] && esc[l] && x[l] < OR_L) {
+                if (ptr <= beg) { bad = 1; break; }
+                x[l] = (x[l] << 16) | words[--ptr];
+            }
+        if (bad) break;
+        /* low chunk of escapes */
+        for (int l = 0; l < 32; ++l)
+            if (act[l] && esc[l]) {
+                uint32_t lo16 = x[l] & 0xFFFFu;
+                x[l] >>= 16;
+                out[t * S + g * 32 + l] = (int32_t)((hi16[l] << 16) | lo16);
+            }
+        for (int l = 31; l >= 0; --l)
+            if (act[l] && esc[l] && x[l] < OR_L) {
+                if (ptr <= beg) { bad = 1; break; }
+                x[l] = (x[l] << 16) | words[--ptr];
+            }
+    }
+    if (bad || ptr != beg) return OR_CORRUPT;
+    for (int l = 0; l < 32; ++l)
+        if (x[l] != OR_L) return OR_CORRUPT;
+    return OR_OK;
+}
+
 int or_decode(const float *params, int K, int64_t N, const uint16_t *words, const int64_t *offsets,
               int32_t S, int32_t *out)
 {
     if (K < 1 || K > OR_MAXK || N < 0 || S <= 0 || S % 32 != 0) return OR_INVALID;
-    for (int64_t n = 0; n < N; ++n) {
-        or_mix m;
-        load_mix(params, K, N, n, &m);
-        if (!mix_ok(&m)) return OR_BAD_PARAMS;
-    }
+    if (!params_ok(params, K, N)) return OR_BAD_PARAMS;
     int64_t nseg = S / 32;
     int64_t T = (N + S - 1) / S;
     int status = OR_OK;
-    for (int64_t g = 0; g < nseg; ++g) {
-        int64_t beg = offsets[g], end = offsets[g + 1];
-        if (end - beg < 64) { status = OR_CORRUPT; continue; }
-        uint32_t x[32];
-        for (int l = 0; l < 32; ++l)
-            x[l] = (uint32_t)words[end - 64 + 2 * l] | ((uint32_t)words[end - 64 + 2 * l + 1] << 16);
-        int64_t ptr = end - 64;
-        int bad = 0;
-        for (int64_t t = 0; t < T && !bad; ++t) {
-            int act[32], esc[32];
-            uint32_t hi16[32];
-            /* main symbol */
-            for (int l = 0; l < 32; ++l) {
-                int64_t n = t * S + g * 32 + l;
-                act[l] = n < N;
-                esc[l] = 0;
-                if (!act[l]) continue;
-                or_mix m;
-                load_mix(params, K, N, n, &m);
-                uint32_t slot = x[l] & 0xFFFFu, st, fr;
-                int32_t s = 0;
-                esc[l] = search_slot(&m, slot, &s, &st, &fr);
-                x[l] = fr * (x[l] >> 16) + slot - st;
-                out[n] = s;
-            }
-            for (int l = 31; l >= 0; --l)
-                if (act[l] && x[l] < OR_L) {
-                    if (ptr <= beg) { bad = 1; break; }
-                    x[l] = (x[l] << 16) | words[--ptr];
-                }
-            if (bad) break;
-            /* high chunk of escapes */
-            for (int l = 0; l < 32; ++l)
-                if (act[l] && esc[l]) { hi16[l] = x[l] & 0xFFFFu; x[l] >>= 16; }
-            for (int l = 31; l >= 0; --l)
-                if (act[l] && esc[l] && x[l] < OR_L) {
-                    if (ptr <= beg) { bad = 1; break; }
-                    x[l] = (x[l] << 16) | words[--ptr];
-                }
-            if (bad) break;
-            /* low chunk of escapes */
-            for (int l = 0; l < 32; ++l)
-                if (act[l] && esc[l]) {
-                    uint32_t lo16 = x[l] & 0xFFFFu;
-                    x[l] >>= 16;
-                    out[t * S + g * 32 + l] = (int32_t)((hi16[l] << 16) | lo16);
-                }
-            for (int l = 31; l >= 0; --l)
-                if (act[l] && esc[l] && x[l] < OR_L) {
-                    if (ptr <= beg) { bad = 1; break; }
-                    x[l] = (x[l] << 16) | words[--ptr];
-                }
-        }
-        if (bad || ptr != beg) { status = OR_CORRUPT; continue; }
-        for (int l = 0; l < 32; ++l)
-            if (x[l] != OR_L) status = OR_CORRUPT;
+    for (int64_t g = 0; g < nseg; ++g)
+        if (decode_segment(params, K, N, words, offsets, S, T, g, out) != OR_OK) status = OR_CORRUPT;
+    return status;
+}
+
+/* ---------------------------------------------------------------------
+ * The same coding with the segments spread over nthreads POSIX threads
+ * (segments are independent by construction of the interleaving); used to
+ * time the oracle on all host cores. The per-segment arithmetic is the
+ * single-thread code above, so the output is identical.
+ * ------------------------------------------------------------------- */
+typedef struct {
+    const float *params;
+    int K;
+    int64_t N;
+    const int32_t *sym;
+    const uint16_t *words;
+    const int64_t *offsets;
+    int32_t S;
+    int64_t T, nseg;
+    uint16_t *bufs;      /* encode: nseg buffers of seg_cap words */
+    int64_t seg_cap;
+    int64_t *lens;       /* encode: segment lengths */
+    int32_t *out;        /* decode: symbols */
+    int *status;         /* decode: per-segment status */
+    int64_t next;        /* next segment to take (shared counter) */
+    pthread_mutex_t mu;
+} mt_job;
+
+static int64_t mt_take(mt_job *j)
+{
+    pthread_mutex_lock(&j->mu);
+    int64_t g = j->next++;
+    pthread_mutex_unlock(&j->mu);
+    return g;
+}
+
+static void *mt_encode_worker(void *arg)
+{
+    mt_job *j = (mt_job *)arg;
+    for (int64_t g = mt_take(j); g < j->nseg; g = mt_take(j))
+        j->lens[g] = encode_segment(j->params, j->K, j->N, j->sym, j->S, j->T, g, j->bufs + g * j->seg_cap);
+    return NULL;
+}
+
+static void *mt_decode_worker(void *arg)
+{
+    mt_job *j = (mt_job *)arg;
+    for (int64_t g = mt_take(j); g < j->nseg; g = mt_take(j))
+        j->status[g] = decode_segment(j->params, j->K, j->N, j->words, j->offsets, j->S, j->T, g, j->out);
+    return NULL;
+}
+
+static void mt_run(mt_job *j, int nthreads, void *(*fn)(void *))
+{
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads > 256) nthreads = 256;
+    pthread_t th[256];
+    int started = 0;
+    for (int i = 1; i < nthreads; ++i)
+        if (pthread_create(&th[started], NULL, fn, j) == 0) ++started;
+    fn(j);
+    for (int i = 0; i < started; ++i) pthread_join(th[i], NULL);
+}
+
+int64_t or_encode_mt(const float *params, int K, int64_t N, const int32_t *sym, int32_t S, uint16_t *words,
+                     int64_t cap, int64_t *offsets, int nthreads)
+{
+    if (K < 1 || K > OR_MAXK || N < 0 || S <= 0 || S % 32 != 0) return -OR_INVALID;
+    if (!params_ok(params, K, N)) return -OR_BAD_PARAMS;
+    mt_job j;
+    memset(&j, 0, sizeof j);
+    j.params = params; j.K = K; j.N = N; j.sym = sym; j.S = S;
+    j.nseg = S / 32;
+    j.T = (N + S - 1) / S;
+    j.seg_cap = 3 * 32 * j.T + 64;
+    j.bufs = (uint16_t *)malloc(sizeof(uint16_t) * (size_t)(j.seg_cap * j.nseg));
+    j.lens = (int64_t *)malloc(sizeof(int64_t) * (size_t)j.nseg);
+    if (!j.bufs || !j.lens) { free(j.bufs); free(j.lens); return -OR_INVALID; }
+    pthread_mutex_init(&j.mu, NULL);
+    mt_run(&j, nthreads, mt_encode_worker);
+    pthread_mutex_destroy(&j.mu);
+    int64_t total = 0;
+    for (int64_t g = 0; g < j.nseg; ++g) {
+        offsets[g] = total;
+        if (total + j.lens[g] > cap) { free(j.bufs); free(j.lens); return -OR_CAPACITY; }
+        memcpy(words + total, j.bufs + g * j.seg_cap, sizeof(uint16_t) * (size_t)j.lens[g]);
+        total += j.lens[g];
     }
+    offsets[j.nseg] = total;
+    free(j.bufs);
+    free(j.lens);
+    return total;
+}
+
+int or_decode_mt(const float *params, int K, int64_t N, const uint16_t *words, const int64_t *offsets, int32_t S,
+                 int32_t *out, int nthreads)
+{
+    if (K < 1 || K > OR_MAXK || N < 0 || S <= 0 || S % 32 != 0) return OR_INVALID;
+    if (!params_ok(params, K, N)) return OR_BAD_PARAMS;
+    mt_job j;
+    memset(&j, 0, sizeof j);
+    j.params = params; j.K = K; j.N = N; j.words = words; j.offsets = offsets; j.S = S;
+    j.nseg = S / 32;
+    j.T = (N + S - 1) / S;
+    j.out = out;
+    j.status = (int *)malloc(sizeof(int) * (size_t)(j.nseg > 0 ? j.nseg : 1));
+    if (!j.status) return OR_INVALID;
+    pthread_mutex_init(&j.mu, NULL);
+    mt_run(&j, nthreads, mt_decode_worker);
+    pthread_mutex_destroy(&j.mu);
+    int status = OR_OK;
+    for (int64_t g = 0; g < j.nseg; ++g)
+        if (j.status[g] != OR_OK) status = OR_CORRUPT;
+    free(j.status);
     return status;
 }
 

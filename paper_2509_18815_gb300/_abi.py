@@ -31,6 +31,7 @@ FGMM_OPT_DECODE_ROUND0 = 3
 FGMM_OPT_TEST_SILENT_STREAM = 4
 FGMM_OPT_PHI = 5
 FGMM_PHI_AS, FGMM_PHI_LOGISTIC, FGMM_PHI_POLYA = 0, 1, 2
+FGMM_PEAK_FMA, FGMM_PEAK_RCP = 0, 1
 FGMM_DEC_LANE, FGMM_DEC_COOP, FGMM_DEC_WIDE, FGMM_DEC_WS = 0, 1, 2, 3
 DECODE_KERNELS = {FGMM_DEC_LANE: "fgmm_dec_kernel", FGMM_DEC_COOP: "fgmm_dec_coop_kernel",
                   FGMM_DEC_WIDE: "fgmm_dec_wide_kernel", FGMM_DEC_WS: "fgmm_dec_ws_kernel"}
@@ -101,6 +102,7 @@ SIGNATURES = {
     "fgmm_mlp_forward": (I32, [P, P, I64, P, P, P]),
     "fgmm_decode_proposal": (I32, [P, LATP, P, P, I64, P, I32, P, P]),
     "fgmm_encode_noalloc": (I32, [LATP, P, I32, P, I64, P, P, P, P]),
+    "fgmm_peak_probe": (I32, [P, I32, I64, P, P, P]),
 }
 
 _lib = None

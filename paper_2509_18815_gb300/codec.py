@@ -198,6 +198,17 @@ def stats_enable(on: bool = True, h: Handle | None = None):
     h.check(_abi.fgmm_stats_enable(h.ptr, 1 if on else 0))
 
 
+def peak_probe(kind: int, iters: int, sink: torch.Tensor, h: Handle | None = None, stream=None) -> float:
+    """Launches the library's throughput probe (fgmm_peak_probe: chains of
+    FP32 FMAs for kind FGMM_PEAK_FMA, XU reciprocals for FGMM_PEAK_RCP) on
+    the stream and returns the per-lane operations it performs; the caller
+    times it. sink: a CUDA float tensor of at least one element."""
+    h = h or handle()
+    ops = ctypes.c_double(0.0)
+    h.check(_abi.fgmm_peak_probe(h.ptr, kind, iters, _ptr(sink), ctypes.addressof(ops), _stream(stream)))
+    return ops.value
+
+
 def stats_read(h: Handle | None = None, with_hits: bool = False):
     """(cdf_evals, symbols_decoded[, proposal_hits]) since the last read."""
     h = h or handle()

@@ -134,3 +134,25 @@ def test_rate_close_to_entropy_bound():
     assert bits >= coded - 1e-6 * coded
     assert bits <= coded + 32 * 32 + 0.01 * coded
     assert math.isfinite(ideal)
+
+
+@pytest.mark.parametrize("threads", [2, 3, 8])
+def test_threaded_oracle_equals_single_thread(threads):
+    """The oracle's segment-parallel entry points (used to time it on all
+    host cores) give the single-thread words, offsets, symbols and status,
+    also with escapes, a ragged last step and a damaged segment."""
+    lat = synth.make_latent(8, 16, 17, 3, seed=91, escape_stress=0.01)
+    for S in (32, 96, 256):
+        w1, o1 = oracle.encode(lat.params, lat.symbols, S)
+        wt, ot = oracle.encode(lat.params, lat.symbols, S, threads=threads)
+        np.testing.assert_array_equal(w1, wt)
+        np.testing.assert_array_equal(o1, ot)
+        d1, s1 = oracle.decode(lat.params, w1, o1, S)
+        dt, st = oracle.decode(lat.params, w1, o1, S, threads=threads)
+        assert s1 == st == oracle.OK
+        np.testing.assert_array_equal(d1, dt)
+        bad = w1.copy()
+        bad[int(o1[1]) - 70] ^= 0x5A5A
+        _, sb1 = oracle.decode(lat.params, bad, o1, S)
+        _, sbt = oracle.decode(lat.params, bad, o1, S, threads=threads)
+        assert sb1 == sbt == oracle.CORRUPT
