@@ -235,7 +235,8 @@ def measure_alu_peaks(dev, h, reps=5):
     from paper_2509_18815_gb300 import _abi, codec
     sink = torch.zeros(1, dtype=torch.float32, device=dev)
     res = {}
-    for name, kind, iters in (("fma", _abi.FGMM_PEAK_FMA, 32), ("rcp", _abi.FGMM_PEAK_RCP, 64)):
+    # about a millisecond per launch, so that launch overhead does not count
+    for name, kind, iters in (("fma", _abi.FGMM_PEAK_FMA, 2048), ("rcp", _abi.FGMM_PEAK_RCP, 256)):
         ops = [0.0]
 
         def run():

@@ -436,9 +436,13 @@ enum { FGMM_DEC_LANE = 0, FGMM_DEC_COOP = 1, FGMM_DEC_WIDE = 2, FGMM_DEC_WS = 3 
 fgmm_status fgmm_decode_plan(fgmm_handle *h, int32_t S, int32_t out[4]);
 
 /* Optional counters. When enabled, decoders add the number of quantised-CDF
- * evaluations they make to a device counter; fgmm_stats_read synchronises
- * `stream` and copies {cdf_evals, symbols_decoded, proposal_hits} to host
- * out[3], then zeroes the counters. */
+ * evaluations they make to a device counter (for the one-lane binary search:
+ * its probes, the evaluations of the plain binary search on the same path);
+ * fgmm_stats_read synchronises `stream` and copies {cdf_evals,
+ * symbols_decoded, proposal_hits, guide_fallbacks} to host out[4], then
+ * zeroes the counters. guide_fallbacks counts the symbols for which the
+ * one-lane decoder's fast-steered search reached a symbol that the exact
+ * check rejected, so that the exact binary search ran instead. */
 fgmm_status fgmm_stats_enable(fgmm_handle *h, int32_t on);
 fgmm_status fgmm_stats_read(fgmm_handle *h, uint64_t *out, void *stream);
 
@@ -447,11 +451,15 @@ fgmm_status fgmm_stats_read(fgmm_handle *h, uint64_t *out, void *stream);
  * 4 CTAs of 256 threads per SM in which every thread runs 8 independent
  * chains of `iters` x 16 steps of one instruction:
  *   FGMM_PEAK_FMA  fma.rn.f32 (the FP32 pipe the CDF evaluations run on);
- *   FGMM_PEAK_RCP  rcp.approx.ftz.f32 (the XU pipe the reciprocals use).
+ *   FGMM_PEAK_RCP  rcp.approx.ftz.f32, each followed by one fma.rn.f32 so
+ *                  that no two steps cancel (the XU pipe the reciprocals
+ *                  use sets the time; ops counts the reciprocals).
  * *ops_out (host) receives the number of per-lane operations the launch
  * performs; the caller times the launch (CUDA events on `stream`) and
- * divides. sink: device float[1], never written in practice (it keeps the
- * chains from being optimised away). iters >= 1. */
+ * divides; a launch should run for a millisecond or more (iters ~2048 for
+ * FMA, ~256 for RCP) so that the launch overhead does not count. sink:
+ * device float[1], never written in practice (it keeps the chains from
+ * being optimised away). iters >= 1. */
 enum { FGMM_PEAK_FMA = 0, FGMM_PEAK_RCP = 1 };
 fgmm_status fgmm_peak_probe(fgmm_handle *h, int32_t kind, int64_t iters, float *sink, double *ops_out,
                             void *stream);

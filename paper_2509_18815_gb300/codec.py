@@ -209,14 +209,18 @@ def peak_probe(kind: int, iters: int, sink: torch.Tensor, h: Handle | None = Non
     return ops.value
 
 
-def stats_read(h: Handle | None = None, with_hits: bool = False):
-    """(cdf_evals, symbols_decoded[, proposal_hits]) since the last read."""
+def stats_read(h: Handle | None = None, with_hits: bool = False, with_fallbacks: bool = False):
+    """(cdf_evals, symbols_decoded[, proposal_hits][, guide_fallbacks]) since
+    the last read."""
     h = h or handle()
-    out = (ctypes.c_uint64 * 3)()
+    out = (ctypes.c_uint64 * 4)()
     h.check(_abi.fgmm_stats_read(h.ptr, out, _stream()))
+    r = (int(out[0]), int(out[1]))
     if with_hits:
-        return int(out[0]), int(out[1]), int(out[2])
-    return int(out[0]), int(out[1])
+        r += (int(out[2]),)
+    if with_fallbacks:
+        r += (int(out[3]),)
+    return r
 
 
 def table_build(params: torch.Tensor, h: Handle | None = None) -> torch.Tensor:

@@ -523,13 +523,11 @@ fgmm_status fgmm_stats_read(fgmm_handle* h, uint64_t* out, void* stream)
     if (!h || !out) return FGMM_ERR_INVALID_ARG;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaError_t e = cudaStreamSynchronize(st);
-    unsigned long long v[3] = {0, 0, 0};
+    unsigned long long v[4] = {0, 0, 0, 0};
     if (e == cudaSuccess) e = cudaMemcpy(v, h->d_stats, sizeof v, cudaMemcpyDeviceToHost);
-    if (e == cudaSuccess) e = cudaMemset(h->d_stats, 0, 3 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(h->d_stats, 0, 4 * sizeof(unsigned long long));
     if (e != cudaSuccess) return cuda_fail(h, e, "fgmm_stats_read");
-    out[0] = v[0];
-    out[1] = v[1];
-    out[2] = v[2];
+    for (int i = 0; i < 4; ++i) out[i] = v[i];
     return FGMM_OK;
 }
 

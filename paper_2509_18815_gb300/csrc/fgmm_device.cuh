@@ -274,6 +274,82 @@ __device__ __forceinline__ bool search_slot(const Mix<K>& m, uint32_t slot, int3
     return a == m.hi + 1;
 }
 
+// Fast steering evaluation of the mixture CDF at b for the decoder's
+// search: the A&S form of phi_hat_s with the hardware reciprocal and base-2
+// exponential, no clamp and no grid rounding (accurate to about 1e-6). It
+// only decides where the search goes next; search_slot_guided confirms the
+// symbol it reaches with the exact quantised CDF (q_at), so this function's
+// rounding never reaches a decoded symbol or a frequency.
+__device__ __forceinline__ float rcp_approx(float d)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(d));
+    return y;
+}
+__device__ __forceinline__ float ex2_approx(float a)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(a));
+    return y;
+}
+
+template <int K>
+__device__ __forceinline__ float mix_cdf_fast(const Mix<K>& m, float b)
+{
+    const float kP22 = 0x1.da6712p-25f;    // p 2^-22 (zs = z 2^22)
+    const float kE = -0x1.715476p-45f;     // -log2(e) / 2 * 2^-44: exp(-z^2/2) = 2^(kE zs^2)
+    float acc = 0.0f;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const float zs = (b - m.mu[k]) * m.isg[k];
+        const float t = rcp_approx(fmaf(kP22, fabsf(zs), 1.0f));
+        float h = fmaf(0x1.0fb844p-1f, t, -0x1.7401c6p-1f);
+        h = fmaf(h, t, 0x1.6be1c6p-1f);
+        h = fmaf(h, t, -0x1.23531cp-3f);
+        h = fmaf(h, t, 0x1.04f20cp-3f);
+        const float q = ex2_approx((zs * kE) * zs) * (h * t);
+        acc = fmaf(m.w[k], zs >= 0.0f ? 1.0f - q : q, acc);
+    }
+    return acc;
+}
+
+// Decoder search with a fast guide (Sec. III-A's binary search, steered by
+// mix_cdf_fast): the binary search over [lo, hi + 2) runs on the fast
+// evaluation, deciding Q(mid) <= slot as (mid - lo) + T' v < slot + 1;
+// then the exact quantised CDF is evaluated at the symbol it reached and at
+// its successor (Q(lo) = 0 and Q(hi + 2) = 2^16 need no evaluation) and
+// must bracket the slot. If it does not (the fast evaluation decided a
+// near-tie the other way), the exact binary search runs. The result is the
+// exact search's in every case: the symbol whose exact interval holds the
+// slot is unique. `probes` counts the search's probes (the evaluations the
+// exact binary search makes on the same path), `fallbacks` the exact
+// searches run after a failed check.
+template <int K>
+__device__ __forceinline__ bool search_slot_guided(const Mix<K>& m, uint32_t slot, int32_t& s, uint32_t& start,
+                                                   uint32_t& freq, int& probes, int& fallbacks)
+{
+    int a = m.lo, b = m.hi + 2;
+    const float thr = (float)(slot + 1u);
+    while (b - a > 1) {
+        const int mid = a + ((b - a) >> 1);
+        const float v = fminf(mix_cdf_fast<K>(m, (float)mid - 0.5f), 1.0f);
+        ++probes;
+        if (fmaf(m.tp, v, (float)(mid - m.lo)) < thr) a = mid;
+        else b = mid;
+    }
+    const uint32_t qa = a == m.lo ? 0u : q_at<K>(m, a);
+    const uint32_t qb = a == m.hi + 1 ? kM : q_at<K>(m, a + 1);
+    if (qa <= slot && slot < qb) {
+        s = a;
+        start = qa;
+        freq = qb - qa;
+        return a == m.hi + 1;
+    }
+    ++fallbacks;
+    int extra = 0;
+    return search_slot<K>(m, slot, s, start, freq, extra);
+}
+
 __device__ __forceinline__ uint32_t lanemask_lt()
 {
     uint32_t m;

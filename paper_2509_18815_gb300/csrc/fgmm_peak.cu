@@ -5,7 +5,8 @@
 // benchmark divides by is measured here rather than derived from unit counts:
 // a grid of 4 CTAs x 256 threads per SM runs independent chains of FP32
 // fused multiply-adds (or of the XU reciprocal approximation that the
-// reciprocal in every CDF evaluation starts from), 8 chains per thread, so
+// reciprocal in every CDF evaluation starts from, each followed by one FMA),
+// 8 chains per thread, so
 // every SM sub-partition has enough independent instructions to issue one
 // per cycle. The caller times the launch with CUDA events; ops counts one
 // FMA (or one reciprocal) per lane as one operation.
@@ -38,7 +39,11 @@ __global__ void __launch_bounds__(kPeakThreads) fgmm_peak_kernel(int64_t iters, 
                 if constexpr (KIND == 0) {
                     asm volatile("fma.rn.f32 %0, %0, %1, %2;" : "+f"(v[i]) : "f"(a), "f"(b));
                 } else {
+                    // x <- a / x + b: the reciprocal (XU) plus one FMA, so
+                    // no pair of steps can cancel; the XU pipe, 1/8 the FMA
+                    // rate, sets the time
                     asm volatile("rcp.approx.ftz.f32 %0, %0;" : "+f"(v[i]));
+                    asm volatile("fma.rn.f32 %0, %0, %1, %2;" : "+f"(v[i]) : "f"(a), "f"(b));
                 }
             }
         }
@@ -46,7 +51,8 @@ __global__ void __launch_bounds__(kPeakThreads) fgmm_peak_kernel(int64_t iters, 
     float s = 0.0f;
 #pragma unroll
     for (int i = 0; i < kChains; ++i) s += v[i];
-    // the values stay near 1 (a x + b with a + b = 1, or x -> 1/x), so this
+    // the values stay near 1 (x -> a x + b with a + b = 1, or x -> a / x + b
+    // with a = 1/2, b = 1), so this
     // store never happens; it only keeps the chains alive
     if (s == -1.0f) *sink = s;
 }
@@ -61,7 +67,7 @@ extern "C" fgmm_status fgmm_peak_probe(fgmm_handle* h, int32_t kind, int64_t ite
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int grid = h->num_sms * kPeakBlocksPerSM;
     if (kind == FGMM_PEAK_FMA) fgmm_peak_kernel<0><<<grid, kPeakThreads, 0, st>>>(iters, 0.999f, 0.001f, sink);
-    else fgmm_peak_kernel<1><<<grid, kPeakThreads, 0, st>>>(iters, 0.0f, 0.0f, sink);
+    else fgmm_peak_kernel<1><<<grid, kPeakThreads, 0, st>>>(iters, 0.5f, 1.0f, sink);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(h, e, "fgmm_peak_probe launch");
     *ops_out = (double)grid * kPeakThreads * (double)iters * kUnroll * kChains;

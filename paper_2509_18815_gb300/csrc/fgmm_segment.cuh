@@ -5,8 +5,9 @@
 //     with the quantised-CDF interval evaluated inline at the coded symbol
 //     and fed straight to rANS (Eq. 3); parameters of the next step are
 //     loaded one step ahead.
-//   dec_segment: binary search over the on-the-fly quantised CDF, inverse
-//     rANS step, ballot-ranked refill; end-of-segment integrity check.
+//   dec_segment: binary search over the on-the-fly quantised CDF (steered
+//     by the fast evaluation and confirmed exactly for A&S), inverse rANS
+//     step, ballot-ranked refill; end-of-segment integrity check.
 #pragma once
 
 #include "fgmm_device.cuh"
@@ -60,13 +61,14 @@ __device__ __forceinline__ bool mix_from_params(const RawParams<K>& r, Mix<K>& m
 }
 
 // Exact x / f and x mod f for x < f * 2^16 (the state after
-// renormalisation), f in [1, 2^16). The FP32 estimate x * (1/f) has relative
-// error below 3 * 2^-24, so with the quotient below 2^16 it is off by less
-// than 0.02 and its truncation by at most one; one correction step each way
-// makes it exact.
+// renormalisation), f in [1, 2^16). The FP32 estimate x * (1/f), with the
+// hardware reciprocal (at most 1 ulp off), has relative error below 2^-21,
+// so with the quotient below 2^16 it is off by less than 1/32 and its
+// truncation by at most one; one correction step each way makes it exact
+// (fgmm_self_check tests it at the remainders 0, 1 and f - 1).
 __device__ __forceinline__ uint32_t divmod_small(uint32_t x, uint32_t f, uint32_t& r)
 {
-    const float rf = recip((float)f);   // equal to __frcp_rn for f <= 2^16
+    const float rf = rcp_approx((float)f);
     uint32_t q = __float2uint_rz(__fmul_rn(__uint2float_rn(x), rf));
     int32_t rem = (int32_t)(x - q * f);
     if (rem < 0) { --q; rem += (int32_t)f; }
@@ -154,7 +156,7 @@ __device__ __forceinline__ void dec_segment(const T* __restrict__ params, int64_
     uint32_t x = (uint32_t)__ldg(words + end - 64 + 2 * lane) | ((uint32_t)__ldg(words + end - 63 + 2 * lane) << 16);
     int64_t ptr = end - 64;
     bool bad = false, badp = false;
-    int probes = 0, decoded = 0;
+    int probes = 0, decoded = 0, fallbacks = 0;
     int64_t n = g * 32 + lane;
     RawParams<K> cur;
     if (T_steps > 0 && n < N) load_raw_params<K, T>(params, N, n, cur);
@@ -173,7 +175,8 @@ __device__ __forceinline__ void dec_segment(const T* __restrict__ params, int64_
             badp |= !mix_from_params<K>(cur, m);
             const uint32_t slot = x & 0xffffu;
             uint32_t st, fr;
-            esc = search_slot<K, PHI>(m, slot, s, st, fr, probes);
+            if constexpr (PHI == kPhiAS) esc = search_slot_guided<K>(m, slot, s, st, fr, probes, fallbacks);
+            else esc = search_slot<K, PHI>(m, slot, s, st, fr, probes);
             x = fr * (x >> 16) + slot - st;
         }
         refill_warp(x, act, words, ptr, beg, bad, lt);
@@ -192,15 +195,17 @@ __device__ __forceinline__ void dec_segment(const T* __restrict__ params, int64_
     if (__ballot_sync(0xffffffffu, fail) && lane == 0) set_error(err, kErrCorrupt);
     if (__ballot_sync(0xffffffffu, badp) && lane == 0) set_error(err, kErrBadParams);
     if (stats) {
-        int p = probes, d = decoded;
+        int p = probes, d = decoded, f = fallbacks;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             p += __shfl_xor_sync(0xffffffffu, p, o);
             d += __shfl_xor_sync(0xffffffffu, d, o);
+            f += __shfl_xor_sync(0xffffffffu, f, o);
         }
         if (lane == 0) {
             atomicAdd(stats, (unsigned long long)p);
             atomicAdd(stats + 1, (unsigned long long)d);
+            if (f) atomicAdd(stats + 3, (unsigned long long)f);
         }
     }
 }

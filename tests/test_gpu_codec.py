@@ -403,3 +403,33 @@ def test_decode_counts_cdf_evaluations():
     # bisection of [lo, hi + 2) (the escape slot searched as symbol hi + 1):
     # floor or ceil of log2(W + 1) CDF evaluations per symbol
     assert np.sum(np.floor(np.log2(W + 1))) <= evals <= np.sum(np.ceil(np.log2(W + 1)))
+
+
+def test_guided_search_fallbacks_decode_exactly():
+    """The one-lane decoder steers its binary search with a fast evaluation
+    of the CDF and confirms the symbol with the exact quantised CDF. On a
+    1,966,080-symbol latent (scales up to 64) the check rejects the steered
+    symbol a few hundred times (near-ties, where the fast evaluation falls on
+    the other side of a boundary); the exact search then decodes those
+    symbols, and the whole latent round-trips. The search still probes as
+    many points as the plain binary search."""
+    codec = _codec()
+    lat = synth.make_latent(320, 64, 96, 3, seed=1003, sigma_max=64.0)
+    dp, ds = dev_params(lat.params), dev_i32(lat.symbols)
+    S = 4096
+    words, off = codec.encode(dp, ds, S)
+    codec.stats_enable(True)
+    codec.stats_read()
+    _set_lanes(1)
+    try:
+        out = codec.decode(dp, words, off, S)
+    finally:
+        _set_lanes(0)
+    evals, nsym, _, fallbacks = codec.stats_read(with_hits=True, with_fallbacks=True)
+    codec.stats_enable(False)
+    assert torch.equal(out, ds)
+    assert nsym == lat.N
+    assert 0 < fallbacks < lat.N // 1000
+    lo, hi = oracle.window(lat.params)
+    W = (hi - lo + 1).astype(np.float64)
+    assert np.sum(np.floor(np.log2(W + 1))) <= evals <= np.sum(np.ceil(np.log2(W + 1)))
