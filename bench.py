@@ -108,6 +108,8 @@ def parse():
                     help="run only the batch case on the first N latents of the 64-latent batch (for profiling)")
     ap.add_argument("--gsm-only", action="store_true",
                     help="run only the Gaussian-single-model case (for profiling its decoder)")
+    ap.add_argument("--proposal-only", action="store_true",
+                    help="run only the learned-proposal case (for profiling its decoders)")
     ap.add_argument("--batch-overhead", type=float, default=0.01,
                     help="container-overhead bound given to the stream autotuner in --batch-only mode")
     return ap.parse_args()
@@ -370,6 +372,79 @@ def ckbd_case(dev, h, flush, reps):
             "note": "host-launched sequence of split, two coder passes, context and merges (no graph)"}
 
 
+def proposal_case(dev, h, alu_peak_tops, reps=3, n_train=10_000_000):
+    """The learned decode proposal on its workload: the network trained on
+    n_train (params, slot, symbol) triples drawn from synthetic latents with
+    scales up to 64 (slots uniform inside each symbol's interval), once with
+    each activation; then a batch of 16 latents of 320x64x96 (scales up to
+    64), autotuned streams, decoded in one persistent launch each by the
+    plain batch decoder (graph replay), the network proposal (both
+    activations) and the analytic proposal. Every arm's roofline fraction
+    uses the same algorithmic work: the plain binary search's CDF
+    evaluations x the fixed operation count."""
+    import numpy as np
+    import torch
+    from paper_2509_18815_gb300 import _abi, codec, synth
+    from paper_2509_18815_gb300.proposal import init_theta
+    train = synth.make_latent(160, 256, 256, 3, seed=1005, sigma_max=64.0)
+    ntr = min(n_train, train.N)
+    tp = torch.from_numpy(np.ascontiguousarray(train.params[:, :, :ntr])).to(dev)
+    ty = torch.from_numpy(np.ascontiguousarray(train.symbols[:ntr])).to(dev)
+    rng = np.random.default_rng(11)
+    X, t = codec.mlp_data(tp, ty, torch.from_numpy(rng.random(ntr).astype(np.float32)).to(dev), h)
+    del tp, ty
+    schedule = [(6000, 3e-3), (3000, 1e-3), (3000, 3e-4)]
+    packed, train_s, final_loss = {}, {}, {}
+    for name, act in (("pl", _abi.FGMM_MLP_ACT_PL), ("sigmoid", _abi.FGMM_MLP_ACT_SIGMOID)):
+        codec.set_mlp_act(act, h)
+        tr = codec.MlpTrainer(init_theta(12), device=dev, h=h)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for steps, lr in schedule:
+            trace = tr.train(X, t, steps=steps, batch=8192, lr=lr)
+        train_s[name] = time.perf_counter() - t0
+        final_loss[name] = float(trace[-200:].mean().item())
+        packed[name] = tr.packed()
+    codec.set_mlp_act(_abi.FGMM_MLP_ACT_PL, h)
+    del X, t
+    lats = [synth.make_latent(320, 64, 96, 3, seed=1105 + i, sigma_max=64.0) for i in range(16)]
+    params = [torch.from_numpy(l.params).to(dev) for l in lats]
+    syms = [torch.from_numpy(l.symbols).to(dev) for l in lats]
+    N = sum(l.N for l in lats)
+    b = codec.Batch(params, syms, S=codec.autotune([l.N for l in lats], h=h), h=h)
+    b.capture()
+    b.encode()
+    arms = {"plain": (lambda: b.decode(sync=False), _abi.FGMM_MLP_ACT_PL),
+            "proposal_pl": (lambda: b.decode_proposal(packed["pl"], sync=False), _abi.FGMM_MLP_ACT_PL),
+            "proposal_sigmoid": (lambda: b.decode_proposal(packed["sigmoid"], sync=False),
+                                 _abi.FGMM_MLP_ACT_SIGMOID),
+            "analytic": (lambda: b.decode_proposal(None, sync=False), _abi.FGMM_MLP_ACT_PL)}
+    res = {}
+    for name, (fn, act) in arms.items():
+        codec.set_mlp_act(act, h)
+        for d in b.decoded:
+            d.zero_()
+        codec.stats_enable(True, h); codec.stats_read(h)
+        fn(); h.sync()
+        probes, nd, hits, fb = codec.stats_read(h, with_hits=True, with_fallbacks=True)
+        codec.stats_enable(False, h)
+        assert nd == N and all(torch.equal(b.decoded[i], syms[i]) for i in range(len(lats))), name
+        ms = _events_ms(fn, reps)
+        res[name] = {"ms_decode": ms, "decode_msym_s": N / ms / 1e3, "probes_per_symbol": probes / N,
+                     "hit_rate": hits / N if name != "plain" else None, "exact_fallbacks": fb}
+    codec.set_mlp_act(_abi.FGMM_MLP_ACT_PL, h)
+    b.close()
+    evals_plain = res["plain"]["probes_per_symbol"] * N   # the binary search's CDF evaluations
+    for r in res.values():
+        r["alu_frac"] = evals_plain * ops_per_eval(3) / (r["ms_decode"] * 1e-3) / 1e12 / alu_peak_tops
+    return {"symbols": N, "latents": len(lats), "streams_per_latent": b.S[0], "segments": b.seg_base[-1],
+            "train_triples": ntr, "train_steps": sum(st for st, _ in schedule), "train_batch": 8192,
+            "train_s": train_s, "train_final_loss": final_loss, "arms": res,
+            "note": "one persistent launch per arm over all 16 latents; the plain arm is the batch decoder "
+                    "(binary search steered by the fast CDF, confirmed exactly); the proposal arms search from "
+                    "the network's guess with the same fast probes and exact confirmation"}
+
+
 def throughput_workloads(dev, alu_peak_tops, hbm_gbs, reps=5):
     """Larger workloads: one 320x64x96 latent (K = 3 and 4, fp32 and bf16
     parameters, autotuned stream count, FP64 rate audit), a batch of 64
@@ -452,57 +527,7 @@ def throughput_workloads(dev, alu_peak_tops, hbm_gbs, reps=5):
                [synth.make_latent(C, H, W, 3, 1004 + i) for i, (C, H, W) in enumerate(shapes)], alu_peak_tops,
                hbm_gbs, reps)
 
-    # learned proposal: trained on 2^21 triples, decoding 16 latents of
-    # 320x64x96 with scales up to 64
-    from paper_2509_18815_gb300.proposal import init_theta
-    train = synth.make_latent(32, 256, 256, 3, seed=1005, sigma_max=64.0)
-    rng = np.random.default_rng(11)
-    X, t = codec.mlp_data(torch.from_numpy(train.params).to(dev), torch.from_numpy(train.symbols).to(dev),
-                          torch.from_numpy(rng.random(train.N).astype(np.float32)).to(dev), h)
-    tr = codec.MlpTrainer(init_theta(12), device=dev, h=h)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for steps, lr in [(2000, 3e-3), (1000, 1e-3), (1000, 3e-4)]:
-        tr.train(X, t, steps=steps, batch=8192, lr=lr)
-    train_s = time.perf_counter() - t0
-    P = tr.packed()
-    del X, t
-    lats = [synth.make_latent(320, 64, 96, 3, seed=1105 + i, sigma_max=64.0) for i in range(16)]
-    S_all = codec.autotune([l.N for l in lats], h=h)
-    res = {"plain": [0.0, 0, 0, 0], "proposal": [0.0, 0, 0, 0], "analytic": [0.0, 0, 0, 0]}
-    for l, S in zip(lats, S_all):
-        dp = torch.from_numpy(l.params).to(dev)
-        ds = torch.from_numpy(l.symbols).to(dev)
-        words, off = codec.encode(dp, ds, S, h=h)
-        o = torch.empty(l.N, dtype=torch.int32, device=dev)
-        for kind in ("plain", "proposal", "analytic"):
-            if kind == "plain":
-                h.check(_abi.fgmm_set_option(h.ptr, _abi.FGMM_OPT_DECODE_LANES, 1))
-                fn = lambda: codec.decode(dp, words, off, S, h=h, out=o, sync=False)
-            else:
-                Pk = P if kind == "proposal" else None
-                fn = lambda: codec.decode_proposal(dp, words, off, S, Pk, h=h, out=o, sync=False)
-            codec.stats_enable(True, h); codec.stats_read(h)
-            fn(); h.sync()
-            ev, nd, hits = codec.stats_read(h, with_hits=True)
-            codec.stats_enable(False, h)
-            assert torch.equal(o, ds), kind
-            ms = _events_ms(fn, 3)
-            r = res[kind]
-            r[0] += ms; r[1] += ev; r[2] += nd; r[3] += hits
-            h.check(_abi.fgmm_set_option(h.ptr, _abi.FGMM_OPT_DECODE_LANES, 0))
-    out["proposal_16x320x64x96_sigma64"] = {
-        "symbols": res["plain"][2], "train_s": train_s, "train_samples": 4000 * 8192,
-        "plain_decode_msym_s": res["plain"][2] / res["plain"][0] / 1e3,
-        "proposal_decode_msym_s": res["proposal"][2] / res["proposal"][0] / 1e3,
-        "plain_cdf_evals_per_symbol": res["plain"][1] / res["plain"][2],
-        "proposal_cdf_evals_per_symbol": res["proposal"][1] / res["proposal"][2],
-        "proposal_hit_rate": res["proposal"][3] / res["proposal"][2],
-        "analytic_decode_msym_s": res["analytic"][2] / res["analytic"][0] / 1e3,
-        "analytic_cdf_evals_per_symbol": res["analytic"][1] / res["analytic"][2],
-        "analytic_hit_rate": res["analytic"][3] / res["analytic"][2],
-        "streams_per_latent": S_all[0],
-    }
+    out["proposal_16x320x64x96_sigma64"] = proposal_case(dev, h, alu_peak_tops, reps=3)
     return out
 
 
@@ -1041,12 +1066,25 @@ def run_gsm_only(args):
     print(json.dumps({"gsm_320x64x96": gsm_case(dev, h, flush, max(args.steps, 1))}))
 
 
+def run_proposal_only(args):
+    import torch
+    from paper_2509_18815_gb300 import build, codec
+    build.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    h = codec.handle(dev)
+    alu_peak = measure_alu_peaks(dev, h)["fma"]
+    print(json.dumps({"proposal_16x320x64x96_sigma64": proposal_case(dev, h, alu_peak, reps=max(args.steps, 1))}))
+
+
 def main():
     args = parse()
     if args.batch_only > 0:
         run_batch_only(args)
     elif args.gsm_only:
         run_gsm_only(args)
+    elif args.proposal_only:
+        run_proposal_only(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -324,15 +324,30 @@ fgmm_status fgmm_batch_capture(fgmm_batch *b);
 /* Encodes / decodes the whole batch on `stream` (graph replay if captured). */
 fgmm_status fgmm_batch_encode(fgmm_batch *b, void *stream);
 fgmm_status fgmm_batch_decode(fgmm_batch *b, void *stream);
+/* Decodes the whole batch with the decode proposal (see the proposal
+ * section below) in one persistent launch of 4-warp CTAs that each hold one
+ * copy of the packed network in shared memory: packed (device,
+ * FGMM_MLP_PACKED_BYTES, from fgmm_mlp_pack) or NULL for the analytic
+ * proposal; the activation is the plan handle's FGMM_OPT_MLP_ACT. Every
+ * latent must have K = 3 and all the same dtype (FGMM_ERR_INVALID_ARG
+ * otherwise). Output and errors as fgmm_batch_decode; not captured in the
+ * plan's graphs. */
+fgmm_status fgmm_batch_decode_proposal(fgmm_batch *b, const void *packed, void *stream);
 
 /* ---- Learned decode proposal (no counterpart in the paper) --------------
  * A 10 -> 64 -> 64 -> 1 MLP guesses a symbol from its mixture (K = 3) and
- * its rANS slot; fgmm_decode_proposal checks the guess against the exact
- * quantised CDF and finishes with a galloping + binary search, so decoded
- * symbols equal fgmm_decode's for any network weights. Features: weights,
- * means and log-scales standardised by the mixture mean m0 and standard
- * deviation s0 (components sorted by mean), and (slot + 1/2)/2^16 - 1/2;
- * output y, guess round(m0 + s0 y). Activation z * sat(1/2 + (1.702/4) z).
+ * its rANS slot; fgmm_decode_proposal searches from the guess (two probes
+ * decide whether the guess is the symbol, else a gallop of growing steps
+ * and a binary search; the probes use a fast evaluation of the CDF) and
+ * confirms the symbol reached with the exact quantised CDF (an exact binary
+ * search if that check fails), so decoded symbols equal fgmm_decode's for
+ * any network weights. Features: weights, means and log-scales standardised
+ * by the mixture mean m0 and standard deviation s0 (components sorted by
+ * mean), and (slot + 1/2)/2^16 - 1/2; output y, guess round(m0 + s0 y).
+ * Activation (FGMM_OPT_MLP_ACT, used by training, fgmm_mlp_forward and the
+ * proposal decoders): FGMM_MLP_ACT_PL, z * sat(1/2 + (1.702/4) z) (default),
+ * or FGMM_MLP_ACT_SIGMOID, z / (1 + exp(-1.702 z)); packed weights must be
+ * used with the activation they were trained with.
  * Parameter vector theta (device fp32[FGMM_MLP_PARAMS]): W1[10][64], b1[64],
  * W2[64][64], b2[64], w3[64], b3. */
 #define FGMM_MLP_PARAMS 4929
@@ -413,6 +428,11 @@ enum { FGMM_OPT_TEST_SILENT_STREAM = 4 };
  * and return FGMM_ERR_INVALID_ARG otherwise. */
 enum { FGMM_OPT_PHI = 5 };
 enum { FGMM_PHI_AS = 0, FGMM_PHI_LOGISTIC = 1, FGMM_PHI_POLYA = 2 };
+
+/* FGMM_OPT_MLP_ACT: activation of the proposal network (see the proposal
+ * section): FGMM_MLP_ACT_PL (0, default) or FGMM_MLP_ACT_SIGMOID (1). */
+enum { FGMM_OPT_MLP_ACT = 6 };
+enum { FGMM_MLP_ACT_PL = 0, FGMM_MLP_ACT_SIGMOID = 1 };
 fgmm_status fgmm_set_option(fgmm_handle *h, int32_t option, int64_t value);
 
 /* The decoder fgmm_decode would run for S streams (S / 32 segments) under

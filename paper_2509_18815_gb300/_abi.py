@@ -32,6 +32,8 @@ FGMM_OPT_TEST_SILENT_STREAM = 4
 FGMM_OPT_PHI = 5
 FGMM_PHI_AS, FGMM_PHI_LOGISTIC, FGMM_PHI_POLYA = 0, 1, 2
 FGMM_PEAK_FMA, FGMM_PEAK_RCP = 0, 1
+FGMM_OPT_MLP_ACT = 6
+FGMM_MLP_ACT_PL, FGMM_MLP_ACT_SIGMOID = 0, 1
 FGMM_DEC_LANE, FGMM_DEC_COOP, FGMM_DEC_WIDE, FGMM_DEC_WS = 0, 1, 2, 3
 DECODE_KERNELS = {FGMM_DEC_LANE: "fgmm_dec_kernel", FGMM_DEC_COOP: "fgmm_dec_coop_kernel",
                   FGMM_DEC_WIDE: "fgmm_dec_wide_kernel", FGMM_DEC_WS: "fgmm_dec_ws_kernel"}
@@ -95,6 +97,7 @@ SIGNATURES = {
     "fgmm_batch_capture": (I32, [P]),
     "fgmm_batch_encode": (I32, [P, P]),
     "fgmm_batch_decode": (I32, [P, P]),
+    "fgmm_batch_decode_proposal": (I32, [P, P, P]),
     "fgmm_mlp_data": (I32, [P, LATP, P, P, P, P, P, P]),
     "fgmm_mlp_loss_grad": (I32, [P, P, P, I64, P, P, P, P]),
     "fgmm_mlp_train": (I32, [P, P, P, I64, P, P, P, I64, I64, I64, ctypes.c_float, P, P]),

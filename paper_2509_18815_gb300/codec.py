@@ -495,6 +495,14 @@ class Batch:
         if sync:
             self.h.sync()
 
+    def decode_proposal(self, packed=None, sync: bool = True):
+        """The whole batch decoded with the proposal (packed network, or the
+        analytic proposal for None) in one persistent launch."""
+        self.h.check(_abi.fgmm_batch_decode_proposal(self.ptr, _ptr(packed) if packed is not None else None,
+                                                     _stream()))
+        if sync:
+            self.h.sync()
+
     def latent_stream(self, i: int):
         """(words, offsets) of latent i, in the single-latent format."""
         off = self.offsets[self.seg_base[i]: self.seg_base[i + 1] + 1]
@@ -579,6 +587,14 @@ class MlpTrainer:
         self.h.check(_abi.fgmm_mlp_pack(self.h.ptr, _ptr(self.theta), _ptr(P), _stream()))
         self.h.sync()
         return P
+
+
+def set_mlp_act(act: int, h: Handle | None = None):
+    """Activation of the proposal network on this handle (training,
+    inference and the proposal decoders): _abi.FGMM_MLP_ACT_PL or
+    _abi.FGMM_MLP_ACT_SIGMOID."""
+    h = h or handle()
+    h.check(_abi.fgmm_set_option(h.ptr, _abi.FGMM_OPT_MLP_ACT, act))
 
 
 def mlp_pack(theta, h: Handle | None = None):

@@ -29,22 +29,7 @@ using namespace fgmm;
 
 namespace {
 
-struct BatchLatentDev {
-    const void* params;
-    const int32_t* symbols;
-    int32_t* decoded;
-    int64_t N;
-    int64_t T;          // steps = ceil(N / S)
-    int64_t seg_base;   // first global segment
-    int64_t scr_base;   // first scratch word of the latent's segments
-    int64_t scr_cap;    // scratch words per segment of this latent
-    int32_t K, dtype, S, pad;
-};
-
-struct WorkItem {
-    int32_t latent;
-    int32_t g;          // segment within the latent
-};
+using WorkItem = BatchWorkItem;
 
 constexpr int kBatchThreads = 32;        // one warp per block: warps spread over all SMs
 constexpr int kTargetWarpsPerSM = 16;    // enough resident warps to keep the issue slots busy
@@ -240,6 +225,7 @@ struct fgmm_batch {
     int grid_enc = 0, grid_dec = 0;
     EncKernel enc_kernel = nullptr;
     DecKernel dec_kernel = nullptr;
+    std::vector<int> Ks, dts;          // per latent, host copies
     cudaGraphExec_t g_enc = nullptr, g_dec = nullptr;
     fgmm_handle* h = nullptr;
 };
@@ -406,6 +392,8 @@ fgmm_status fgmm_batch_create(fgmm_handle* h, const fgmm_batch_latent* lats, int
         std::vector<int> Ks(n), dts(n);
         for (int i = 0; i < n; ++i) { Ks[i] = lats[i].K; dts[i] = lats[i].dtype; }
         pick_kernels(Ks, dts, &b->enc_kernel, &b->dec_kernel);
+        b->Ks = Ks;
+        b->dts = dts;
     }
     int bpm_e = 0, bpm_d = 0;
     if (e == cudaSuccess)
@@ -500,6 +488,24 @@ fgmm_status fgmm_batch_decode(fgmm_batch* b, void* stream)
     enqueue_decode(b, st);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? FGMM_OK : cuda_fail(b->h, e, "fgmm_batch_decode launch");
+}
+
+fgmm_status fgmm_batch_decode_proposal(fgmm_batch* b, const void* packed, void* stream)
+{
+    if (!b) return FGMM_ERR_INVALID_ARG;
+    fgmm_handle* h = b->h;
+    for (int i = 0; i < b->n; ++i)
+        if (b->Ks[i] != 3 || b->dts[i] != b->dts[0])
+            return fail(h, FGMM_ERR_INVALID_ARG, "fgmm_batch_decode_proposal: latents must be K = 3 of one dtype");
+    if (packed && reinterpret_cast<uintptr_t>(packed) % 16 != 0)
+        return fail(h, FGMM_ERR_INVALID_ARG, "fgmm_batch_decode_proposal: packed must be 16-byte aligned");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemsetAsync(b->d_counters + 1, 0, sizeof(unsigned long long), st);
+    if (e == cudaSuccess && b->nseg > 0)
+        e = launch_batch_prop(b->d_lats, b->d_work, b->nseg, b->d_counters + 1, b->words, b->words_cap, b->offsets,
+                              packed, b->n > 0 ? b->dts[0] : FGMM_DTYPE_F32, h->mlp_act, h->d_err,
+                              h->stats_on ? h->d_stats : nullptr, h->num_sms, st);
+    return e == cudaSuccess ? FGMM_OK : cuda_fail(h, e, "fgmm_batch_decode_proposal launch");
 }
 
 }  // extern "C"

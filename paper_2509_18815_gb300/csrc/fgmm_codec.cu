@@ -682,6 +682,11 @@ fgmm_status fgmm_set_option(fgmm_handle* h, int32_t option, int64_t value)
         if (value < -1 || value > 31) return fail(h, FGMM_ERR_INVALID_ARG, "silent stream must be -1 (off) or 0..31");
         h->test_silent_stream = (int)value;
         return FGMM_OK;
+    case FGMM_OPT_MLP_ACT:
+        if (!(value == FGMM_MLP_ACT_PL || value == FGMM_MLP_ACT_SIGMOID))
+            return fail(h, FGMM_ERR_INVALID_ARG, "activation must be FGMM_MLP_ACT_PL or FGMM_MLP_ACT_SIGMOID");
+        h->mlp_act = (int)value;
+        return FGMM_OK;
     case FGMM_OPT_DECODE_ROUND0:
         if (!(value == 0 || value == 16 || value == 32))
             return fail(h, FGMM_ERR_INVALID_ARG, "decode first-round points must be 0 (auto), 16 or 32");

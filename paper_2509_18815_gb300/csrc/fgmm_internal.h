@@ -22,6 +22,7 @@ struct fgmm_handle {
     int decode_round0 = 0;             // 0 = automatic; else first-round points of the ws decoder (16, 32)
     int test_silent_stream = -1;       // test hook: a stream of segment 0 that posts no refill flags
     int phi = 0;                       // Phi approximation (FGMM_PHI_*)
+    int mlp_act = 0;                   // activation of the proposal network (FGMM_MLP_ACT_*)
     std::string last_error;
 };
 
@@ -99,5 +100,32 @@ cudaError_t launch_ws_bf16(const DecodeArgs& a, int K, int CL, int SPW, cudaStre
 void decode_resolve(int64_t nseg, int num_sms, int opt_lanes, int opt_cluster, int opt_round0, int phi, int* lanes,
                     int* cluster, int* round0, int* kernel);
 cudaError_t launch_decode(const DecodeArgs& a, int K, int dtype, int lanes, int cluster, cudaStream_t st);
+
+// Batch plan records shared by the batch coder (fgmm_batch.cu) and the
+// batched proposal decoder (fgmm_mlp.cu).
+struct BatchLatentDev {
+    const void* params;
+    const int32_t* symbols;
+    int32_t* decoded;
+    int64_t N;
+    int64_t T;          // steps = ceil(N / S)
+    int64_t seg_base;   // first global segment
+    int64_t scr_base;   // first scratch word of the latent's segments
+    int64_t scr_cap;    // scratch words per segment of this latent
+    int32_t K, dtype, S, pad;
+};
+
+struct BatchWorkItem {
+    int32_t latent;
+    int32_t g;          // segment within the latent
+};
+
+// Persistent proposal-bracketed decode of a batch (all latents K = 3, one
+// dtype): warps take work items from *counter (zeroed by the caller).
+// packed == nullptr selects the analytic proposal.
+cudaError_t launch_batch_prop(const BatchLatentDev* lats, const BatchWorkItem* work, int64_t nwork,
+                              unsigned long long* counter, const uint16_t* words, int64_t n_words,
+                              const int64_t* offsets, const void* packed, int dtype, int act, int32_t* err,
+                              unsigned long long* stats, int num_sms, cudaStream_t st);
 
 }  // namespace fgmm

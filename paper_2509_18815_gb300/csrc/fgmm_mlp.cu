@@ -42,13 +42,33 @@ constexpr float kActC = 1.702f / 4.0f;
 constexpr int kTS = 64;            // samples per training block
 constexpr int kTrainThreads = 128;
 
-__device__ __forceinline__ float act(float z) { return z * __saturatef(fmaf(kActC, z, 0.5f)); }
+// Activations (FGMM_MLP_ACT_*): ACT 0, z * sat(1/2 + c z), the GELU
+// z Phi(z) with the logistic CDF of Eq. 9 replaced by its tangent at 0;
+// ACT 1, z * sigma(1.702 z), the GELU with Phi replaced by the logistic CDF
+// of Eq. 9 itself. FAST uses the hardware exponential (inference only).
+template <int ACT, bool FAST = false>
+__device__ __forceinline__ float act(float z)
+{
+    if constexpr (ACT == 0) {
+        return z * __saturatef(fmaf(kActC, z, 0.5f));
+    } else if constexpr (FAST) {
+        return __fdividef(z, 1.0f + __expf(-1.702f * z));
+    } else {
+        return z / (1.0f + expf(-1.702f * z));
+    }
+}
+template <int ACT>
 __device__ __forceinline__ float act_grad(float z)
 {
-    const float r = fmaf(kActC, z, 0.5f);
-    if (r <= 0.0f) return 0.0f;
-    if (r >= 1.0f) return 1.0f;
-    return r + kActC * z;
+    if constexpr (ACT == 0) {
+        const float r = fmaf(kActC, z, 0.5f);
+        if (r <= 0.0f) return 0.0f;
+        if (r >= 1.0f) return 1.0f;
+        return r + kActC * z;
+    } else {
+        const float sg = 1.0f / (1.0f + expf(-1.702f * z));
+        return sg + 1.702f * z * sg * (1.0f - sg);
+    }
 }
 
 // Standardised features of one query (see the file comment). FAST selects
@@ -132,6 +152,7 @@ __global__ void __launch_bounds__(256) mlp_data_kernel(const T* __restrict__ par
 // ---------------------------------------------------------------------------
 // Loss and gradient of one block of kTS samples; partial sums per block.
 // ---------------------------------------------------------------------------
+template <int ACT>
 __global__ void __launch_bounds__(kTrainThreads) mlp_grad_kernel(const float* __restrict__ X,
                                                                  const float* __restrict__ tgt, int64_t B,
                                                                  const float* __restrict__ theta,
@@ -164,14 +185,14 @@ __global__ void __launch_bounds__(kTrainThreads) mlp_grad_kernel(const float* __
     for (int e = tid; e < kTS * kHid; e += kTrainThreads) {
         const int s = e / kHid, j = e % kHid;
         float a = th[oB2 + j];
-        for (int i = 0; i < kHid; ++i) a = fmaf(act(z1[s * kHid + i]), th[oW2 + i * kHid + j], a);
+        for (int i = 0; i < kHid; ++i) a = fmaf(act<ACT>(z1[s * kHid + i]), th[oW2 + i * kHid + j], a);
         z2[e] = a;
     }
     __syncthreads();
     float lsum = 0.0f;
     if (tid < kTS) {
         float y = th[oB3];
-        for (int j = 0; j < kHid; ++j) y = fmaf(act(z2[tid * kHid + j]), th[oW3 + j], y);
+        for (int j = 0; j < kHid; ++j) y = fmaf(act<ACT>(z2[tid * kHid + j]), th[oW3 + j], y);
         float r = 0.0f;
         if (tid < ns) r = y - tgt[s0 + tid];
         dy[tid] = 2.0f * r / (float)B;
@@ -182,7 +203,7 @@ __global__ void __launch_bounds__(kTrainThreads) mlp_grad_kernel(const float* __
     // output layer gradients
     if (tid < kHid) {
         float g = 0.0f;
-        for (int s = 0; s < kTS; ++s) g = fmaf(act(z2[s * kHid + tid]), dy[s], g);
+        for (int s = 0; s < kTS; ++s) g = fmaf(act<ACT>(z2[s * kHid + tid]), dy[s], g);
         out[oW3 + tid] = g;
     }
     if (tid == 0) {
@@ -195,13 +216,13 @@ __global__ void __launch_bounds__(kTrainThreads) mlp_grad_kernel(const float* __
     __syncthreads();
     for (int e = tid; e < kTS * kHid; e += kTrainThreads) {
         const int s = e / kHid, j = e % kHid;
-        z2[e] = dy[s] * th[oW3 + j] * act_grad(z2[e]);   // d2
+        z2[e] = dy[s] * th[oW3 + j] * act_grad<ACT>(z2[e]);   // d2
     }
     __syncthreads();
     for (int e = tid; e < kHid * kHid; e += kTrainThreads) {
         const int i = e / kHid, j = e % kHid;
         float g = 0.0f;
-        for (int s = 0; s < kTS; ++s) g = fmaf(act(z1[s * kHid + i]), z2[s * kHid + j], g);
+        for (int s = 0; s < kTS; ++s) g = fmaf(act<ACT>(z1[s * kHid + i]), z2[s * kHid + j], g);
         out[oW2 + e] = g;
     }
     if (tid < kHid) {
@@ -214,7 +235,7 @@ __global__ void __launch_bounds__(kTrainThreads) mlp_grad_kernel(const float* __
         const int s = e / kHid, i = e % kHid;
         float a = 0.0f;
         for (int j = 0; j < kHid; ++j) a = fmaf(th[oW2 + i * kHid + j], z2[s * kHid + j], a);
-        z1[e] = a * act_grad(z1[e]);   // d1
+        z1[e] = a * act_grad<ACT>(z1[e]);   // d1
     }
     __syncthreads();
     for (int e = tid; e < kIn * kHid; e += kTrainThreads) {
@@ -314,6 +335,7 @@ __device__ __forceinline__ void mma_bf16(float& c0, float& c1, float& c2, float&
 
 // Forward pass for the 32 queries of a warp; x: this lane's 10 features.
 // xs: per-warp shared scratch of 32 x 12 words. Returns this lane's y.
+template <int ACT>
 __device__ __forceinline__ float mlp_warp_forward(const MlpPacked* __restrict__ P, const float* x, uint32_t* xs)
 {
     const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
@@ -337,7 +359,7 @@ __device__ __forceinline__ float mlp_warp_forward(const MlpPacked* __restrict__ 
             const float bb0 = P->b1[8 * nt + 2 * t], bb1 = P->b1[8 * nt + 2 * t + 1];
             float c0 = bb0, c1 = bb1, c2 = bb0, c3 = bb1;
             mma_bf16(c0, c1, c2, c3, a0, a1, a2, a3, P->w1f[nt][lane]);
-            const uint32_t lo = pack_bf16(act(c0), act(c1)), hi = pack_bf16(act(c2), act(c3));
+            const uint32_t lo = pack_bf16(act<ACT, true>(c0), act<ACT, true>(c1)), hi = pack_bf16(act<ACT, true>(c2), act<ACT, true>(c3));
             if (nt & 1) { h[nt >> 1][2] = lo; h[nt >> 1][3] = hi; }
             else { h[nt >> 1][0] = lo; h[nt >> 1][1] = hi; }
         }
@@ -349,8 +371,8 @@ __device__ __forceinline__ float mlp_warp_forward(const MlpPacked* __restrict__ 
 #pragma unroll
             for (int kt = 0; kt < 4; ++kt) mma_bf16(c0, c1, c2, c3, h[kt][0], h[kt][1], h[kt][2], h[kt][3], P->w2f[kt][nt][lane]);
             const float w0 = P->w3[8 * nt + 2 * t], w1 = P->w3[8 * nt + 2 * t + 1];
-            y0 = fmaf(act(c0), w0, fmaf(act(c1), w1, y0));
-            y1 = fmaf(act(c2), w0, fmaf(act(c3), w1, y1));
+            y0 = fmaf(act<ACT, true>(c0), w0, fmaf(act<ACT, true>(c1), w1, y0));
+            y1 = fmaf(act<ACT, true>(c2), w0, fmaf(act<ACT, true>(c3), w1, y1));
         }
         y0 += __shfl_xor_sync(0xffffffffu, y0, 1);
         y0 += __shfl_xor_sync(0xffffffffu, y0, 2);
@@ -365,6 +387,7 @@ __device__ __forceinline__ float mlp_warp_forward(const MlpPacked* __restrict__ 
     return (lane < 16) ? ((r < 8) ? v00 : v01) : ((r < 8) ? v10 : v11);
 }
 
+template <int ACT>
 __global__ void __launch_bounds__(128) mlp_forward_kernel(const float* __restrict__ X, int64_t B,
                                                           const MlpPacked* __restrict__ Pg, float* __restrict__ y)
 {
@@ -380,7 +403,7 @@ __global__ void __launch_bounds__(128) mlp_forward_kernel(const float* __restric
         float x[kIn];
 #pragma unroll
         for (int i = 0; i < kIn; ++i) x[i] = q < B ? X[q * kIn + i] : 0.0f;
-        const float v = mlp_warp_forward(&P, x, xs[w]);
+        const float v = mlp_warp_forward<ACT>(&P, x, xs[w]);
         if (q < B) y[q] = v;
     }
 }
@@ -390,36 +413,88 @@ __global__ void __launch_bounds__(128) mlp_forward_kernel(const float* __restric
 // from the network, or (ANALYTIC) from the inverse of the logistic
 // approximation of Phi (Sec. III-B) on the component of largest weight:
 // mu + sigma' ln(u / (1 - u)) / 1.702, u = (slot + 1/2) / 2^16.
+//
+// The search from the guess g (clamped to [lo, hi + 1], hi + 1 the escape
+// slot) runs on the fast steering evaluation of the CDF (mix_cdf_fast):
+// two probes decide whether Q(g) <= slot < Q(g + 1); otherwise a gallop of
+// steps 1, 2, 4, ... away from g brackets the slot and a binary search
+// finishes it. The symbol reached is then confirmed with the exact
+// quantised CDF at it and its successor, as in search_slot_guided; a failed
+// check runs the exact binary search. Decoded symbols therefore never
+// depend on the network or on the fast evaluation. Counters: probes (fast
+// evaluations of the search), hits (g was the symbol), fallbacks.
 // ---------------------------------------------------------------------------
-template <typename T, bool ANALYTIC>
-__global__ void __launch_bounds__(32) fgmm_dec_prop_kernel(const T* __restrict__ params, int64_t N, int32_t S,
-                                                            int64_t T_steps, const uint16_t* __restrict__ words,
-                                                            int64_t n_words, const int64_t* __restrict__ offsets,
-                                                            int64_t nseg, const MlpPacked* __restrict__ Pg,
-                                                            int32_t* __restrict__ out, int32_t* err,
-                                                            unsigned long long* stats)
+__device__ __forceinline__ bool fast_le(const Mix<3>& m, int j, float thr)
 {
-    __shared__ MlpPacked P;
-    __shared__ uint32_t xs[1][32 * 12];
-    if constexpr (!ANALYTIC) {
-        for (int i = threadIdx.x; i < (int)(sizeof(MlpPacked) / 4); i += blockDim.x)
-            reinterpret_cast<uint32_t*>(&P)[i] = reinterpret_cast<const uint32_t*>(Pg)[i];
-        __syncthreads();
+    const float v = fminf(mix_cdf_fast<3>(m, (float)j - 0.5f), 1.0f);
+    return fmaf(m.tp, v, (float)(j - m.lo)) < thr;   // Q(j) <= slot, decided on the fast evaluation
+}
+
+__device__ __forceinline__ bool search_from_guess(const Mix<3>& m, uint32_t slot, int gi, int32_t& s,
+                                                  uint32_t& start, uint32_t& freq, int& probes, int& hits,
+                                                  int& fallbacks)
+{
+    const float thr = (float)(slot + 1u);
+    const int top = m.hi + 2;   // Q(hi + 2) = 2^16 > slot
+    int a, b;
+    ++probes;
+    if (gi == m.lo || fast_le(m, gi, thr)) {
+        a = gi;   // Q(a) <= slot: gallop up for b with Q(b) > slot
+        int step = 1;
+        for (;;) {
+            b = a + step;
+            if (b >= top) { b = top; break; }
+            ++probes;
+            if (!fast_le(m, b, thr)) break;
+            a = b;
+            step <<= 1;
+        }
+    } else {
+        b = gi;   // Q(b) > slot: gallop down for a with Q(a) <= slot
+        int step = 1;
+        for (;;) {
+            a = b - step;
+            if (a <= m.lo) { a = m.lo; break; }
+            ++probes;
+            if (fast_le(m, a, thr)) break;
+            b = a;
+            step <<= 1;
+        }
     }
-    const int wib = 0;
-    const int64_t g = blockIdx.x;   // one warp (segment) per block: segments spread over all SMs
+    while (b - a > 1) {
+        const int mid = a + ((b - a) >> 1);
+        ++probes;
+        if (fast_le(m, mid, thr)) a = mid;
+        else b = mid;
+    }
+    const uint32_t qa = a == m.lo ? 0u : q_at<3>(m, a);
+    const uint32_t qb = a == m.hi + 1 ? kM : q_at<3>(m, a + 1);
+    if (qa <= slot && slot < qb) {
+        s = a;
+        start = qa;
+        freq = qb - qa;
+        hits += a == gi;
+        return a == m.hi + 1;
+    }
+    ++fallbacks;
+    int extra = 0;
+    return search_slot<3>(m, slot, s, start, freq, extra);
+}
+
+// Decodes segment g of a K = 3 latent (words[beg, end)) with the proposal;
+// all 32 lanes of the warp must call it (the network runs warp-wide).
+template <typename T, bool ANALYTIC, int ACT>
+__device__ __forceinline__ void dec_segment_prop(const T* __restrict__ params, int64_t N, int32_t S, int64_t T_steps,
+                                                 int64_t g, const uint16_t* __restrict__ words, int64_t beg,
+                                                 int64_t end, const MlpPacked* __restrict__ P, uint32_t* xs,
+                                                 int32_t* __restrict__ out, int32_t* err, unsigned long long* stats)
+{
     const int lane = threadIdx.x & 31;
-    if (g >= nseg) return;   // after the block-wide load; no block barrier follows
-    const int64_t beg = offsets[g], end = offsets[g + 1];
-    if (!(beg >= 0 && end <= n_words && end - beg >= 64)) {
-        if (lane == 0) set_error(err, kErrCorrupt);
-        return;
-    }
     const uint32_t lt = lanemask_lt();
     uint32_t x = (uint32_t)__ldg(words + end - 64 + 2 * lane) | ((uint32_t)__ldg(words + end - 63 + 2 * lane) << 16);
     int64_t ptr = end - 64;
     bool bad = false, badp = false;
-    int probes = 0, decoded = 0, hits = 0;
+    int probes = 0, decoded = 0, hits = 0, fallbacks = 0;
     int64_t n = g * 32 + lane;
     RawParams<3> cur;
     if (T_steps > 0 && n < N) load_raw_params<3, T>(params, N, n, cur);
@@ -444,7 +519,7 @@ __global__ void __launch_bounds__(32) fgmm_dec_prop_kernel(const T* __restrict__
         } else {
             float f[kIn], m0, s0;
             features<true>(&cur.v[0], &cur.v[3], &cur.v[6], slot, f, m0, s0);
-            const float yv = mlp_warp_forward(&P, f, xs[wib]);   // all lanes take part
+            const float yv = mlp_warp_forward<ACT>(P, f, xs);   // all lanes take part
             guess = fmaf(s0, yv, m0);
         }
         int32_t s = 0;
@@ -452,65 +527,9 @@ __global__ void __launch_bounds__(32) fgmm_dec_prop_kernel(const T* __restrict__
         if (act_l) {
             ++decoded;
             float gf = rintf(guess);
-            gf = isfinite(gf) ? fminf(fmaxf(gf, (float)m.lo), (float)m.hi) : (float)m.lo;
-            const int gi = (int)gf;
-            const uint32_t qg = gi == m.lo ? 0u : q_at<3>(m, gi);
-            const uint32_t qg1 = q_at<3>(m, gi + 1);
-            probes += (gi == m.lo ? 1 : 2);
-            uint32_t start = 0, freq = 0;
-            int a = 0, b = 0;
-            uint32_t qa = 0, qb = 0;
-            bool search = true;
-            if (qg <= slot && slot < qg1) {
-                s = gi; start = qg; freq = qg1 - qg;
-                ++hits;
-                search = false;
-            } else if (slot < qg) {
-                // gallop down from gi: find a with Q(a) <= slot
-                b = gi; qb = qg;
-                int step = 1;
-                for (;;) {
-                    a = b - step;
-                    if (a <= m.lo) { a = m.lo; qa = 0; break; }
-                    qa = q_at<3>(m, a);
-                    ++probes;
-                    if (qa <= slot) break;
-                    b = a; qb = qa; step <<= 1;
-                }
-            } else {
-                // gallop up from gi + 1: find b with Q(b) > slot, or escape
-                a = gi + 1; qa = qg1;
-                int step = 1;
-                if (a == m.hi + 1) {
-                    esc = true;
-                } else {
-                    for (;;) {
-                        b = a + step;
-                        if (b >= m.hi + 1) {
-                            b = m.hi + 1;
-                            qb = q_at<3>(m, b);
-                            ++probes;
-                            if (slot >= qb) esc = true;
-                            break;
-                        }
-                        qb = q_at<3>(m, b);
-                        ++probes;
-                        if (qb > slot) break;
-                        a = b; qa = qb; step <<= 1;
-                    }
-                }
-                if (esc) { start = (a == m.hi + 1) ? qa : qb; freq = kM - start; search = false; }
-            }
-            if (search) {
-                while (b - a > 1) {
-                    const int mid = a + ((b - a) >> 1);
-                    const uint32_t qm = q_at<3>(m, mid);
-                    ++probes;
-                    if (qm <= slot) { a = mid; qa = qm; }
-                    else { b = mid; qb = qm; }
-                }
-                s = a; start = qa; freq = qb - qa;
-            }
+            gf = isfinite(gf) ? fminf(fmaxf(gf, (float)m.lo), (float)(m.hi + 1)) : (float)m.lo;
+            uint32_t start, freq;
+            esc = search_from_guess(m, slot, (int)gf, s, start, freq, probes, hits, fallbacks);
             x = freq * (x >> 16) + slot - start;
         }
         refill_warp(x, act_l, words, ptr, beg, bad, lt);
@@ -529,19 +548,101 @@ __global__ void __launch_bounds__(32) fgmm_dec_prop_kernel(const T* __restrict__
     if (__ballot_sync(0xffffffffu, fail) && lane == 0) set_error(err, kErrCorrupt);
     if (__ballot_sync(0xffffffffu, badp) && lane == 0) set_error(err, kErrBadParams);
     if (stats) {
-        int p = probes, d = decoded, hh = hits;
+        int p = probes, d = decoded, hh = hits, fb = fallbacks;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             p += __shfl_xor_sync(0xffffffffu, p, o);
             d += __shfl_xor_sync(0xffffffffu, d, o);
             hh += __shfl_xor_sync(0xffffffffu, hh, o);
+            fb += __shfl_xor_sync(0xffffffffu, fb, o);
         }
         if (lane == 0) {
             atomicAdd(stats, (unsigned long long)p);
             atomicAdd(stats + 1, (unsigned long long)d);
             atomicAdd(stats + 2, (unsigned long long)hh);
+            if (fb) atomicAdd(stats + 3, (unsigned long long)fb);
         }
     }
+}
+
+// Single latent: one warp (one segment) per block, so that segments spread
+// over all SMs.
+template <typename T, bool ANALYTIC, int ACT>
+__global__ void __launch_bounds__(32) fgmm_dec_prop_kernel(const T* __restrict__ params, int64_t N, int32_t S,
+                                                            int64_t T_steps, const uint16_t* __restrict__ words,
+                                                            int64_t n_words, const int64_t* __restrict__ offsets,
+                                                            int64_t nseg, const MlpPacked* __restrict__ Pg,
+                                                            int32_t* __restrict__ out, int32_t* err,
+                                                            unsigned long long* stats)
+{
+    __shared__ MlpPacked P;
+    __shared__ uint32_t xs[32 * 12];
+    if constexpr (!ANALYTIC) {
+        for (int i = threadIdx.x; i < (int)(sizeof(MlpPacked) / 4); i += blockDim.x)
+            reinterpret_cast<uint32_t*>(&P)[i] = reinterpret_cast<const uint32_t*>(Pg)[i];
+        __syncthreads();
+    }
+    const int64_t g = blockIdx.x;
+    if (g >= nseg) return;   // after the block-wide load; no block barrier follows
+    const int64_t beg = offsets[g], end = offsets[g + 1];
+    if (!(beg >= 0 && end <= n_words && end - beg >= 64)) {
+        if ((threadIdx.x & 31) == 0) set_error(err, kErrCorrupt);
+        return;
+    }
+    dec_segment_prop<T, ANALYTIC, ACT>(params, N, S, T_steps, g, words, beg, end, &P, xs, out, err, stats);
+}
+
+// Batch: persistent CTAs of 4 warps sharing one copy of the packed network
+// in shared memory; each warp takes (latent, segment) items from the queue.
+constexpr int kPropWarps = 4;
+
+template <typename T, bool ANALYTIC, int ACT>
+__global__ void __launch_bounds__(32 * kPropWarps) fgmm_batch_dec_prop_kernel(
+    const BatchLatentDev* __restrict__ lats, const BatchWorkItem* __restrict__ work, int64_t nwork,
+    unsigned long long* counter, const uint16_t* __restrict__ words, int64_t n_words,
+    const int64_t* __restrict__ offsets, const MlpPacked* __restrict__ Pg, int32_t* err, unsigned long long* stats)
+{
+    __shared__ MlpPacked P;
+    __shared__ uint32_t xs[kPropWarps][32 * 12];
+    if constexpr (!ANALYTIC) {
+        for (int i = threadIdx.x; i < (int)(sizeof(MlpPacked) / 4); i += blockDim.x)
+            reinterpret_cast<uint32_t*>(&P)[i] = reinterpret_cast<const uint32_t*>(Pg)[i];
+        __syncthreads();
+    }
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (;;) {
+        unsigned long long i = 0;
+        if (lane == 0) i = atomicAdd(counter, 1ull);
+        i = __shfl_sync(0xffffffffu, i, 0);
+        if (i >= (unsigned long long)nwork) break;
+        const BatchWorkItem it = work[i];
+        const BatchLatentDev L = lats[it.latent];
+        const int64_t gg = L.seg_base + it.g;
+        const int64_t beg = offsets[gg], end = offsets[gg + 1];
+        if (!(beg >= 0 && end <= n_words && end - beg >= 64)) {
+            if (lane == 0) set_error(err, kErrCorrupt);
+            continue;
+        }
+        dec_segment_prop<T, ANALYTIC, ACT>(static_cast<const T*>(L.params), L.N, L.S, L.T, it.g, words, beg, end, &P,
+                                           xs[w], L.decoded, err, stats);
+    }
+}
+
+template <typename T, bool ANALYTIC, int ACT>
+cudaError_t launch_batch_prop_t(const BatchLatentDev* lats, const BatchWorkItem* work, int64_t nwork,
+                                unsigned long long* counter, const uint16_t* words, int64_t n_words,
+                                const int64_t* offsets, const MlpPacked* P, int32_t* err, unsigned long long* stats,
+                                int num_sms, cudaStream_t st)
+{
+    auto kern = fgmm_batch_dec_prop_kernel<T, ANALYTIC, ACT>;
+    int bpm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bpm, kern, 32 * kPropWarps, 0);
+    if (e != cudaSuccess) return e;
+    const int64_t blocks_needed = (nwork + kPropWarps - 1) / kPropWarps;
+    const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((int64_t)num_sms * std::max(bpm, 1), blocks_needed));
+    kern<<<(unsigned)grid, 32 * kPropWarps, 0, st>>>(lats, work, nwork, counter, words, n_words, offsets, P, err,
+                                                     stats);
+    return cudaGetLastError();
 }
 
 constexpr size_t grad_smem_bytes()
@@ -557,9 +658,10 @@ fgmm_status launch_grad(fgmm_handle* h, const float* X, const float* tgt, int64_
     if (s != FGMM_OK) return s;
     float* partial = static_cast<float*>(h->ws);
     const size_t smem = grad_smem_bytes();
-    cudaError_t e = cudaFuncSetAttribute(mlp_grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    auto kern = h->mlp_act == FGMM_MLP_ACT_SIGMOID ? mlp_grad_kernel<1> : mlp_grad_kernel<0>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(h, e, "mlp grad attribute");
-    mlp_grad_kernel<<<(unsigned)nb, kTrainThreads, smem, st>>>(X, tgt, B, theta, partial);
+    kern<<<(unsigned)nb, kTrainThreads, smem, st>>>(X, tgt, B, theta, partial);
     *partial_out = partial;
     *nblocks_out = (int)nb;
     return FGMM_OK;
@@ -650,7 +752,8 @@ fgmm_status fgmm_mlp_forward(fgmm_handle* h, const float* X, int64_t B, const vo
     if (B == 0) return FGMM_OK;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int64_t blocks = std::min<int64_t>((B + 127) / 128, (int64_t)h->num_sms * 8);
-    mlp_forward_kernel<<<(unsigned)blocks, 128, 0, st>>>(X, B, static_cast<const MlpPacked*>(packed), y);
+    auto kern = h->mlp_act == FGMM_MLP_ACT_SIGMOID ? mlp_forward_kernel<1> : mlp_forward_kernel<0>;
+    kern<<<(unsigned)blocks, 128, 0, st>>>(X, B, static_cast<const MlpPacked*>(packed), y);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? FGMM_OK : cuda_fail(h, e, "fgmm_mlp_forward launch");
 }
@@ -671,12 +774,15 @@ fgmm_status fgmm_decode_proposal(fgmm_handle* h, const fgmm_latent* lat, const v
     const int64_t blocks = nseg;
     unsigned long long* stats = h->stats_on ? h->d_stats : nullptr;
     const MlpPacked* P = static_cast<const MlpPacked*>(packed);
+    const bool sig = h->mlp_act == FGMM_MLP_ACT_SIGMOID;
     if (lat->dtype == FGMM_DTYPE_BF16) {
-        auto kern = P ? fgmm_dec_prop_kernel<__nv_bfloat16, false> : fgmm_dec_prop_kernel<__nv_bfloat16, true>;
+        auto kern = !P ? fgmm_dec_prop_kernel<__nv_bfloat16, true, 0>
+                       : (sig ? fgmm_dec_prop_kernel<__nv_bfloat16, false, 1> : fgmm_dec_prop_kernel<__nv_bfloat16, false, 0>);
         kern<<<(unsigned)blocks, 32, 0, st>>>(static_cast<const __nv_bfloat16*>(lat->params), lat->N, S, T, words,
                                               n_words, offsets, nseg, P, symbols_out, h->d_err, stats);
     } else {
-        auto kern = P ? fgmm_dec_prop_kernel<float, false> : fgmm_dec_prop_kernel<float, true>;
+        auto kern = !P ? fgmm_dec_prop_kernel<float, true, 0>
+                       : (sig ? fgmm_dec_prop_kernel<float, false, 1> : fgmm_dec_prop_kernel<float, false, 0>);
         kern<<<(unsigned)blocks, 32, 0, st>>>(static_cast<const float*>(lat->params), lat->N, S, T, words, n_words,
                                               offsets, nseg, P, symbols_out, h->d_err, stats);
     }
@@ -685,3 +791,33 @@ fgmm_status fgmm_decode_proposal(fgmm_handle* h, const fgmm_latent* lat, const v
 }
 
 }  // extern "C"
+
+namespace fgmm {
+
+cudaError_t launch_batch_prop(const BatchLatentDev* lats, const BatchWorkItem* work, int64_t nwork,
+                              unsigned long long* counter, const uint16_t* words, int64_t n_words,
+                              const int64_t* offsets, const void* packed, int dtype, int act, int32_t* err,
+                              unsigned long long* stats, int num_sms, cudaStream_t st)
+{
+    const MlpPacked* P = static_cast<const MlpPacked*>(packed);
+    if (dtype == FGMM_DTYPE_BF16) {
+        if (!P)
+            return launch_batch_prop_t<__nv_bfloat16, true, 0>(lats, work, nwork, counter, words, n_words, offsets,
+                                                              P, err, stats, num_sms, st);
+        if (act == FGMM_MLP_ACT_SIGMOID)
+            return launch_batch_prop_t<__nv_bfloat16, false, 1>(lats, work, nwork, counter, words, n_words, offsets,
+                                                               P, err, stats, num_sms, st);
+        return launch_batch_prop_t<__nv_bfloat16, false, 0>(lats, work, nwork, counter, words, n_words, offsets, P,
+                                                           err, stats, num_sms, st);
+    }
+    if (!P)
+        return launch_batch_prop_t<float, true, 0>(lats, work, nwork, counter, words, n_words, offsets, P, err, stats,
+                                                  num_sms, st);
+    if (act == FGMM_MLP_ACT_SIGMOID)
+        return launch_batch_prop_t<float, false, 1>(lats, work, nwork, counter, words, n_words, offsets, P, err,
+                                                   stats, num_sms, st);
+    return launch_batch_prop_t<float, false, 0>(lats, work, nwork, counter, words, n_words, offsets, P, err, stats,
+                                               num_sms, st);
+}
+
+}  // namespace fgmm

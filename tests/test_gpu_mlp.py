@@ -58,15 +58,20 @@ def test_training_triples_match_oracle():
     np.testing.assert_allclose(t.cpu().numpy(), to, rtol=1e-4, atol=1e-4)
 
 
-def test_loss_and_gradient_match_oracle():
+@pytest.mark.parametrize("act", [mlp.ACT_PL, mlp.ACT_SIGMOID])
+def test_loss_and_gradient_match_oracle(act):
     codec = _codec()
     lat = synth.make_latent(4, 16, 16, 3, seed=901, sigma_max=64.0)
     _, X, t, _ = _data(codec, lat, 2)
     rng = np.random.default_rng(3)
     theta = (mlp.init_params(5) + rng.normal(0, 0.05, mlp.N_PARAMS)).astype(np.float32)
-    loss, g = codec.mlp_loss_grad(X, t, torch.from_numpy(theta).cuda())
+    codec.set_mlp_act(act)
+    try:
+        loss, g = codec.mlp_loss_grad(X, t, torch.from_numpy(theta).cuda())
+    finally:
+        codec.set_mlp_act(mlp.ACT_PL)
     lo, go = mlp.loss_and_grad(theta.astype(np.float64), X.cpu().numpy().astype(np.float64),
-                               t.cpu().numpy().astype(np.float64))
+                               t.cpu().numpy().astype(np.float64), act)
     assert abs(loss - lo) <= 1e-5 * abs(lo)
     g = g.cpu().numpy().astype(np.float64)
     scale = np.abs(go).max()
@@ -93,17 +98,22 @@ def test_training_is_deterministic_and_resumes_exactly():
     assert tr_a[-1] < tr_a[0]
 
 
-def test_bf16_inference_matches_oracle_with_bf16_rounding():
+@pytest.mark.parametrize("act", [mlp.ACT_PL, mlp.ACT_SIGMOID])
+def test_bf16_inference_matches_oracle_with_bf16_rounding(act):
     codec = _codec()
     lat = synth.make_latent(4, 8, 8, 3, seed=903, sigma_max=64.0)
     _, X, _, _ = _data(codec, lat, 5)
     rng = np.random.default_rng(7)
     theta = (mlp.init_params(8) + rng.normal(0, 0.1, mlp.N_PARAMS)).astype(np.float32)
-    y = codec.mlp_forward(X, codec.mlp_pack(torch.from_numpy(theta).cuda())).cpu().numpy()
+    codec.set_mlp_act(act)
+    try:
+        y = codec.mlp_forward(X, codec.mlp_pack(torch.from_numpy(theta).cuda())).cpu().numpy()
+    finally:
+        codec.set_mlp_act(mlp.ACT_PL)
     W1, b1, W2, b2, w3, b3 = mlp.unpack(theta.astype(np.float64))
     x = _bf16(X.cpu().numpy())
-    h1 = _bf16(mlp.act(x @ _bf16(W1) + b1))
-    h2 = mlp.act(h1 @ _bf16(W2) + b2)
+    h1 = _bf16(mlp.act(x @ _bf16(W1) + b1, act))
+    h2 = mlp.act(h1 @ _bf16(W2) + b2, act)
     yo = h2 @ w3 + b3
     np.testing.assert_allclose(y, yo, rtol=2e-3, atol=2e-3 * (1 + np.abs(yo).max()))
 
@@ -210,3 +220,37 @@ def test_trained_proposal_beats_plain_binary_search():
           f"hit rate {hits / n_prop:.3f}")
     assert ev_prop / n_prop < 0.6 * (ev_plain / n_plain)
     assert hits / n_prop > 0.3
+
+
+@pytest.mark.parametrize("act", [mlp.ACT_PL, mlp.ACT_SIGMOID])
+def test_batched_proposal_decode_is_exact(act):
+    """One persistent launch decodes a batch of uneven K = 3 latents (scales
+    up to 64, escapes) with the network proposal (trained briefly, either
+    activation) and with the analytic proposal: every symbol equals the
+    encoded one, and the plain batch decode of the same plan agrees."""
+    codec = _codec()
+    shapes = [(8, 12, 20), (4, 32, 32), (16, 8, 8), (2, 4, 4)]
+    lats = [synth.make_latent(C, H, W, 3, seed=920 + i, sigma_max=64.0, escape_stress=0.002)
+            for i, (C, H, W) in enumerate(shapes)]
+    params = [dev_params(l.params) for l in lats]
+    syms = [dev_i32(l.symbols) for l in lats]
+    codec.set_mlp_act(act)
+    try:
+        _, X, t, _ = _data(codec, lats[1], 12)
+        tr = codec.MlpTrainer(mlp.init_params(13))
+        tr.train(X, t, steps=60, batch=1024, lr=3e-3)
+        P = tr.packed()
+        b = codec.Batch(params, syms, S=[64, 96, 32, 32])
+        b.encode()
+        for packed in (P, None):
+            for d in b.decoded:
+                d.fill_(12345)
+            b.decode_proposal(packed)
+            for i in range(len(lats)):
+                assert torch.equal(b.decoded[i], syms[i]), (act, packed is None, i)
+        for d in b.decoded:
+            d.fill_(-7)
+        b.decode()
+        assert all(torch.equal(b.decoded[i], syms[i]) for i in range(len(lats)))
+    finally:
+        codec.set_mlp_act(mlp.ACT_PL)

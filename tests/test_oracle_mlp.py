@@ -18,23 +18,25 @@ def _batch(seed, B=16):
     return theta, x, t
 
 
+@pytest.mark.parametrize("kind", [mlp.ACT_PL, mlp.ACT_SIGMOID])
 @pytest.mark.parametrize("seed", [0, 1])
-def test_gradient_matches_finite_differences(seed):
+def test_gradient_matches_finite_differences(seed, kind):
     theta, x, t = _batch(seed)
-    _, g = mlp.loss_and_grad(theta, x, t)
+    _, g = mlp.loss_and_grad(theta, x, t, kind)
     rng = np.random.default_rng(seed + 10)
     idx = rng.choice(mlp.N_PARAMS, 200, replace=False)
     eps = 1e-6
     for i in idx:
         tp = theta.copy(); tp[i] += eps
         tm = theta.copy(); tm[i] -= eps
-        fd = (mlp.loss_and_grad(tp, x, t)[0] - mlp.loss_and_grad(tm, x, t)[0]) / (2 * eps)
+        fd = (mlp.loss_and_grad(tp, x, t, kind)[0] - mlp.loss_and_grad(tm, x, t, kind)[0]) / (2 * eps)
         assert abs(fd - g[i]) <= 1e-6 + 1e-5 * abs(fd), (i, fd, g[i])
 
 
-def test_gradient_matches_autograd():
+@pytest.mark.parametrize("kind", [mlp.ACT_PL, mlp.ACT_SIGMOID])
+def test_gradient_matches_autograd(kind):
     theta, x, t = _batch(3, B=64)
-    loss, g = mlp.loss_and_grad(theta, x, t)
+    loss, g = mlp.loss_and_grad(theta, x, t, kind)
     th = torch.tensor(theta, dtype=torch.float64, requires_grad=True)
     I, H = mlp.N_IN, mlp.N_HID
     o = [0]
@@ -49,6 +51,8 @@ def test_gradient_matches_autograd():
     T = torch.tensor(t)
 
     def act(z):
+        if kind == mlp.ACT_SIGMOID:
+            return z * torch.sigmoid(1.702 * z)
         return z * torch.clamp(0.5 + mlp.ACT_C * z, 0.0, 1.0)
 
     y = act(act(X @ W1 + b1) @ W2 + b2) @ w3 + b3
@@ -71,6 +75,27 @@ def test_activation_is_piecewise_linear_gelu():
     from scipy.special import ndtr
     zz = np.linspace(-3, 3, 601)
     assert np.abs(mlp.act(zz) - zz * ndtr(zz)).max() < 0.2
+
+
+def test_sigmoid_activation_is_the_logistic_gelu():
+    """ACT_SIGMOID is z / (1 + exp(-1.702 z)) (GELU with Phi replaced by the
+    logistic form of Eq. 9): checked against that formula in extended
+    precision, the exact GELU z Phi(z) within the logistic form's known
+    0.02, and its limits (0 far left, identity far right, 0 at 0)."""
+    from scipy.special import ndtr
+    z = np.linspace(-8, 8, 3201)
+    a = mlp.act(z, mlp.ACT_SIGMOID)
+    zl = z.astype(np.longdouble)
+    ref = zl / (1 + np.exp(-np.longdouble(1.702) * zl))
+    np.testing.assert_allclose(a, ref.astype(np.float64), rtol=1e-12, atol=1e-15)
+    assert np.abs(a - z * ndtr(z)).max() < 0.021
+    assert mlp.act(np.array([0.0]), mlp.ACT_SIGMOID)[0] == 0.0
+    assert abs(mlp.act(np.array([-40.0]), mlp.ACT_SIGMOID)[0]) < 1e-20
+    assert abs(mlp.act(np.array([40.0]), mlp.ACT_SIGMOID)[0] - 40.0) < 1e-20
+    # derivative by central differences
+    h = 1e-6
+    fd = (mlp.act(z + h, mlp.ACT_SIGMOID) - mlp.act(z - h, mlp.ACT_SIGMOID)) / (2 * h)
+    np.testing.assert_allclose(mlp.act_grad(z, mlp.ACT_SIGMOID), fd, atol=1e-8)
 
 
 def test_features_are_standardised_and_order_free():
