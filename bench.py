@@ -110,6 +110,11 @@ def parse():
                     help="run only the Gaussian-single-model case (for profiling its decoder)")
     ap.add_argument("--proposal-only", action="store_true",
                     help="run only the learned-proposal case (for profiling its decoders)")
+    ap.add_argument("--proposal-latents", type=int, default=16, help="latents decoded in --proposal-only mode")
+    ap.add_argument("--proposal-train-scale", type=float, default=1.0,
+                    help="fraction of the training schedule in --proposal-only mode")
+    ap.add_argument("--batch-table", action="store_true",
+                    help="in --batch-only mode, also time the table-based coder on the batch in chunks")
     ap.add_argument("--batch-overhead", type=float, default=0.01,
                     help="container-overhead bound given to the stream autotuner in --batch-only mode")
     return ap.parse_args()
@@ -251,9 +256,63 @@ def measure_alu_peaks(dev, h, reps=5):
     return res
 
 
-def batch_case(dev, h, out, name, lats, alu_peak_tops, hbm_gbs, reps=5, max_overhead=0.01):
+def table_batch(dev, h, b, params, syms):
+    """The table-based comparison coder on a batch, in chunks of one latent
+    (its table, 1 KB per symbol, built for that latent alone and reused for
+    the next): per latent the table build + table-driven encode, then the
+    table build + table search decode, each launched on one stream; the
+    stream of every latent is asserted identical to the table-free batch's.
+    Returns total device time per direction (CUDA events around the whole
+    chunk loop)."""
+    import torch
+    from paper_2509_18815_gb300 import _abi, codec
+    import ctypes
+    nmax = max(int(p.shape[2]) for p in params)
+    table = torch.empty((nmax, 512), dtype=torch.int16, device=dev)
+    capmax = max(codec.encode_bound_words(int(p.shape[2]), S) for p, S in zip(params, b.S))
+    words = torch.empty(capmax, dtype=torch.int16, device=dev)
+    offsets = torch.empty(max(S // 32 for S in b.S) + 1, dtype=torch.int64, device=dev)
+    total = torch.empty(1, dtype=torch.int64, device=dev)
+    outs = torch.empty(nmax, dtype=torch.int32, device=dev)
+    sp = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    descs = [codec.latent(p) for p in params]
+    streams = [b.latent_stream(i) for i in range(len(params))]
+
+    def enc_all(check=False):
+        for i, (p, y, S) in enumerate(zip(params, syms, b.S)):
+            cap = codec.encode_bound_words(int(p.shape[2]), S)
+            h.check(_abi.fgmm_table_encode(h.ptr, ctypes.byref(descs[i]), y.data_ptr(), S, table.data_ptr(),
+                                           words.data_ptr(), cap, offsets.data_ptr(), total.data_ptr(), sp))
+            if check:
+                h.sync()
+                w_ref, o_ref = streams[i]
+                nw = int(total.item())
+                assert nw == w_ref.numel() and torch.equal(words[:nw], w_ref), f"table stream differs (latent {i})"
+                assert torch.equal(offsets[: S // 32 + 1], o_ref)
+
+    def dec_all(check=False):
+        for i, (p, y, S) in enumerate(zip(params, syms, b.S)):
+            w_ref, o_ref = streams[i]
+            n = int(p.shape[2])
+            h.check(_abi.fgmm_table_decode(h.ptr, ctypes.byref(descs[i]), table.data_ptr(), w_ref.data_ptr(),
+                                           w_ref.numel(), o_ref.data_ptr(), S, outs.data_ptr(), sp))
+            if check:
+                h.sync()
+                assert torch.equal(outs[:n], y), f"table decode differs (latent {i})"
+
+    enc_all(check=True)
+    dec_all(check=True)
+    te = _events_ms(enc_all, 2)
+    td = _events_ms(dec_all, 2)
+    h.sync()
+    del table
+    return te, td, nmax * 512 * 2
+
+
+def batch_case(dev, h, out, name, lats, alu_peak_tops, hbm_gbs, reps=5, max_overhead=0.01, table=False):
     """Batch of latents: one persistent launch per direction replayed from a
-    CUDA graph, autotuned streams per latent; adds out[name]."""
+    CUDA graph, autotuned streams per latent; adds out[name]. table: also
+    time the table-based comparison coder on the same batch."""
     import torch
     from paper_2509_18815_gb300 import codec
     params = [torch.from_numpy(l.params).to(dev) for l in lats]
@@ -274,6 +333,7 @@ def batch_case(dev, h, out, name, lats, alu_peak_tops, hbm_gbs, reps=5, max_over
     coded = 0.0
     for p_, s_ in zip(params, syms):
         coded += codec.rate_audit(p_, s_, h)[1]
+    tab = table_batch(dev, h, b, params, syms) if table else None
     b.close()
     bytes_sym = 36.0 + 4.0 + 16.0 * nw / N / 8.0
     enc_ops = 2 * N * ops_per_eval(3)
@@ -287,6 +347,13 @@ def batch_case(dev, h, out, name, lats, alu_peak_tops, hbm_gbs, reps=5, max_over
         "decode_roofline": {"alu_frac": dec_ops / (td * 1e-3) / 1e12 / alu_peak_tops,
                             "hbm_frac": N * bytes_sym / (td * 1e-3) / 1e9 / hbm_gbs},
     }
+    if tab is not None:
+        tte, ttd, tbytes = tab
+        out[name]["table_coder"] = {
+            "encode_msym_s": N / tte / 1e3, "decode_msym_s": N / ttd / 1e3, "ms_encode": tte, "ms_decode": ttd,
+            "encode_speedup_table_free": tte / te, "decode_speedup_table_free": ttd / td,
+            "chunks": len(lats), "table_mb_per_chunk_max": tbytes / 1e6, "stream_identical": True,
+            "schedule": "one latent per chunk: table build + table-driven coding per latent, launched back to back"}
     del params, syms
 
 
@@ -372,7 +439,7 @@ def ckbd_case(dev, h, flush, reps):
             "note": "host-launched sequence of split, two coder passes, context and merges (no graph)"}
 
 
-def proposal_case(dev, h, alu_peak_tops, reps=3, n_train=10_000_000):
+def proposal_case(dev, h, alu_peak_tops, reps=3, n_train=10_000_000, n_latents=16, train_scale=1.0):
     """The learned decode proposal on its workload: the network trained on
     n_train (params, slot, symbol) triples drawn from synthetic latents with
     scales up to 64 (slots uniform inside each symbol's interval), once with
@@ -393,7 +460,7 @@ def proposal_case(dev, h, alu_peak_tops, reps=3, n_train=10_000_000):
     rng = np.random.default_rng(11)
     X, t = codec.mlp_data(tp, ty, torch.from_numpy(rng.random(ntr).astype(np.float32)).to(dev), h)
     del tp, ty
-    schedule = [(6000, 3e-3), (3000, 1e-3), (3000, 3e-4)]
+    schedule = [(max(1, int(st * train_scale)), lr) for st, lr in [(6000, 3e-3), (3000, 1e-3), (3000, 3e-4)]]
     packed, train_s, final_loss = {}, {}, {}
     for name, act in (("pl", _abi.FGMM_MLP_ACT_PL), ("sigmoid", _abi.FGMM_MLP_ACT_SIGMOID)):
         codec.set_mlp_act(act, h)
@@ -407,7 +474,7 @@ def proposal_case(dev, h, alu_peak_tops, reps=3, n_train=10_000_000):
         packed[name] = tr.packed()
     codec.set_mlp_act(_abi.FGMM_MLP_ACT_PL, h)
     del X, t
-    lats = [synth.make_latent(320, 64, 96, 3, seed=1105 + i, sigma_max=64.0) for i in range(16)]
+    lats = [synth.make_latent(320, 64, 96, 3, seed=1105 + i, sigma_max=64.0) for i in range(n_latents)]
     params = [torch.from_numpy(l.params).to(dev) for l in lats]
     syms = [torch.from_numpy(l.symbols).to(dev) for l in lats]
     N = sum(l.N for l in lats)
@@ -525,7 +592,7 @@ def throughput_workloads(dev, alu_peak_tops, hbm_gbs, reps=5):
     shapes = synth.batch_shapes(64, seed=1004)
     batch_case(dev, h, out, "batch64_uneven_k3",
                [synth.make_latent(C, H, W, 3, 1004 + i) for i, (C, H, W) in enumerate(shapes)], alu_peak_tops,
-               hbm_gbs, reps)
+               hbm_gbs, reps, table=True)
 
     out["proposal_16x320x64x96_sigma64"] = proposal_case(dev, h, alu_peak_tops, reps=3)
     return out
@@ -1051,7 +1118,8 @@ def run_batch_only(args):
     out = {}
     batch_case(dev, h, out, f"batch{len(shapes)}_uneven_k3",
                [synth.make_latent(C, H, W, 3, 1004 + i) for i, (C, H, W) in enumerate(shapes)], alu_peak,
-               float(peaks.get("hbm_gbs", 6800.0)), reps=max(args.steps, 1), max_overhead=args.batch_overhead)
+               float(peaks.get("hbm_gbs", 6800.0)), reps=max(args.steps, 1), max_overhead=args.batch_overhead,
+               table=args.batch_table)
     print(json.dumps(out))
 
 
@@ -1074,7 +1142,9 @@ def run_proposal_only(args):
     torch.cuda.set_device(dev)
     h = codec.handle(dev)
     alu_peak = measure_alu_peaks(dev, h)["fma"]
-    print(json.dumps({"proposal_16x320x64x96_sigma64": proposal_case(dev, h, alu_peak, reps=max(args.steps, 1))}))
+    res = proposal_case(dev, h, alu_peak, reps=max(args.steps, 1), n_latents=args.proposal_latents,
+                        train_scale=args.proposal_train_scale)
+    print(json.dumps({f"proposal_{args.proposal_latents}x320x64x96_sigma64": res}))
 
 
 def main():

@@ -398,8 +398,8 @@ fgmm_status fgmm_decode_proposal(fgmm_handle *h, const fgmm_latent *lat, const v
  * stream), 2, 4, 8, 16 or 32 (G-ary search, G lanes per stream), or 0 to
  * choose from the number of segments (default). FGMM_OPT_DECODE_CLUSTER:
  * CTAs (a thread-block cluster, one SM each) sharing one segment when G > 1:
- * 1, 2 or 4 (at most G), 8 for G >= 8, or 0 for automatic.
- * FGMM_OPT_DECODE_ROUND0: points of the first search round that producer
+ * 1, 2 or 4 (at most G), 8 for G >= 8, or 0 for automatic; G = 32 takes at
+ * least 2. FGMM_OPT_DECODE_ROUND0: points of the first search round that producer
  * warps of the warp-specialised decoder evaluate ahead of the state chain
  * when G = 16: 16 (two streams per producer warp) or 32, or 0 for
  * automatic; G = 8 and 32 always take 32. The decoded symbols depend on
@@ -510,8 +510,12 @@ fgmm_status fgmm_peak_probe(fgmm_handle *h, int32_t kind, int64_t iters, float *
  * on the array and corrupt each other's output: serialise them.
  *
  * The first call on each device looks up the array's device address
- * (cudaGetSymbolAddress, with that device current) and caches it; make that
- * first call before any stream capture on the device.
+ * (cudaGetSymbolAddress, with that device current) and caches it with the
+ * id of the CUDA context it belongs to; make that first call before any
+ * stream capture on the device. A call in another context of the device
+ * (after cudaDeviceReset, which reloads the library's device code) looks the
+ * address up again, so make the first call after a reset outside stream
+ * capture too.
  *
  * Arguments are those of fgmm_encode (all device pointers, caller-owned),
  * without the handle, plus

@@ -12,6 +12,7 @@
 //   4. fgmm_compact_kernel: copies segments to their offsets.
 // Decode (Sec. III-A: binary search over the same on-the-fly CDF) is one
 // launch of a kernel in fgmm_decode.cu.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -716,9 +717,44 @@ constexpr int kNoAllocMaxDevices = 128;
 std::mutex g_noalloc_mu;
 void* g_noalloc_ptr[kNoAllocMaxDevices];
 int g_noalloc_sms[kNoAllocMaxDevices];
+unsigned long long g_noalloc_ctx[kNoAllocMaxDevices];   // context the address belongs to (0 = none yet)
 
-// One-time set-up per device, with that device current: look up and cache
-// the device address of the scratch array and the SM count.
+// Unique id of the calling thread's current CUDA context (0 if none), from
+// the driver entry points the runtime hands out (no link against the driver
+// library). A context that replaces another (after cudaDeviceReset, for
+// example) has a new id, and the array may have a new address in it.
+unsigned long long current_context_id()
+{
+    using GetCurrent = CUresult (*)(CUcontext*);
+    using GetId = CUresult (*)(CUcontext, unsigned long long*);
+    static GetCurrent get_current = nullptr;
+    static GetId get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<GetCurrent>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<GetId>(f);
+        cudaGetLastError();
+    });
+    if (!get_current || !get_id) return 0;
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (get_current(&ctx) != CUDA_SUCCESS || !ctx) return 0;
+    if (get_id(ctx, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
+
+// Set-up per device and context, with that device current: look up (with
+// cudaGetSymbolAddress, which also makes the device's context current if
+// none is) and cache the device address of the scratch array and the SM
+// count; look them up again whenever the current context is not the one
+// the cached address was taken in.
 cudaError_t noalloc_scratch_for_current_device(void** ptr, int* sms)
 {
     int dev = 0;
@@ -726,7 +762,8 @@ cudaError_t noalloc_scratch_for_current_device(void** ptr, int* sms)
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kNoAllocMaxDevices) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
+    const unsigned long long ctx = current_context_id();
+    if (!g_noalloc_ptr[dev] || ctx == 0 || ctx != g_noalloc_ctx[dev]) {
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, fgmm_noalloc_scratch);
         if (e != cudaSuccess) return e;
@@ -735,6 +772,7 @@ cudaError_t noalloc_scratch_for_current_device(void** ptr, int* sms)
         if (e != cudaSuccess) return e;
         g_noalloc_ptr[dev] = p;
         g_noalloc_sms[dev] = n;
+        g_noalloc_ctx[dev] = current_context_id();   // the context is current now
     }
     *ptr = g_noalloc_ptr[dev];
     *sms = g_noalloc_sms[dev];

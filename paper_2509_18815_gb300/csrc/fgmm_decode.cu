@@ -52,18 +52,16 @@ void decode_resolve(int64_t nseg, int num_sms, int opt_lanes, int opt_cluster, i
     if (G < 2) CL = 1;
     if (G < 8 && CL > 4) CL = 4;   // the G-ary kernel takes clusters of up to 4
     if (CL > G) CL = G;
+    if (G == 32 && CL < 2) CL = 2;   // 32 lanes per stream: the warp-specialised kernel, clusters of 2 or more
     *lanes = G;
     *cluster = CL;
     // G >= 8 with a cluster: the warp-specialised kernel (32 / G streams per
-    // consumer warp; a 16-point first round only with 16 lanes per stream);
-    // G = 32 in one CTA: the wide kernel
+    // consumer warp; a 16-point first round only with 16 lanes per stream)
     if (G == 1) *kernel = FGMM_DEC_LANE;
     else if (CL >= 2 && G >= 8) *kernel = FGMM_DEC_WS;
-    else if (G == 32) *kernel = FGMM_DEC_WIDE;
     else *kernel = FGMM_DEC_COOP;
     if (opt_round0 > 0) R0 = opt_round0;
-    if (*kernel == FGMM_DEC_WS) *round0 = G == 16 ? R0 : 32;
-    else *round0 = *kernel == FGMM_DEC_WIDE ? 32 : 0;
+    *round0 = *kernel == FGMM_DEC_WS ? (G == 16 ? R0 : 32) : 0;
 }
 
 cudaError_t launch_decode(const DecodeArgs& a, int K, int dtype, int G, int CL, cudaStream_t st)

@@ -13,11 +13,12 @@
 //   symbol; the choice when there are enough segments to fill the GPU. The
 //   next step's parameters are loaded one step ahead into registers.
 //
-// * fgmm_dec_ws_kernel (G = 32, clusters of 2-8 CTAs): one consumer warp per
-//   stream runs the state-dependent chain; a producer warp per stream
-//   prepares the mixture and the 32-point round 0 two steps ahead.
+// * fgmm_dec_ws_kernel (G = 8, 16 or 32, clusters of 2-8 CTAs; its own
+//   units, fgmm_decode_ws.cuh): consumer warps run the state-dependent
+//   chain; producer warps prepare the mixture and the first search round two
+//   steps ahead.
 //
-// * fgmm_dec_coop_kernel (G = 2 .. 32): G lanes cooperate on one stream and
+// * fgmm_dec_coop_kernel (G = 2 .. 16): G lanes cooperate on one stream and
 //   evaluate G points of the quantised CDF per round (G-ary search), so a
 //   step needs ~log_{G+1}(W) dependent rounds instead of ~log_2(W). A CTA of
 //   G warps holds one segment; parameters are staged through a cp.async ring
@@ -383,269 +384,6 @@ __global__ void __launch_bounds__(32 * G / CL) fgmm_dec_coop_kernel(const T* __r
     seg_sync<CL>();   // no CTA leaves while another may still address its shared memory
 }
 
-// ---------------------------------------------------------------------------
-// Wide decoder: one warp (32 lanes) per stream, CL CTAs per segment.
-// Round 0 evaluates Q at 32 points of the window (the last is hi + 1, the
-// escape test); it depends only on the parameters, so the round 0 of step
-// t + 1 is computed while step t runs and leaves the dependent chain. With
-// 32 points the bracket it leaves holds at most 16 symbols, so one more
-// round over its interior always finishes the search: each step costs one
-// dependent CDF evaluation. The segment's refill mask is combined with one
-// shared-memory OR per warp (remote for CL > 1) into triple-buffered words.
-// ---------------------------------------------------------------------------
-template <int CL>
-__device__ __forceinline__ void or_all(uint32_t* local, uint32_t v)
-{
-    if constexpr (CL == 1) {
-        atomicOr(local, v);
-    } else {
-        const uint32_t a = (uint32_t)__cvta_generic_to_shared(local);
-#pragma unroll
-        for (uint32_t r = 0; r < (uint32_t)CL; ++r) {
-            uint32_t ra;
-            asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(a), "r"(r));
-            asm volatile("red.shared::cluster.or.b32 [%0], %1;" ::"r"(ra), "r"(v) : "memory");
-        }
-    }
-}
-
-template <int K>
-__device__ __forceinline__ int wide_point(const Mix<K>& m, int lane)
-{
-    const int W = m.hi - m.lo + 1;
-    return m.lo + ((lane + 1) * W + 31) / 32;
-}
-
-template <int K, typename T, int CL>
-__global__ void __launch_bounds__(32 * 32 / CL) fgmm_dec_wide_kernel(const T* __restrict__ params, int64_t N,
-                                                                     int32_t S, int64_t T_steps,
-                                                                     const uint16_t* __restrict__ words,
-                                                                     int64_t n_words,
-                                                                     const int64_t* __restrict__ offsets,
-                                                                     int32_t* __restrict__ out, int32_t* err,
-                                                                     unsigned long long* stats, int mode)
-{
-    constexpr int SPC = 32 / CL;       // streams (warps) per CTA
-    constexpr int NT = 32 * SPC;
-    extern __shared__ __align__(16) unsigned char smem[];
-    T* ring = reinterpret_cast<T*>(smem);                                                  // [kRing][3K][SPC]
-    uint32_t* masks = reinterpret_cast<uint32_t*>(smem + sizeof(T) * kRing * 3 * K * SPC); // [3][4]
-    uint16_t* wsm = reinterpret_cast<uint16_t*>(masks + 12);                               // [kWordCap]
-
-    const int rank = CL > 1 ? (int)cluster_rank() : 0;
-    const int tid = threadIdx.x, lane = tid & 31, wl = tid >> 5;
-    const int ws = rank * SPC + wl;                    // stream within the segment
-    const uint32_t bit = 1u << ws;
-    const int64_t g = blockIdx.x / CL;
-    const int64_t beg = offsets[g], end = offsets[g + 1];
-    if (!(beg >= 0 && end <= n_words && end - beg >= 64)) {
-        if (tid == 0 && rank == 0) set_error(err, kErrCorrupt);
-        return;
-    }
-    const int64_t seg_len = end - beg;
-    const bool staged = seg_len <= kWordCap;
-    const uint16_t* wsrc = staged ? wsm : words;
-    const int64_t wbase = staged ? beg : 0;
-    const int64_t nbase = g * 32 + rank * SPC;
-#pragma unroll
-    for (int p = 0; p < kPF; ++p) {
-        if (p < T_steps)
-            stage_params<K, T, SPC>(ring + (p % kRing) * 3 * K * SPC, params, N, p * (int64_t)S + nbase, tid, NT, mode);
-        cp_async_commit();
-    }
-    if (staged)
-        for (int64_t i = tid; i < seg_len; i += NT) wsm[i] = __ldg(words + beg + i);
-    if (tid < 12) masks[tid] = 0u;
-    cp_async_wait<kPF - 2>();   // steps 0 and 1 resident
-    seg_sync<CL>();
-
-    uint32_t x = (uint32_t)wsrc[end - 64 + 2 * ws - wbase] | ((uint32_t)wsrc[end - 63 + 2 * ws - wbase] << 16);
-    int64_t ptr = end - 64;
-    bool bad = false, badp = false;
-    int probes = 0, decoded = 0;
-
-    // step 0's mixture and round-0 probe
-    Mix<K> m;
-    uint32_t q0 = 0;
-    {
-        RawParams<K> r;
-#pragma unroll
-        for (int i = 0; i < 3 * K; ++i) r.v[i] = smem_param<T>(ring + i * SPC + wl);
-        const bool ok = mix_from_params<K>(r, m);
-        const bool act0 = T_steps > 0 && g * 32 + ws < N;
-        badp |= act0 && !ok;
-        if (act0) { q0 = q_at<K>(m, wide_point<K>(m, lane)); ++probes; }
-    }
-
-    for (int64_t t = 0; t < T_steps; ++t) {
-        if (t + kPF < T_steps)
-            stage_params<K, T, SPC>(ring + ((t + kPF) % kRing) * 3 * K * SPC, params, N,
-                                    (t + kPF) * (int64_t)S + nbase, tid, NT, mode);
-        cp_async_commit();
-        const int64_t n = t * (int64_t)S + g * 32 + ws;
-        const bool act = n < N;   // uniform over the warp
-        const uint32_t slot = x & 0xffffu;
-        int32_t s = 0;
-        bool esc = false;
-        uint32_t start = 0, freq = 1;
-        // round 0 (precomputed): the symbol lies between points c-1 and c
-        const int c = __popc(__ballot_sync(kFull, act && q0 <= slot));
-        const uint32_t q_last = __shfl_sync(kFull, q0, 31);   // Q(hi + 1)
-        if (act && c == 32) {
-            esc = true;
-            start = q_last;
-            freq = kM - start;
-        }
-        const int W = m.hi - m.lo + 1;
-        const int a = c > 0 ? m.lo + (c * W + 31) / 32 : m.lo;
-        const int b = m.lo + ((min(c, 31) + 1) * W + 31) / 32;
-        const uint32_t qc1 = __shfl_sync(kFull, q0, c > 0 ? c - 1 : 0);
-        const uint32_t qa0 = c > 0 ? qc1 : 0u;                 // Q(lo) = 0
-        const uint32_t qb0 = __shfl_sync(kFull, q0, c < 32 ? c : 31);
-        // Round 1 over the points strictly inside (a, b) (at most 15) and the
-        // next step's mixture and round-0 probe (independent of the state)
-        // are evaluated unconditionally -- pure arithmetic on values already
-        // in registers and shared memory -- so the two dependent chains sit
-        // in one basic block and overlap; unused results are discarded.
-        const int L = b - a;
-        const bool valid = act && !esc && lane < L - 1;
-        const uint32_t q1 = q_at<K>(m, min(a + 1 + lane, m.hi + 1));
-        probes += valid;
-        Mix<K> mn;
-        uint32_t q0n;
-        const bool actn = (t + 1 < T_steps) && (n + S < N);
-        {
-            const T* slot_p = ring + ((t + 1) % kRing) * 3 * K * SPC;
-            RawParams<K> r;
-#pragma unroll
-            for (int i = 0; i < 3 * K; ++i) r.v[i] = smem_param<T>(slot_p + i * SPC + wl);
-            const bool ok = mix_from_params<K>(r, mn);
-            badp |= actn && !ok;
-            q0n = q_at<K>(mn, wide_point<K>(mn, lane));
-            probes += actn;
-        }
-        const int c1 = __popc(__ballot_sync(kFull, valid && q1 <= slot));
-        const uint32_t q1a = __shfl_sync(kFull, q1, c1 > 0 ? c1 - 1 : 0);
-        const uint32_t q1b = __shfl_sync(kFull, q1, c1 < 31 ? c1 : 31);
-        if (act && !esc) {
-            s = a + c1;
-            start = c1 > 0 ? q1a : qa0;
-            freq = (c1 < L - 1 ? q1b : qb0) - start;
-        }
-        if (act) {
-            x = freq * (x >> 16) + slot - start;
-            decoded += (lane == 0);
-        }
-        // parameters of step t + 2 resident before the barrier publishes them
-        cp_async_wait<kPF - 2>();
-        uint32_t* mk = masks + (int)(t % 3) * 4;
-        const bool need = act && x < kL;
-        if (lane == 0) {
-            if (need) or_all<CL>(mk, bit);
-            if (esc) or_all<CL>(mk + 1, bit);
-        }
-        seg_sync<CL>();
-        const uint32_t M = mk[0], E = mk[1];
-        if (tid < 4) masks[(int)((t + 2) % 3) * 4 + tid] = 0u;   // buffer of step t + 2 (last read at t - 1)
-        const uint32_t below = bit - 1u;
-        if (M) {
-            const int cnt = __popc(M);
-            if (need) {
-                const int64_t idx = ptr - cnt + __popc(M & below);
-                uint32_t v = 0;
-                if (idx >= beg) v = wsrc[idx - wbase];
-                else bad = true;
-                x = (x << 16) | v;
-            }
-            ptr -= cnt;
-        }
-        if (E) {   // uniform over the segment
-            uint32_t hi16 = 0, lo16 = 0;
-            if (esc) { hi16 = x & 0xffffu; x >>= 16; }
-            const bool n2 = esc && x < kL;
-            if (lane == 0 && n2) or_all<CL>(mk + 2, bit);
-            seg_sync<CL>();
-            const uint32_t M2 = mk[2];
-            if (M2) {
-                const int cnt = __popc(M2);
-                if (n2) {
-                    const int64_t idx = ptr - cnt + __popc(M2 & below);
-                    uint32_t v = 0;
-                    if (idx >= beg) v = wsrc[idx - wbase];
-                    else bad = true;
-                    x = (x << 16) | v;
-                }
-                ptr -= cnt;
-            }
-            if (esc) { lo16 = x & 0xffffu; x >>= 16; }
-            const bool n3 = esc && x < kL;
-            if (lane == 0 && n3) or_all<CL>(mk + 3, bit);
-            seg_sync<CL>();
-            const uint32_t M3 = mk[3];
-            if (M3) {
-                const int cnt = __popc(M3);
-                if (n3) {
-                    const int64_t idx = ptr - cnt + __popc(M3 & below);
-                    uint32_t v = 0;
-                    if (idx >= beg) v = wsrc[idx - wbase];
-                    else bad = true;
-                    x = (x << 16) | v;
-                }
-                ptr -= cnt;
-            }
-            if (esc) s = (int32_t)((hi16 << 16) | lo16);
-        }
-        if (act && lane == 0) out[n] = s;
-        m = mn;
-        q0 = q0n;
-    }
-    cp_async_wait<0>();
-    const bool fail = bad || x != kL || ptr != beg;
-    if (__syncthreads_or(fail) && tid == 0) set_error(err, kErrCorrupt);
-    if (__syncthreads_or(badp) && tid == 0) set_error(err, kErrBadParams);
-    if (stats) {
-        int p = probes, d = decoded;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            p += __shfl_xor_sync(kFull, p, o);
-            d += __shfl_xor_sync(kFull, d, o);
-        }
-        if (lane == 0) {
-            atomicAdd(stats, (unsigned long long)p);
-            atomicAdd(stats + 1, (unsigned long long)d);
-        }
-    }
-    seg_sync<CL>();
-}
-
-template <int K, typename T, int CL>
-cudaError_t launch_wide(const DecodeArgs& a, cudaStream_t st)
-{
-    constexpr int SPC = 32 / CL;
-    const size_t smem = sizeof(T) * kRing * 3 * K * SPC + sizeof(uint32_t) * 12 + sizeof(uint16_t) * kWordCap;
-    auto kern = fgmm_dec_wide_kernel<K, T, CL>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    const uintptr_t base = reinterpret_cast<uintptr_t>(a.params);
-    int mode = 0;
-    if (base % 16 == 0 && (a.N * (int64_t)sizeof(T)) % 16 == 0 && SPC * sizeof(T) >= 16) mode = 2;
-    else if (base % 4 == 0 && (a.N * (int64_t)sizeof(T)) % 4 == 0 && SPC * sizeof(T) >= 4) mode = 1;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)(a.nseg * CL));
-    cfg.blockDim = dim3(32 * SPC);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = CL;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = CL > 1 ? 1 : 0;
-    return cudaLaunchKernelEx(&cfg, kern, static_cast<const T*>(a.params), a.N, a.S, a.T, a.words, a.n_words,
-                              a.offsets, a.out, a.err, a.stats, mode);
-}
-
 // Warp-specialised decoder (fgmm_decode_ws.cuh), compiled in its own units.
 template <typename T>
 cudaError_t launch_ws_any(const DecodeArgs& a, int K, int CL, int SPW, cudaStream_t st)
@@ -654,14 +392,6 @@ cudaError_t launch_ws_any(const DecodeArgs& a, int K, int CL, int SPW, cudaStrea
     else return launch_ws_f32(a, K, CL, SPW, st);
 }
 
-template <int K, typename T>
-cudaError_t launch_wide_cl(const DecodeArgs& a, int CL, cudaStream_t st)
-{
-    // warp-specialised with a cluster per segment; CL = 1 keeps one warp per
-    // stream in one CTA
-    if (CL >= 2) return launch_ws_any<T>(a, K, CL, 1, st);
-    return launch_wide<K, T, 1>(a, st);
-}
 
 template <int K, typename T, int G, int CL>
 cudaError_t launch_coop(const DecodeArgs& a, cudaStream_t st)
@@ -713,7 +443,7 @@ cudaError_t launch_k(const DecodeArgs& a, int G, int CL, cudaStream_t st)
     case 4: return launch_coop_cl<K, T, 4>(a, CL, st);
     case 8: return CL >= 2 ? launch_ws_any<T>(a, K, CL, 4, st) : launch_coop_cl<K, T, 8>(a, 1, st);
     case 16: return CL >= 2 ? launch_ws_any<T>(a, K, CL, 2, st) : launch_coop_cl<K, T, 16>(a, 1, st);
-    case 32: return launch_wide_cl<K, T>(a, CL, st);
+    case 32: return launch_ws_any<T>(a, K, CL < 2 ? 2 : CL, 1, st);
     default: {
         const int threads = 32;   // one warp (segment) per block: segments spread over all SMs
         const int64_t blocks = (a.nseg * 32 + threads - 1) / threads;

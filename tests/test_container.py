@@ -18,9 +18,11 @@ def _coded(seed=3, S=64):
 def test_round_trip_decodes_the_same_symbols():
     lat, words, offsets, S = _coded()
     blob = container.pack(words, offsets, S, lat.N, 3)
-    assert len(blob) == 28 + 4 * (S // 32) + 2 * words.size
+    assert len(blob) == 36 + 4 * (S // 32) + 2 * words.size
     c = container.unpack(blob)
     assert (c["S"], c["N"], c["K"], c["coder"]) == (S, lat.N, 3, container.CODER_GMM)
+    assert (c["phi"], c["dtype"], c["levels"]) == (container.PHI_AS, container.DTYPE_F32, 0)
+    container.expect(c, container.PHI_AS, container.DTYPE_F32)
     np.testing.assert_array_equal(c["words"], words)
     np.testing.assert_array_equal(c["offsets"], offsets)
     out, st = oracle.decode(lat.params, c["words"], c["offsets"], c["S"])
@@ -30,18 +32,56 @@ def test_round_trip_decodes_the_same_symbols():
 
 def test_gsm_kind_and_empty_latent():
     words, offsets = oracle.encode(np.zeros((3, 1, 0), np.float32), np.zeros(0, np.int32), 32)
-    c = container.unpack(container.pack(words, offsets, 32, 0, 1, coder=container.CODER_GSM))
+    lv = oracle.gsm_levels()
+    c = container.unpack(container.pack(words, offsets, 32, 0, 1, coder=container.CODER_GSM, levels=lv))
     assert c["coder"] == container.CODER_GSM and c["N"] == 0 and c["words"].size == 64
+    assert c["levels"] == 64 and c["levels_digest"] == container.levels_digest(lv)
+    container.expect(c, container.PHI_AS, container.DTYPE_F32, levels=lv)
+    other = lv.copy()
+    other[7] = np.nextafter(other[7], np.float32(1e9))
+    for bad in (None, lv[:63], other):
+        with pytest.raises(ValueError):
+            container.expect(c, container.PHI_AS, container.DTYPE_F32, levels=bad)
+    with pytest.raises(ValueError):
+        container.pack(words, offsets, 32, 0, 1, coder=container.CODER_GSM)          # GSM without levels
+    with pytest.raises(ValueError):
+        container.pack(words, offsets, 32, 0, 1, levels=lv)                          # levels on the mixture coder
+
+
+def test_logistic_stream_records_its_approximation():
+    """A stream coded with the logistic approximation round-trips through
+    the container with that approximation recorded; a decoder set to A&S is
+    refused before it decodes, and the recorded approximation decodes it."""
+    lat = synth.make_latent(4, 8, 16, 3, seed=8)
+    with oracle.approximation(oracle.PHI_LOGISTIC):
+        words, offsets = oracle.encode(lat.params, lat.symbols, 64)
+    blob = container.pack(words, offsets, 64, lat.N, 3, phi=container.PHI_LOGISTIC, dtype=container.DTYPE_BF16)
+    c = container.unpack(blob)
+    assert (c["phi"], c["dtype"]) == (container.PHI_LOGISTIC, container.DTYPE_BF16)
+    with pytest.raises(ValueError):
+        container.expect(c, container.PHI_AS, container.DTYPE_BF16)
+    with pytest.raises(ValueError):
+        container.expect(c, container.PHI_LOGISTIC, container.DTYPE_F32)
+    container.expect(c, container.PHI_LOGISTIC, container.DTYPE_BF16)
+    with oracle.approximation(c["phi"]):
+        out, st = oracle.decode(lat.params, c["words"], c["offsets"], c["S"])
+    assert st == oracle.OK
+    np.testing.assert_array_equal(out, lat.symbols)
+    for field, value in ((21, 3), (22, 2), (23, 5)):   # unknown phi, dtype; levels on the mixture coder
+        b = bytearray(blob)
+        b[field] = value
+        with pytest.raises(ValueError):
+            container.unpack(bytes(b))
 
 
 def test_malformed_containers_are_refused():
     lat, words, offsets, S = _coded()
     blob = container.pack(words, offsets, S, lat.N, 3)
     bad = [blob[:10], blob[:40], blob[:-2], blob + b"\0\0", b"XGMM" + blob[4:],
-           blob[:4] + b"\x02\x00" + blob[6:]]
+           blob[:4] + b"\x01\x00" + blob[6:]]
     # a segment length below the 64 words of its final states
     b = bytearray(blob)
-    b[28:32] = (10).to_bytes(4, "little")
+    b[36:40] = (10).to_bytes(4, "little")
     bad.append(bytes(b))
     # S not matching the segment count
     b = bytearray(blob)

@@ -257,7 +257,7 @@ def test_decode_plan_follows_segments_and_options():
         _set_lanes(4)
         assert codec.decode_plan(few) == {"lanes": 4, "cluster": 1, "round0": 0, "kernel": "fgmm_dec_coop_kernel"}
         _set_lanes(32)
-        assert codec.decode_plan(few) == {"lanes": 32, "cluster": 1, "round0": 32, "kernel": "fgmm_dec_wide_kernel"}
+        assert codec.decode_plan(few) == {"lanes": 32, "cluster": 2, "round0": 32, "kernel": "fgmm_dec_ws_kernel"}
         _set_lanes(4)
         _set_cluster(8)
         assert codec.decode_plan(few) == {"lanes": 4, "cluster": 4, "round0": 0, "kernel": "fgmm_dec_coop_kernel"}
@@ -271,7 +271,7 @@ def test_decode_plan_follows_segments_and_options():
         assert codec.decode_plan(few) == {"lanes": 1, "cluster": 1, "round0": 0, "kernel": "fgmm_dec_kernel"}
         _set_lanes(32)
         _set_cluster(1)
-        assert codec.decode_plan(few) == {"lanes": 32, "cluster": 1, "round0": 32, "kernel": "fgmm_dec_wide_kernel"}
+        assert codec.decode_plan(few) == {"lanes": 32, "cluster": 2, "round0": 32, "kernel": "fgmm_dec_ws_kernel"}
         _set_lanes(0)
         _set_cluster(0)
         _set_round0(32)

@@ -73,3 +73,44 @@ def test_noalloc_rejects_requests_beyond_its_scratch():
                                   out.data_ptr(), out.data_ptr(), None)
     assert st == _abi.FGMM_ERR_TOO_LARGE
     assert b"scratch" in _abi.fgmm_status_string(st)
+
+
+def _scratch_bytes(N, S):
+    """The scratch a request needs, by the size rule the header states:
+    align256(4 N) + align256(2 (S/32) align8(96 ceil(N/S) + 64)) + 8 (S/32)."""
+    def a(x, m):
+        return (x + m - 1) // m * m
+    T = -(-N // S)
+    return a(4 * N, 256) + a(2 * (S // 32) * a(96 * T + 64, 8), 256) + 8 * (S // 32)
+
+
+def test_noalloc_at_the_largest_request_that_fits():
+    """At S = 1024 the largest N whose scratch fits the fixed array (found
+    from the header's size rule) encodes exactly as fgmm_encode does, and
+    N + S symbols are rejected as too large without any launch."""
+    need_gpu()
+    from paper_2509_18815_gb300 import _abi, codec
+    S, limit = 1024, _abi.FGMM_NOALLOC_SCRATCH_BYTES
+    lo, hi = 0, 1 << 24
+    while hi - lo > 1:
+        mid = (lo + hi) // 2
+        if _scratch_bytes(mid, S) <= limit:
+            lo = mid
+        else:
+            hi = mid
+    N = lo
+    assert _scratch_bytes(N, S) <= limit < _scratch_bytes(N + S, S)
+    lat = synth.make_latent(1, 1, N, 3, seed=78)
+    dp, ds = dev_params(lat.params), dev_i32(lat.symbols)
+    w1, o1, n1 = _encode_noalloc(dp, ds, S)
+    w0, o0, n0 = _encode_reference(dp, ds, S)
+    assert n1 == n0
+    np.testing.assert_array_equal(o1, o0)
+    np.testing.assert_array_equal(w1, w0)
+    big = synth.make_latent(1, 1, N + S, 3, seed=79)
+    dpb, dsb = dev_params(big.params), dev_i32(big.symbols)
+    lat_b = codec.latent(dpb)
+    out = torch.zeros(16, dtype=torch.int64, device="cuda")
+    st = _abi.fgmm_encode_noalloc(ctypes.byref(lat_b), dsb.data_ptr(), S, out.data_ptr(), 0, out.data_ptr(),
+                                  out.data_ptr(), out.data_ptr(), None)
+    assert st == _abi.FGMM_ERR_TOO_LARGE
