@@ -219,7 +219,11 @@ def cpu_baseline(lat, S, budget_s=6.0):
 
 
 def _events_ms(fn, reps, flush=None):
+    """Median CUDA-event time of fn over reps runs, after one untimed run
+    (first-launch costs such as a graph's upload stay out)."""
     import torch
+    fn()
+    torch.cuda.synchronize()
     ts = []
     for i in range(reps):
         if flush is not None:

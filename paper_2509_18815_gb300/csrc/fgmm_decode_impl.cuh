@@ -42,6 +42,15 @@ namespace {
 
 constexpr uint32_t kFull = 0xffffffffu;
 
+// Q(j) <= slot for lo < j <= hi + 1, decided on the fast steering
+// evaluation of the CDF (thr = slot + 1); see search_slot_guided.
+template <int K>
+__device__ __forceinline__ bool fast_le(const Mix<K>& m, int j, float thr)
+{
+    const float v = fminf(mix_cdf_fast<K>(m, (float)j - 0.5f), 1.0f);
+    return fmaf(m.tp, v, (float)(j - m.lo)) < thr;
+}
+
 // ---------------------------------------------------------------------------
 // G = 1: binary search, one lane per stream.
 // ---------------------------------------------------------------------------
@@ -283,57 +292,79 @@ __global__ void __launch_bounds__(32 * G / CL) fgmm_dec_coop_kernel(const T* __r
             badp |= act && !ok;
         }
         const uint32_t slot = x & 0xffffu;
-        // round 0: G points p_i = lo + ceil((i+1) W / G); p_{G-1} = hi + 1
+        const uint32_t gm = (G == 32) ? kFull : ((1u << G) - 1u);
         const int W = m.hi - m.lo + 1;
-        int a = m.lo, b = m.hi + 1;
-        uint32_t qa = 0, qb = 0;
+        // G-ary search over [lo, hi + 2) steered by the fast evaluation of
+        // the CDF (fast_le); Q(hi + 2) = 2^16 is never evaluated. Round 0:
+        // G points p_i = lo + ceil((i+1) W / G), p_{G-1} = hi + 1.
+        const float thr = (float)(slot + 1u);
+        int a = m.lo, b = m.hi + 2;
         {
             const int p = m.lo + ((sub + 1) * W + G - 1) / G;
-            const uint32_t q = act ? q_at<K>(m, p) : 0u;
+            const bool le = act && fast_le<K>(m, p, thr);
             probes += act;
-            const uint32_t bal = (__ballot_sync(kFull, act && q <= slot) >> gshift) & ((G == 32) ? kFull : ((1u << G) - 1u));
-            const int c = __popc(bal);
-            const uint32_t q_c = __shfl_sync(kFull, q, grp * G + (c < G ? c : G - 1));
-            const uint32_t q_c1 = __shfl_sync(kFull, q, grp * G + (c > 0 ? c - 1 : 0));
-            const int p_c = m.lo + ((min(c, G - 1) + 1) * W + G - 1) / G;
-            const int p_c1 = m.lo + (c * W + G - 1) / G;   // p_{c-1}
-            if (c == G) {
-                esc = true;
-                start = q_c;   // Q(hi + 1)
-                freq = kM - q_c;
-                a = b;         // nothing left to search
-            } else {
-                b = p_c;
-                qb = q_c;
-                if (c > 0) { a = p_c1; qa = q_c1; }
-            }
+            const int c = __popc((__ballot_sync(kFull, le) >> gshift) & gm);
+            if (c > 0) a = m.lo + (c * W + G - 1) / G;
+            if (c < G) b = m.lo + ((c + 1) * W + G - 1) / G;
         }
         // further rounds: G points strictly inside (a, b)
-        while (__any_sync(kFull, act && !esc && b - a > 1)) {
-            const bool live = act && !esc && b - a > 1;
+        while (__any_sync(kFull, act && b - a > 1)) {
+            const bool live = act && b - a > 1;
             const int L = b - a;
             const bool fine = L - 1 <= G;
             const int p = fine ? a + 1 + sub : a + ((sub + 1) * L) / (G + 1);
             const bool valid = live && (fine ? sub < L - 1 : true);
-            const uint32_t q = valid ? q_at<K>(m, p) : 0u;
+            const bool le = valid && fast_le<K>(m, p, thr);
             probes += valid;
-            const uint32_t bal = (__ballot_sync(kFull, valid && q <= slot) >> gshift) & ((G == 32) ? kFull : ((1u << G) - 1u));
+            const int c = __popc((__ballot_sync(kFull, le) >> gshift) & gm);
             const int nvalid = fine ? min(L - 1, G) : G;
-            const int c = __popc(bal);
-            const uint32_t q_c = __shfl_sync(kFull, q, grp * G + (c < G ? c : G - 1));
-            const uint32_t q_c1 = __shfl_sync(kFull, q, grp * G + (c > 0 ? c - 1 : 0));
-            const int p_c = fine ? a + 1 + c : a + ((c + 1) * L) / (G + 1);
-            const int p_c1 = fine ? a + c : a + (c * L) / (G + 1);
             if (live) {
-                const int na = c > 0 ? p_c1 : a;
-                const uint32_t nqa = c > 0 ? q_c1 : qa;
-                if (c < nvalid) { b = p_c; qb = q_c; }
+                const int na = c > 0 ? (fine ? a + c : a + (c * L) / (G + 1)) : a;
+                if (c < nvalid) b = fine ? a + 1 + c : a + ((c + 1) * L) / (G + 1);
                 a = na;
-                qa = nqa;
             }
         }
-        if (act && !esc) {
+        // exact check: lane 0 of the group evaluates Q(a), lane 1 Q(a + 1)
+        // (Q(lo) = 0 and Q(hi + 2) = 2^16 need no evaluation), together
+        uint32_t qa, qb;
+        {
+            const int jv = sub == 1 ? a + 1 : a;
+            uint32_t qv = jv <= m.lo ? 0u : kM;
+            if (act && sub < 2 && jv > m.lo && jv <= m.hi + 1) qv = q_at<K>(m, jv);
+            qa = __shfl_sync(kFull, qv, grp * G);
+            qb = __shfl_sync(kFull, qv, grp * G + 1);
+        }
+        bool ok = !act || (qa <= slot && slot < qb);
+        if (__any_sync(kFull, !ok)) {
+            // a near-tie the fast evaluation decided the other way: the exact
+            // G-ary search over [lo, hi + 2) for the streams concerned
+            const bool redo = !ok;
+            int ea = m.lo, eb = m.hi + 2;
+            uint32_t eqa = 0, eqb = kM;
+            while (__any_sync(kFull, redo && eb - ea > 1)) {
+                const bool live = redo && eb - ea > 1;
+                const int L = eb - ea;
+                const bool fine = L - 1 <= G;
+                const int p = fine ? ea + 1 + sub : ea + ((sub + 1) * L) / (G + 1);
+                const bool valid = live && (fine ? sub < L - 1 : true);
+                const uint32_t q = valid ? q_at<K>(m, p) : 0u;
+                const int c = __popc((__ballot_sync(kFull, valid && q <= slot) >> gshift) & gm);
+                const uint32_t q_c = __shfl_sync(kFull, q, grp * G + (c < G ? c : G - 1));
+                const uint32_t q_c1 = __shfl_sync(kFull, q, grp * G + (c > 0 ? c - 1 : 0));
+                const int nvalid = fine ? min(L - 1, G) : G;
+                if (live) {
+                    const int na = c > 0 ? (fine ? ea + c : ea + (c * L) / (G + 1)) : ea;
+                    const uint32_t nqa = c > 0 ? q_c1 : eqa;
+                    if (c < nvalid) { eb = fine ? ea + 1 + c : ea + ((c + 1) * L) / (G + 1); eqb = q_c; }
+                    ea = na;
+                    eqa = nqa;
+                }
+            }
+            if (redo) { a = ea; qa = eqa; qb = eqb; }
+        }
+        if (act) {
             s = a;
+            esc = a == m.hi + 1;
             start = qa;
             freq = qb - qa;
         }
