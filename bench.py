@@ -42,9 +42,22 @@ FP32_LANES_PER_SM = 128
 # Rotating input sets of the timed loop (more than L2 holds).
 ROTATE_SETS = 16
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of
-# the decoder the plan names, from the ncu captures summarised under
-# profiles/; valid for each kernel as captured there (null otherwise).
-DECODE_TRAFFIC_BYTES = {"fgmm_dec_ws_kernel/16/4/16": 10794240}   # "kernel/lanes/cluster/round0": bytes per launch
+# the decoder the plan names, from the ncu capture of the traffic probe
+# (profiles/traffic_roofline_kernels.md); valid for the kernel as captured
+# there (null for any other plan).
+DECODE_TRAFFIC_BYTES = {"fgmm_dec_ws_kernel/16/4/16": 10794496}   # "kernel/lanes/cluster/round0": bytes per launch
+# DRAM bytes per symbol of each roofline row's kernels (K = 3, fp32
+# parameters), from the same capture: a launch's bytes divided by its
+# symbols; rows multiply by their own symbol count. Other parameter types
+# and K were not captured (null).
+TRAFFIC_PER_SYMBOL = {
+    "encode": 44.61,                       # interval + rANS encode + scan + compaction, one latent
+    "fgmm_dec_ws_kernel": 36.60,           # warp-specialised decoder
+    "batch_encode": 40.69,                 # fgmm_batch_enc_kt_kernel + scan + batch compaction
+    "fgmm_batch_dec_kt_kernel": 38.47,     # batch decoder
+    "fgmm_batch_dec_prop_kernel": 38.28,   # batched proposal decoder
+}
+TRAFFIC_SOURCE = "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch of bench.py --traffic-probe"
 
 
 def ops_per_eval(K: int) -> int:
@@ -111,6 +124,8 @@ def parse():
     ap.add_argument("--proposal-only", action="store_true",
                     help="run only the learned-proposal case (for profiling its decoders)")
     ap.add_argument("--proposal-latents", type=int, default=16, help="latents decoded in --proposal-only mode")
+    ap.add_argument("--traffic-probe", action="store_true",
+                    help="launch each roofline kernel twice on small cases, for an ncu capture of DRAM bytes")
     ap.add_argument("--proposal-train-scale", type=float, default=1.0,
                     help="fraction of the training schedule in --proposal-only mode")
     ap.add_argument("--batch-table", action="store_true",
@@ -347,9 +362,13 @@ def batch_case(dev, h, out, name, lats, alu_peak_tops, hbm_gbs, reps=5, max_over
         "encode_msym_s": N / te / 1e3, "decode_msym_s": N / td / 1e3, "ms_encode": te, "ms_decode": td,
         "container_overhead_pct": 100.0 * (16.0 * nw / coded - 1.0),
         "encode_roofline": {"hbm_frac": N * bytes_sym / (te * 1e-3) / 1e9 / hbm_gbs,
-                            "alu_frac": enc_ops / (te * 1e-3) / 1e12 / alu_peak_tops},
+                            "alu_frac": enc_ops / (te * 1e-3) / 1e12 / alu_peak_tops,
+                            "traffic": TRAFFIC_PER_SYMBOL["batch_encode"] * N},
         "decode_roofline": {"alu_frac": dec_ops / (td * 1e-3) / 1e12 / alu_peak_tops,
-                            "hbm_frac": N * bytes_sym / (td * 1e-3) / 1e9 / hbm_gbs},
+                            "hbm_frac": N * bytes_sym / (td * 1e-3) / 1e9 / hbm_gbs,
+                            "traffic": TRAFFIC_PER_SYMBOL["fgmm_batch_dec_kt_kernel"] * N},
+        "traffic_source": TRAFFIC_SOURCE,
+        "ops_per_cdf_eval": ops_per_eval(3), "cdf_evals_per_symbol": evals / N,
     }
     if tab is not None:
         tte, ttd, tbytes = tab
@@ -506,8 +525,10 @@ def proposal_case(dev, h, alu_peak_tops, reps=3, n_train=10_000_000, n_latents=1
     codec.set_mlp_act(_abi.FGMM_MLP_ACT_PL, h)
     b.close()
     evals_plain = res["plain"]["probes_per_symbol"] * N   # the binary search's CDF evaluations
-    for r in res.values():
+    for name, r in res.items():
         r["alu_frac"] = evals_plain * ops_per_eval(3) / (r["ms_decode"] * 1e-3) / 1e12 / alu_peak_tops
+        r["traffic"] = TRAFFIC_PER_SYMBOL["fgmm_batch_dec_kt_kernel" if name == "plain" else
+                                          "fgmm_batch_dec_prop_kernel"] * N
     return {"symbols": N, "latents": len(lats), "streams_per_latent": b.S[0], "segments": b.seg_base[-1],
             "train_triples": ntr, "train_steps": sum(st for st, _ in schedule), "train_batch": 8192,
             "train_s": train_s, "train_final_loss": final_loss, "arms": res,
@@ -563,9 +584,14 @@ def throughput_workloads(dev, alu_peak_tops, hbm_gbs, reps=5):
             "overhead_pct": 100.0 * (coded3 / ideal3 - 1.0), "max_cdf_err": maxerr3, "escapes": nesc3,
             "container_overhead_pct": 100.0 * (16.0 * w3.numel() / coded3 - 1.0),
             "encode_roofline": {"hbm_frac": N3 * bytes_sym / (te3 * 1e-3) / 1e9 / hbm_gbs,
-                                "alu_frac": 2 * N3 * ops_eval / (te3 * 1e-3) / 1e12 / alu_peak_tops},
+                                "alu_frac": 2 * N3 * ops_eval / (te3 * 1e-3) / 1e12 / alu_peak_tops,
+                                "traffic": (TRAFFIC_PER_SYMBOL["encode"] * N3) if (K3 == 3 and not bf16) else None},
             "decode_roofline": {"alu_frac": evals3 * ops_eval / (td3 * 1e-3) / 1e12 / alu_peak_tops,
-                                "cdf_evals_per_symbol": evals3 / N3},
+                                "cdf_evals_per_symbol": evals3 / N3,
+                                "traffic": (TRAFFIC_PER_SYMBOL["fgmm_dec_ws_kernel"] * N3)
+                                if (K3 == 3 and not bf16 and codec.decode_plan(S3, h=h)["kernel"] == "fgmm_dec_ws_kernel")
+                                else None},
+            "traffic_source": TRAFFIC_SOURCE,
         }
         del dp3, ds3, w3, o3, out3
     # the autotuner's trade-off on the K = 3 fp32 latent: a looser bound on
@@ -1151,6 +1177,58 @@ def run_proposal_only(args):
     print(json.dumps({f"proposal_{args.proposal_latents}x320x64x96_sigma64": res}))
 
 
+def run_traffic_probe(args):
+    """Each kernel that has a roofline line in the benchmark, launched once
+    after one warm-up, for an ncu capture of DRAM bytes per launch: the
+    192x32x48 latent at 1024 streams (interval, rANS encode, scan,
+    compaction; decoder), the 320x64x96 K = 3 latent at the autotuned stream
+    count (the same kernels), the first 8 latents of the 64-latent batch
+    (batch encode, scan, compaction; batch decode), and 2 latents of
+    320x64x96 with scales up to 64 through the batched proposal decoder (a
+    zero network). Prints the symbols each case codes."""
+    import torch
+    from paper_2509_18815_gb300 import build, codec, synth
+    build.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    h = codec.handle(dev)
+    cases = {}
+    for name, (C, H, W, seed, S) in {"latent_192x32x48": (192, 32, 48, 1002, 1024),
+                                     "latent_320x64x96": (320, 64, 96, 1003, None)}.items():
+        lat = synth.make_latent(C, H, W, 3, seed)
+        dp = torch.from_numpy(lat.params).to(dev)
+        ds = torch.from_numpy(lat.symbols).to(dev)
+        S = S or codec.autotune([lat.N], h=h)[0]
+        for _ in range(2):   # warm-up, then the captured launches
+            words, off = codec.encode(dp, ds, S, h=h)
+            codec.decode(dp, words, off, S, h=h)
+        cases[name] = {"symbols": lat.N, "S": S, "decoder": codec.decode_plan(S, h=h)["kernel"]}
+    shapes = synth.batch_shapes(64, seed=1004)[:8]
+    lats = [synth.make_latent(C, H, W, 3, 1004 + i) for i, (C, H, W) in enumerate(shapes)]
+    b = codec.Batch([torch.from_numpy(l.params).to(dev) for l in lats],
+                    [torch.from_numpy(l.symbols).to(dev) for l in lats], h=h)
+    for _ in range(2):
+        b.encode()
+        b.decode()
+    cases["batch8"] = {"symbols": sum(l.N for l in lats), "segments": b.seg_base[-1]}
+    b.close()
+    lats = [synth.make_latent(320, 64, 96, 3, seed=1105 + i, sigma_max=64.0) for i in range(2)]
+    b = codec.Batch([torch.from_numpy(l.params).to(dev) for l in lats],
+                    [torch.from_numpy(l.symbols).to(dev) for l in lats], h=h)
+    b.encode()
+    P = codec.mlp_pack(torch.zeros(_mlp_params(), dtype=torch.float32, device=dev), h=h)
+    for _ in range(2):
+        b.decode_proposal(P)
+    cases["proposal2_sigma64"] = {"symbols": sum(l.N for l in lats), "segments": b.seg_base[-1]}
+    b.close()
+    print(json.dumps({"traffic_probe": cases}))
+
+
+def _mlp_params():
+    from paper_2509_18815_gb300 import _abi
+    return _abi.FGMM_MLP_PARAMS
+
+
 def main():
     args = parse()
     if args.batch_only > 0:
@@ -1159,6 +1237,8 @@ def main():
         run_gsm_only(args)
     elif args.proposal_only:
         run_proposal_only(args)
+    elif args.traffic_probe:
+        run_traffic_probe(args)
     elif args.impl == "reference":
         run_reference(args)
     else:
