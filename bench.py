@@ -444,8 +444,18 @@ def ckbd_case(dev, h, flush, reps):
     first, second = codec.ckbd_encode(dp, dy, shape, Sa, Sn, h=h)
     y = codec.ckbd_decode(dp, first, second, shape, Sa, Sn, h=h)
     assert torch.equal(y, dy)
-    te = _events_ms(lambda: codec.ckbd_encode(dp, dy, shape, Sa, Sn, h=h), reps, flush)
-    td = _events_ms(lambda: codec.ckbd_decode(dp, first, second, shape, Sa, Sn, h=h, sync=False), reps, flush)
+    te_host = _events_ms(lambda: codec.ckbd_encode(dp, dy, shape, Sa, Sn, h=h), reps, flush)
+    td_host = _events_ms(lambda: codec.ckbd_decode(dp, first, second, shape, Sa, Sn, h=h, sync=False), reps, flush)
+    # the same sequences captured once into CUDA graphs and replayed
+    gr = codec.CkbdGraphs(dp, shape, Sa, Sn, h=h)
+    gr.capture_encode(dy)
+    (wa, oa, ta), (wn, on, tn) = gr.encode()
+    assert torch.equal(wa[: int(ta.item())], first[0]) and torch.equal(wn[: int(tn.item())], second[0])
+    gr.capture_decode(first, second)
+    assert torch.equal(gr.decode(), dy)
+    te = _events_ms(lambda: gr.encode(sync=False), reps, flush)
+    td = _events_ms(lambda: gr.decode(sync=False), reps, flush)
+    h.sync()
     w1, o1 = codec.encode(dp, dy, 1024, h=h)
     out = torch.empty(N, dtype=torch.int32, device=dev)
     td1 = _events_ms(lambda: codec.decode(dp, w1, o1, 1024, h=h, out=out, sync=False), reps, flush)
@@ -457,9 +467,11 @@ def ckbd_case(dev, h, flush, reps):
     bits2 = 16.0 * (first[0].numel() + second[0].numel())
     return {"symbols": N, "S_per_pass": [Sa, Sn], "ms_encode": te, "ms_decode": td,
             "encode_msym_s": N / te / 1e3, "decode_msym_s": N / td / 1e3, "one_pass_ms_decode": td1,
+            "host_launched": {"ms_encode": te_host, "ms_decode": td_host},
             "ideal_bits_per_symbol_one_pass": ideal1 / N, "ideal_bits_per_symbol_two_pass": (ia + inn) / N,
             "coded_bits_per_symbol_two_pass": bits2 / N,
-            "note": "host-launched sequence of split, two coder passes, context and merges (no graph)"}
+            "note": "split, two coder passes, context and merges replayed from one CUDA graph per direction "
+                    "(host_launched: the same calls launched one by one)"}
 
 
 def proposal_case(dev, h, alu_peak_tops, reps=3, n_train=10_000_000, n_latents=16, train_scale=1.0):

@@ -414,6 +414,64 @@ def ckbd_decode(params, first, second, shape, Sa: int, Sn: int, h: Handle | None
     return y
 
 
+class CkbdGraphs:
+    """Checkerboard two-pass coding of one latent shape replayed from CUDA
+    graphs. The encode sequence (anchor/non-anchor split, the stand-in
+    context, the two passes' encodes) and the decode sequence (split, pass 1
+    decode, anchor merge, context, pass 2 decode, merge) are each captured
+    once with fixed buffers; every node of a replay is a library kernel, and
+    the graphs remove the host's per-launch work and the gaps between
+    kernels. params: [3, K, C H W] on the GPU; shape (C, H, W); Sa, Sn: the
+    passes' stream counts. capture_encode(y) / encode() fill enc_first and
+    enc_second ((words, offsets, total) of each pass, untrimmed);
+    capture_decode(first, second) / decode() decode the given (words,
+    offsets) pairs into `y`."""
+
+    def __init__(self, params, shape, Sa: int, Sn: int, h: Handle | None = None):
+        self.h = h or handle(params.device)
+        self.params = params.contiguous()
+        self.shape = tuple(shape)
+        self.Sa, self.Sn = Sa, Sn
+        self.g_enc = self.g_dec = None
+
+    def _encode_seq(self, y):
+        pa, ya, _, yn = ckbd_split(self.params, y, self.shape, self.h)
+        pn = ckbd_context(self.params, y, self.shape, h=self.h)
+        return (encode(pa, ya, self.Sa, self.h, sync=False), encode(pn, yn, self.Sn, self.h, sync=False))
+
+    def _decode_seq(self):
+        return ckbd_decode(self.params, self._first, self._second, self.shape, self.Sa, self.Sn, self.h, sync=False)
+
+    def capture_encode(self, y):
+        self._y_in = y.to(torch.int32).contiguous()
+        self._encode_seq(self._y_in)          # grows the handle's workspace outside the capture
+        self.h.sync()
+        self.g_enc = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.g_enc, capture_error_mode="thread_local"):
+            self.enc_first, self.enc_second = self._encode_seq(self._y_in)
+
+    def encode(self, sync: bool = True):
+        self.g_enc.replay()
+        if sync:
+            self.h.sync()
+        return self.enc_first, self.enc_second
+
+    def capture_decode(self, first, second):
+        self._first = (first[0].contiguous(), first[1].to(torch.int64).contiguous())
+        self._second = (second[0].contiguous(), second[1].to(torch.int64).contiguous())
+        self._decode_seq()
+        self.h.sync()
+        self.g_dec = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.g_dec, capture_error_mode="thread_local"):
+            self.y = self._decode_seq()
+
+    def decode(self, sync: bool = True):
+        self.g_dec.replay()
+        if sync:
+            self.h.sync()
+        return self.y
+
+
 def rate_audit(params, symbols, h: Handle | None = None):
     """(ideal_bits, coded_bits, max_cdf_err, n_escape) computed in FP64 on the GPU."""
     h = h or handle(params.device)

@@ -76,8 +76,12 @@ __device__ __forceinline__ float recip(float d)
     return __fmaf_rn(y, e, y);
 }
 
-// 1/s for a floored scale s >= 0.11 (any finite value above).
-__device__ __forceinline__ float recip_scale(float s) { return s < 0x1p125f ? recip(s) : __frcp_rn(s); }
+// 1/s for a floored scale s >= 0.11 (any finite value above): the inline
+// reciprocal below 2^125; above, where 1/s may be subnormal, the correctly
+// rounded division, kept out of line so that the common path carries none
+// of its code.
+static __device__ __noinline__ float recip_scale_slow(float s) { return __frcp_rn(s); }
+__device__ __forceinline__ float recip_scale(float s) { return s < 0x1p125f ? recip(s) : recip_scale_slow(s); }
 
 // Phi-hat(z): A&S 26.2.17, Phi(x) ~ 1 - Z(x) sum_i b_i t^i, t = 1/(1+px),
 // x = |z|, mirrored for z < 0. p = 0.2316419 and b_1..b_5 are the handbook's;

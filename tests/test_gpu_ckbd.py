@@ -94,3 +94,37 @@ def test_errors_are_reported():
                                   None) == FGMM_ERR_INVALID_ARG
     assert _abi.fgmm_ckbd_merge(h.ptr, -1, 4, 4, None, None, None, None) == FGMM_ERR_INVALID_ARG
     assert _abi.fgmm_ckbd_anchors(3, 5, 5) == 39
+
+
+@pytest.mark.parametrize("bf16", [False, True])
+def test_two_pass_from_cuda_graphs(bf16):
+    """The two-pass encode and decode captured into CUDA graphs replay to
+    the oracle's streams and the exact symbols, twice in a row, and again
+    after the input buffers were overwritten with a second latent."""
+    codec = _codec()
+    shape, Sa, Sn = (8, 16, 24), 64, 96
+    lat = synth.make_ckbd_latent(*shape, 3, seed=961)
+    dp, dy = dev_params(lat.params, bf16), dev_i32(lat.symbols)
+    po = oracle_params(lat.params, bf16)
+    gr = codec.CkbdGraphs(dp, shape, Sa, Sn)
+    gr.capture_encode(dy)
+    (wa_o, oa_o), (wn_o, on_o) = oracle.ckbd_encode(po, lat.symbols, shape, Sa, Sn)
+    for _ in range(2):
+        (wa, oa, ta), (wn, on, tn) = gr.encode()
+        np.testing.assert_array_equal(host_u16(wa[: int(ta.item())]), wa_o)
+        np.testing.assert_array_equal(oa.cpu().numpy(), oa_o)
+        np.testing.assert_array_equal(host_u16(wn[: int(tn.item())]), wn_o)
+        np.testing.assert_array_equal(on.cpu().numpy(), on_o)
+    gr.capture_decode((wa[: int(ta.item())].clone(), oa.clone()), (wn[: int(tn.item())].clone(), on.clone()))
+    for _ in range(2):
+        gr.y.fill_(-3)
+        np.testing.assert_array_equal(gr.decode().cpu().numpy(), lat.symbols)
+    # new symbols and parameters in the captured input buffers: the encode
+    # replay codes the new latent
+    lat2 = synth.make_ckbd_latent(*shape, 3, seed=962)
+    gr.params.copy_(dev_params(lat2.params, bf16))
+    gr._y_in.copy_(dev_i32(lat2.symbols))
+    (wa, oa, ta), (wn, on, tn) = gr.encode()
+    (wa_o, _), (wn_o, _) = oracle.ckbd_encode(oracle_params(lat2.params, bf16), lat2.symbols, shape, Sa, Sn)
+    np.testing.assert_array_equal(host_u16(wa[: int(ta.item())]), wa_o)
+    np.testing.assert_array_equal(host_u16(wn[: int(tn.item())]), wn_o)

@@ -86,6 +86,20 @@ def test_extreme_params():
     _check_latent(p, lat.symbols, 64)
 
 
+def test_scales_at_and_beyond_2_to_125():
+    """Scales of 2^125 and more take the correctly rounded reciprocal (the
+    inverse may be subnormal); with means up to the float range the
+    frequencies and the stream still match the oracle bit for bit."""
+    lat = synth.make_latent(4, 16, 16, 3, seed=303)
+    p = lat.params.copy()
+    big = np.array([2.0 ** 125, 2.0 ** 126, 1e38, 3.4e38], dtype=np.float32)
+    p[2, 1, ::3] = np.resize(big, p[2, 1, ::3].shape)
+    p[2, 2, 1::7] = 3.4e38
+    p[1, 1, ::6] = 1e38
+    p[1, 2, 2::9] = -3e38
+    _check_latent(p, lat.symbols, 64)
+
+
 def test_large_scales_workload_distribution():
     lat = synth.make_latent(32, 32, 32, 3, seed=302, sigma_max=64.0)
     _check_latent(lat.params, lat.symbols, 512)
