@@ -52,11 +52,12 @@ __device__ __forceinline__ bool mix_from_params(const RawParams<K>& r, Mix<K>& m
     }
     lo_f = fminf(fmaxf(floorf(lo_f), -(float)kYmax), (float)kYmax);
     hi_f = fminf(fmaxf(ceilf(hi_f), -(float)kYmax), (float)kYmax);
-    int lo = (int)lo_f, hi = (int)hi_f;
-    if (lo > hi) { int t = lo; lo = hi; hi = t; }
-    m.lo = lo;
-    m.hi = hi;
-    m.tp = (float)(int)(kM - (uint32_t)(hi - lo + 1) - 1u);
+    // lo <= hi always: floor(a) <= ceil(b) for a <= b (a, b the extreme
+    // window ends, both finite here), and clamping keeps the order, so the
+    // coded definition's swap of lo and hi never applies
+    m.lo = (int)lo_f;
+    m.hi = (int)hi_f;
+    m.tp = (float)(int)(kM - (uint32_t)(m.hi - m.lo + 1) - 1u);
     return ok;
 }
 
