@@ -445,7 +445,9 @@ fgmm_status fgmm_set_option(fgmm_handle *h, int32_t option, int64_t value);
  *   FGMM_DEC_COOP  G = 2..16 lanes per stream, G-ary search (clusters of
  *                  up to 4 CTAs for G = 2, 4; one CTA for G = 8, 16);
  *   FGMM_DEC_WIDE  32 lanes per stream, 32-point search, one CTA per segment;
- *   FGMM_DEC_WS    G = 8, 16 or 32 with a cluster of 2, 4 or 8 CTAs per
+ *   FGMM_DEC_WS    (streams of fewer than 2^24 steps, ceil(N / S) < 2^24;
+ *                  fgmm_decode runs FGMM_DEC_LANE for longer ones)
+ *                  G = 8, 16 or 32 with a cluster of 2, 4 or 8 CTAs per
  *                  segment: producer warps evaluate a 32-point first round
  *                  two steps ahead, consumer warps (32 / G streams each,
  *                  G lanes per stream) search inside the bracket.

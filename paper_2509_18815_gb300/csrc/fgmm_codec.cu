@@ -639,6 +639,12 @@ fgmm_status fgmm_decode(fgmm_handle* h, const fgmm_latent* lat, const uint16_t* 
     int lanes = 1, cluster = 1, round0 = 0, kernel = 0;
     decode_resolve(a.nseg, h->num_sms, h->decode_lanes, h->decode_cluster, h->decode_round0, h->phi, &lanes,
                    &cluster, &round0, &kernel);
+    if (kernel == FGMM_DEC_WS && a.T >= ((int64_t)1 << 24)) {   // streams beyond the warp-specialised kernel's range
+        lanes = 1;
+        cluster = 1;
+        round0 = 0;
+        kernel = FGMM_DEC_LANE;
+    }
     a.r0 = round0 > 0 ? round0 : 32;
     a.phi = h->phi;
     a.silent = h->test_silent_stream;

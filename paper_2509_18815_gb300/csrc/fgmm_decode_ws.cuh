@@ -93,20 +93,22 @@ __device__ __forceinline__ uint32_t exchange(uint32_t* xflag, uint32_t* abort_fl
 }
 
 // Refill of one sub-step: M holds the segment's refill bits (stream q at
-// bit q); streams read in rank order from the words just below ptr.
+// bit q); streams read in rank order from the words just below rp, the read
+// position relative to the segment's first word wseg[0] (32-bit: a segment
+// holds fewer than 2^31 words, see launch_ws).
 __device__ __forceinline__ void ws_refill(uint32_t& x, bool need, uint32_t M, uint32_t below,
-                                          const uint16_t* wsrc, int64_t wbase, int64_t& ptr, int64_t beg, bool& bad)
+                                          const uint16_t* wseg, int32_t& rp, bool& bad)
 {
     if (M) {
         const int cnt = __popc(M);
         if (need) {
-            const int64_t idx = ptr - cnt + __popc(M & below);
+            const int32_t idx = rp - cnt + __popc(M & below);
             uint32_t v = 0;
-            if (idx >= beg) v = wsrc[idx - wbase];
+            if (idx >= 0) v = wseg[idx];
             else bad = true;
             x = (x << 16) | v;
         }
-        ptr -= cnt;
+        rp -= cnt;
     }
 }
 
@@ -164,8 +166,7 @@ __global__ void __launch_bounds__(32 * (32 / CL / SPW + 32 / CL * R0 / 32))
     }
     const int64_t seg_len = end - beg;
     const bool staged = seg_len <= kWordCap;
-    const uint16_t* wsrc = staged ? wsm : words;
-    const int64_t wbase = staged ? beg : 0;
+    const uint16_t* wseg = staged ? wsm : words + beg;   // the segment's words
     const int64_t nbase = g * 32 + rank * SPC;
 
     // producer: prepare step u of this warp's stream into pre[u % kPre]
@@ -232,8 +233,9 @@ __global__ void __launch_bounds__(32 * (32 / CL / SPW + 32 / CL * R0 / 32))
         for (int64_t u = 0; u < kLead && u < T_steps; ++u) produce(u);
     seg_sync<CL>();       // flags initialised in every CTA before any exchange
 
-    uint32_t x = (uint32_t)wsrc[end - 64 + 2 * ws - wbase] | ((uint32_t)wsrc[end - 63 + 2 * ws - wbase] << 16);
-    int64_t ptr = end - 64;
+    int32_t rp = (int32_t)(seg_len - 64);   // read position in the segment
+    uint32_t x = (uint32_t)wseg[rp + 2 * ws] | ((uint32_t)wseg[rp + 2 * ws + 1] << 16);
+    int64_t n = g * 32 + ws;                  // this stream's symbol at step t (consumers)
     bool bad = false;
     int decoded = 0;
     uint32_t e = 0;       // exchange number (the same in every stream)
@@ -252,7 +254,6 @@ __global__ void __launch_bounds__(32 * (32 / CL / SPW + 32 / CL * R0 / 32))
             if (t + kLead < T_steps) produce(t + kLead);
             cp_async_wait<1>();   // step t + kLead + 1 resident for the next iteration
         } else {
-            const int64_t n = t * (int64_t)S + g * 32 + ws;
             const bool act = n < N;
             int32_t s = 0;
             bool esc = false;
@@ -333,27 +334,28 @@ __global__ void __launch_bounds__(32 * (32 / CL / SPW + 32 / CL * R0 / 32))
             if (t + 1 < T_steps) fetch(t + 1, m, q0);
             const uint32_t f = exchange_wait<CL>(xflag, abort_flag, e++, lane, err);
             const uint32_t M = __ballot_sync(kFull, f & 1u), E = __ballot_sync(kFull, f & 2u);
-            ws_refill(x, need, M, below, wsrc, wbase, ptr, beg, bad);
+            ws_refill(x, need, M, below, wseg, rp, bad);
             if (E) {   // the same in every stream of the segment
                 uint32_t hi16 = 0, lo16 = 0;
                 if (esc) { hi16 = x & 0xffffu; x >>= 16; }
                 const bool n2 = esc && x < kL;
                 const uint32_t M2 =
                     __ballot_sync(kFull, exchange<CL>(xflag, abort_flag, e++, ws, j, lane, n2 ? 1u : 0u, err, posts) & 1u);
-                ws_refill(x, n2, M2, below, wsrc, wbase, ptr, beg, bad);
+                ws_refill(x, n2, M2, below, wseg, rp, bad);
                 if (esc) { lo16 = x & 0xffffu; x >>= 16; }
                 const bool n3 = esc && x < kL;
                 const uint32_t M3 =
                     __ballot_sync(kFull, exchange<CL>(xflag, abort_flag, e++, ws, j, lane, n3 ? 1u : 0u, err, posts) & 1u);
-                ws_refill(x, n3, M3, below, wsrc, wbase, ptr, beg, bad);
+                ws_refill(x, n3, M3, below, wseg, rp, bad);
                 if (esc) s = (int32_t)((hi16 << 16) | lo16);
             }
             if (act && j == 0) out[n] = s;
+            n += S;
         }
         __syncthreads();   // producers' round for step t + 2 visible; slots read
     }
     cp_async_wait<0>();
-    const bool fail = !producer && (bad || x != kL || ptr != beg);
+    const bool fail = !producer && (bad || x != kL || rp != 0);
     if (__syncthreads_or(fail) && tid == 0) set_error(err, kErrCorrupt);
     if (__syncthreads_or(badp) && tid == 0) set_error(err, kErrBadParams);
     if (stats) {
@@ -378,7 +380,9 @@ cudaError_t launch_ws(const DecodeArgs& a, cudaStream_t st)
     constexpr int NT = 32 * (SPC / SPW + SPC * R0 / 32);
     const size_t smem = sizeof(PreStep<K>) * kPre * SPC + sizeof(T) * kRing * 3 * K * SPC + sizeof(uint32_t) * 68 +
                         sizeof(uint16_t) * kWordCap;
-    if (a.T >= ((int64_t)1 << 28)) return cudaErrorInvalidValue;   // exchange numbers stay below 2^30
+    // exchange numbers stay below 2^30, and a segment (at most 96 T + 64
+    // words) below 2^31 words for the 32-bit read position
+    if (a.T >= ((int64_t)1 << 24)) return cudaErrorInvalidValue;
     auto kern = fgmm_dec_ws_kernel<K, T, CL, SPW, R0>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
