@@ -431,8 +431,9 @@ def ckbd_case(dev, h, flush, reps):
     """Checkerboard two-pass coding (anchors, then the non-anchors with the
     stand-in context's parameters) of the 192x32x48 K = 3 latent with 512
     streams per pass (288 steps each, as the one-pass headline at 1024):
-    time per direction including split, context and merge, and the rate of
-    both passes against one pass with the hyperprior's parameters."""
+    time per direction including split, context and merge (decode: the
+    fused two-pass launch and, for comparison, the separate calls), and the
+    rate of both passes against one pass with the hyperprior's parameters."""
     import torch
     from paper_2509_18815_gb300 import codec, synth
     shape = (192, 32, 48)
@@ -456,6 +457,19 @@ def ckbd_case(dev, h, flush, reps):
     te = _events_ms(lambda: gr.encode(sync=False), reps, flush)
     td = _events_ms(lambda: gr.decode(sync=False), reps, flush)
     h.sync()
+    fused = codec.ckbd_decode_fused(3, torch.float32, shape, Sa, Sn, h=h)
+    # the same decode as its separate calls (split, pass 1, merge, context,
+    # pass 2, merge), captured into a graph too
+    y_s = codec.ckbd_decode_steps(dp, first, second, shape, Sa, Sn, h=h)
+    assert torch.equal(y_s, dy)
+    g_s = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g_s, capture_error_mode="thread_local"):
+        y_s = codec.ckbd_decode_steps(dp, first, second, shape, Sa, Sn, h=h, sync=False)
+    g_s.replay()
+    h.sync()
+    assert torch.equal(y_s, dy)
+    td_steps = _events_ms(lambda: g_s.replay(), reps, flush)
+    h.sync()
     w1, o1 = codec.encode(dp, dy, 1024, h=h)
     out = torch.empty(N, dtype=torch.int32, device=dev)
     td1 = _events_ms(lambda: codec.decode(dp, w1, o1, 1024, h=h, out=out, sync=False), reps, flush)
@@ -467,11 +481,14 @@ def ckbd_case(dev, h, flush, reps):
     bits2 = 16.0 * (first[0].numel() + second[0].numel())
     return {"symbols": N, "S_per_pass": [Sa, Sn], "ms_encode": te, "ms_decode": td,
             "encode_msym_s": N / te / 1e3, "decode_msym_s": N / td / 1e3, "one_pass_ms_decode": td1,
+            "decode_fused": fused, "ms_decode_separate_calls": td_steps,
             "host_launched": {"ms_encode": te_host, "ms_decode": td_host},
             "ideal_bits_per_symbol_one_pass": ideal1 / N, "ideal_bits_per_symbol_two_pass": (ia + inn) / N,
             "coded_bits_per_symbol_two_pass": bits2 / N,
-            "note": "split, two coder passes, context and merges replayed from one CUDA graph per direction "
-                    "(host_launched: the same calls launched one by one)"}
+            "note": "each direction replayed from one CUDA graph: encode = split, context, two coder passes; "
+                    "decode = fgmm_ckbd_decode (split, both passes in one launch with the context applied as "
+                    "pass 2 loads its parameters, merge); ms_decode_separate_calls: split, pass 1, merge, "
+                    "context, pass 2, merge as separate launches (host_launched: the calls launched one by one)"}
 
 
 def proposal_case(dev, h, alu_peak_tops, reps=3, n_train=10_000_000, n_latents=16, train_scale=1.0):

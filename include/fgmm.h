@@ -18,7 +18,9 @@
  *  - A handle owns reusable device workspace (grown with cudaMalloc on
  *    demand, before any launch of the call) and a sticky device error word.
  *    Use one handle per stream; calls on one handle must not overlap on the
- *    device.
+ *    device. A CUDA graph that captured a call holds the workspace's
+ *    address: a later call on the same handle that needs more workspace
+ *    frees it, and the graph must not be replayed after that.
  *  - Host-side argument errors are returned immediately; data-dependent
  *    errors found by a kernel (bad parameters, corrupt stream, capacity) are
  *    recorded in the device error word and returned by fgmm_sync_status().
@@ -258,6 +260,38 @@ fgmm_status fgmm_ckbd_merge(fgmm_handle *h, int64_t C, int64_t H, int64_t W, con
  * float(ctx)), mu_k), sigma'_k = 0.75 sigma_k (FP32, round to nearest). */
 fgmm_status fgmm_ckbd_context(fgmm_handle *h, const fgmm_latent *lat, int64_t C, int64_t H, int64_t W,
                               const int32_t *y, float *params_n, void *stream);
+
+/* The whole two-pass decode in one call: from the hyperprior parameters lat
+ * (N = C H W) and the two passes' streams (words_a / offsets_a of the
+ * anchors coded with Sa streams from the anchors' hyperprior parameters;
+ * words_n / offsets_n of the non-anchors coded with Sn streams from
+ * fgmm_ckbd_context's parameters; the layout of fgmm_decode), writes the
+ * latent's symbols to y (device int32 [N]). The same symbols as fgmm_ckbd_split,
+ * fgmm_decode of the anchors, fgmm_ckbd_merge, fgmm_ckbd_context,
+ * fgmm_decode of the non-anchors and fgmm_ckbd_merge, which it runs when it
+ * cannot do better. It does better for fp32 parameters and the A&S
+ * approximation when the automatic decoder plan of the Sa / 32 + Sn / 32
+ * segments is the warp-specialised decoder with 16 lanes per stream,
+ * clusters of 4 and a 16-point first round, every cluster fits on the
+ * device at once, each pass has fewer than 2^24 steps, C H W < 2^31, and
+ * no decoder option or test hook is set (fgmm_ckbd_decode_plan): then one
+ * launch decodes both passes, the non-anchors' streams starting as soon as
+ * the anchors next to their symbols are decoded (each waiting for them is
+ * bounded: FGMM_ERR_TIMEOUT from fgmm_sync_status if it runs out), with
+ * the context applied as their parameters are loaded. Uses the handle's
+ * workspace (anchor parameters, non-anchor parameters, the two passes'
+ * symbols). Stream errors are reported as by fgmm_decode. */
+fgmm_status fgmm_ckbd_decode(fgmm_handle *h, const fgmm_latent *lat, int64_t C, int64_t H, int64_t W,
+                             const uint16_t *words_a, int64_t n_words_a, const int64_t *offsets_a, int32_t Sa,
+                             const uint16_t *words_n, int64_t n_words_n, const int64_t *offsets_n, int32_t Sn,
+                             int32_t *y, void *stream);
+
+/* *fused = 1 if fgmm_ckbd_decode on this handle decodes a K-component
+ * latent of parameter type dtype and shape C x H x W, coded with Sa and Sn
+ * streams, in one launch, else 0 (host-only; may query the device's
+ * occupancy once per K). */
+fgmm_status fgmm_ckbd_decode_plan(fgmm_handle *h, int32_t K, int32_t dtype, int64_t C, int64_t H, int64_t W,
+                                  int32_t Sa, int32_t Sn, int32_t *fused);
 
 /* ---- FP64 rate audit (Sec. V "no approximation" reference) --------------
  * For a latent and its symbols, computes in FP64 on the GPU:

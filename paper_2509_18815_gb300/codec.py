@@ -400,8 +400,29 @@ def ckbd_encode(params, y, shape, Sa: int, Sn: int, h: Handle | None = None):
     return encode(pa, ya, Sa, h), encode(pn, yn, Sn, h)
 
 
-def ckbd_decode(params, first, second, shape, Sa: int, Sn: int, h: Handle | None = None, sync: bool = True):
-    """Two-pass decode: the anchors, the context from them, the non-anchors."""
+def ckbd_decode(params, first, second, shape, Sa: int, Sn: int, h: Handle | None = None, sync: bool = True,
+                out=None):
+    """Two-pass decode (fgmm_ckbd_decode): the anchors, the context from
+    them, the non-anchors; one fused launch where the library can."""
+    h = h or handle(params.device)
+    lat = latent(params)
+    C, H, W = shape
+    (wa, oa), (wn, on) = first, second
+    oa, on = oa.to(torch.int64).contiguous(), on.to(torch.int64).contiguous()
+    if out is None:
+        out = torch.empty(C * H * W, dtype=torch.int32, device=params.device)
+    h.check(_abi.fgmm_ckbd_decode(h.ptr, ctypes.byref(lat), C, H, W, _ptr(wa), wa.numel(), _ptr(oa), Sa,
+                                  _ptr(wn), wn.numel(), _ptr(on), Sn, _ptr(out), _stream()))
+    if sync:
+        h.sync()
+    return out
+
+
+def ckbd_decode_steps(params, first, second, shape, Sa: int, Sn: int, h: Handle | None = None,
+                      sync: bool = True):
+    """The two-pass decode as its separate library calls, one after the
+    other: split, pass-1 decode, anchor merge, context, pass-2 decode,
+    merge (the same symbols as ckbd_decode)."""
     h = h or handle(params.device)
     pa, _, _, _ = ckbd_split(params, None, shape, h)
     ya = decode(pa, first[0], first[1], Sa, h, sync=False)
@@ -414,25 +435,39 @@ def ckbd_decode(params, first, second, shape, Sa: int, Sn: int, h: Handle | None
     return y
 
 
+def ckbd_decode_fused(K: int, dtype, shape, Sa: int, Sn: int, h: Handle | None = None) -> bool:
+    """Whether ckbd_decode decodes both passes in one launch for this case."""
+    h = h or handle()
+    C, H, W = shape
+    dt = _abi.FGMM_DTYPE_BF16 if dtype == torch.bfloat16 else _abi.FGMM_DTYPE_F32
+    out = ctypes.c_int32(-1)
+    h.check(_abi.fgmm_ckbd_decode_plan(h.ptr, K, dt, C, H, W, Sa, Sn, ctypes.byref(out)))
+    return bool(out.value)
+
+
 class CkbdGraphs:
     """Checkerboard two-pass coding of one latent shape replayed from CUDA
     graphs. The encode sequence (anchor/non-anchor split, the stand-in
-    context, the two passes' encodes) and the decode sequence (split, pass 1
-    decode, anchor merge, context, pass 2 decode, merge) are each captured
-    once with fixed buffers; every node of a replay is a library kernel, and
-    the graphs remove the host's per-launch work and the gaps between
-    kernels. params: [3, K, C H W] on the GPU; shape (C, H, W); Sa, Sn: the
-    passes' stream counts. capture_encode(y) / encode() fill enc_first and
-    enc_second ((words, offsets, total) of each pass, untrimmed);
-    capture_decode(first, second) / decode() decode the given (words,
-    offsets) pairs into `y`."""
+    context, the two passes' encodes) and the decode sequence
+    (fgmm_ckbd_decode) are each captured once with fixed buffers; every node
+    of a replay is a library kernel, and the graphs remove the host's
+    per-launch work and the gaps between kernels. params: [3, K, C H W] on
+    the GPU; shape (C, H, W); Sa, Sn: the passes' stream counts.
+    capture_encode(y) / encode() fill enc_first and enc_second ((words,
+    offsets, total) of each pass, untrimmed); capture_decode(first, second)
+    / decode() decode the given (words, offsets) pairs into `y`. The graphs
+    hold the handle's workspace, so the class uses a handle of its own
+    unless one is given (a call that grows a given handle's workspace after
+    a capture invalidates the graphs); every capture first runs each
+    sequence it holds once, so that both graphs see the final workspace."""
 
     def __init__(self, params, shape, Sa: int, Sn: int, h: Handle | None = None):
-        self.h = h or handle(params.device)
+        self.h = h or Handle(params.device)
         self.params = params.contiguous()
         self.shape = tuple(shape)
         self.Sa, self.Sn = Sa, Sn
         self.g_enc = self.g_dec = None
+        self._y_in = self._first = None
 
     def _encode_seq(self, y):
         pa, ya, _, yn = ckbd_split(self.params, y, self.shape, self.h)
@@ -442,13 +477,26 @@ class CkbdGraphs:
     def _decode_seq(self):
         return ckbd_decode(self.params, self._first, self._second, self.shape, self.Sa, self.Sn, self.h, sync=False)
 
+    def _capture(self):
+        # every sequence once outside the captures (grows the workspace), then
+        # every graph again, so that none holds a workspace that was freed
+        if self._y_in is not None:
+            self._encode_seq(self._y_in)
+        if self._first is not None:
+            self._decode_seq()
+        self.h.sync()
+        if self._y_in is not None:
+            self.g_enc = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(self.g_enc, capture_error_mode="thread_local"):
+                self.enc_first, self.enc_second = self._encode_seq(self._y_in)
+        if self._first is not None:
+            self.g_dec = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(self.g_dec, capture_error_mode="thread_local"):
+                self.y = self._decode_seq()
+
     def capture_encode(self, y):
         self._y_in = y.to(torch.int32).contiguous()
-        self._encode_seq(self._y_in)          # grows the handle's workspace outside the capture
-        self.h.sync()
-        self.g_enc = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(self.g_enc, capture_error_mode="thread_local"):
-            self.enc_first, self.enc_second = self._encode_seq(self._y_in)
+        self._capture()
 
     def encode(self, sync: bool = True):
         self.g_enc.replay()
@@ -459,11 +507,7 @@ class CkbdGraphs:
     def capture_decode(self, first, second):
         self._first = (first[0].contiguous(), first[1].to(torch.int64).contiguous())
         self._second = (second[0].contiguous(), second[1].to(torch.int64).contiguous())
-        self._decode_seq()
-        self.h.sync()
-        self.g_dec = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(self.g_dec, capture_error_mode="thread_local"):
-            self.y = self._decode_seq()
+        self._capture()
 
     def decode(self, sync: bool = True):
         self.g_dec.replay()

@@ -133,9 +133,56 @@ fgmm_status check_geom(fgmm_handle* h, int64_t C, int64_t H, int64_t W)
     return FGMM_OK;
 }
 
+// Whether fgmm_ckbd_decode runs both passes in one launch: fp32
+// parameters, the A&S approximation, no decoder option or test hook, the
+// automatic plan of the combined segments is the fused kernel's (16 lanes,
+// clusters of 4, 16-point first round), every cluster resident at once,
+// fewer than 2^24 steps per pass and C H W < 2^31.
+fgmm_status ckbd_fusable(fgmm_handle* h, int K, int dtype, int64_t C, int64_t H, int64_t W, int32_t Sa, int32_t Sn,
+                         bool* fuse)
+{
+    *fuse = false;
+    const Geom g = make_geom(C, H, W);
+    const int64_t Na = g.C * g.per_a, Nn = g.C * g.per_n;
+    if (dtype != FGMM_DTYPE_F32 || h->phi != FGMM_PHI_AS || h->decode_lanes != 0 || h->decode_cluster != 0 ||
+        h->decode_round0 != 0 || h->test_silent_stream >= 0 || Na == 0 || Nn == 0 ||
+        steps_of(Na, Sa) >= ((int64_t)1 << 24) || steps_of(Nn, Sn) >= ((int64_t)1 << 24) ||
+        g.N >= ((int64_t)1 << 31))
+        return FGMM_OK;
+    const int64_t nseg = Sa / 32 + Sn / 32;
+    int lanes = 1, cluster = 1, round0 = 0, kernel = 0;
+    decode_resolve(nseg, h->num_sms, 0, 0, 0, FGMM_PHI_AS, &lanes, &cluster, &round0, &kernel);
+    if (!(kernel == FGMM_DEC_WS && lanes == 16 && cluster == 4 && round0 == 16)) return FGMM_OK;
+    if (h->ckbd_clusters[K] < 0) {
+        int n = 0;
+        cudaError_t e = ws_ckbd_capacity(K, &n);
+        if (e != cudaSuccess) return cuda_fail(h, e, "checkerboard decode: occupancy query");
+        h->ckbd_clusters[K] = n;
+    }
+    *fuse = nseg <= h->ckbd_clusters[K];
+    return FGMM_OK;
+}
+
 }  // namespace
 
 extern "C" {
+
+fgmm_status fgmm_ckbd_decode_plan(fgmm_handle* h, int32_t K, int32_t dtype, int64_t C, int64_t H, int64_t W,
+                                  int32_t Sa, int32_t Sn, int32_t* fused)
+{
+    if (!h || !fused) return fail(h, FGMM_ERR_INVALID_ARG, "fgmm_ckbd_decode_plan: NULL argument");
+    if (K < 1 || K > 4 || (dtype != FGMM_DTYPE_F32 && dtype != FGMM_DTYPE_BF16))
+        return fail(h, FGMM_ERR_INVALID_ARG, "fgmm_ckbd_decode_plan: bad K or dtype");
+    if (Sa <= 0 || Sa % 32 != 0 || Sn <= 0 || Sn % 32 != 0)
+        return fail(h, FGMM_ERR_INVALID_ARG, "S must be a positive multiple of 32");
+    fgmm_status s = check_geom(h, C, H, W);
+    if (s != FGMM_OK) return s;
+    bool f = false;
+    s = ckbd_fusable(h, K, dtype, C, H, W, Sa, Sn, &f);
+    if (s != FGMM_OK) return s;
+    *fused = f ? 1 : 0;
+    return FGMM_OK;
+}
 
 int64_t fgmm_ckbd_anchors(int64_t C, int64_t H, int64_t W)
 {
@@ -204,6 +251,122 @@ fgmm_status fgmm_ckbd_context(fgmm_handle* h, const fgmm_latent* lat, int64_t C,
                                                               params_n);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? FGMM_OK : cuda_fail(h, e, "fgmm_ckbd_context launch");
+}
+
+fgmm_status fgmm_ckbd_decode(fgmm_handle* h, const fgmm_latent* lat, int64_t C, int64_t H, int64_t W,
+                             const uint16_t* words_a, int64_t n_words_a, const int64_t* offsets_a, int32_t Sa,
+                             const uint16_t* words_n, int64_t n_words_n, const int64_t* offsets_n, int32_t Sn,
+                             int32_t* y, void* stream)
+{
+    fgmm_status s = check_latent(h, lat);
+    if (s != FGMM_OK) return s;
+    s = check_geom(h, C, H, W);
+    if (s != FGMM_OK) return s;
+    if (lat->N != C * H * W) return fail(h, FGMM_ERR_INVALID_ARG, "fgmm_ckbd_decode: N != C * H * W");
+    if (Sa <= 0 || Sa % 32 != 0 || Sn <= 0 || Sn % 32 != 0)
+        return fail(h, FGMM_ERR_INVALID_ARG, "S must be a positive multiple of 32");
+    if (!offsets_a || !offsets_n || n_words_a < 0 || n_words_n < 0 || (n_words_a > 0 && !words_a) ||
+        (n_words_n > 0 && !words_n) || (lat->N > 0 && !y))
+        return fail(h, FGMM_ERR_INVALID_ARG, "fgmm_ckbd_decode: NULL buffer");
+    const Geom g = make_geom(C, H, W);
+    const int64_t Na = g.C * g.per_a, Nn = g.C * g.per_n;
+    const int K = lat->K;
+    const size_t esz = lat->dtype == FGMM_DTYPE_BF16 ? 2 : 4;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // workspace: anchor params [3K][Na] | non-anchor params [3K][Nn] fp32 |
+    // anchors [Na] | non-anchors [Nn] | pass-0 step arrivals [steps]
+    const size_t b_pa = align_up(3 * (size_t)K * Na * esz, 256), b_pn = align_up(3 * (size_t)K * Nn * 4, 256);
+    const size_t b_ya = align_up(4 * (size_t)Na, 256), b_yn = align_up(4 * (size_t)Nn, 256);
+    const size_t b_pr = align_up(4 * (size_t)steps_of(Na, Sa), 256);
+    s = ws_reserve(h, b_pa + b_pn + b_ya + b_yn + b_pr, st);
+    if (s != FGMM_OK) return s;
+    unsigned char* base = static_cast<unsigned char*>(h->ws);
+    void* pa = base;
+    float* pn = reinterpret_cast<float*>(base + b_pa);
+    int32_t* ya = reinterpret_cast<int32_t*>(base + b_pa + b_pn);
+    int32_t* yn = reinterpret_cast<int32_t*>(base + b_pa + b_pn + b_ya);
+    uint32_t* arrivals = reinterpret_cast<uint32_t*>(base + b_pa + b_pn + b_ya + b_yn);
+    DecodeArgs da, dn;
+    da.params = pa;
+    da.N = Na;
+    da.S = Sa;
+    da.T = steps_of(Na, Sa);
+    da.words = words_a;
+    da.n_words = n_words_a;
+    da.offsets = offsets_a;
+    da.nseg = Sa / 32;
+    da.out = ya;
+    dn.params = pn;
+    dn.N = Nn;
+    dn.S = Sn;
+    dn.T = steps_of(Nn, Sn);
+    dn.words = words_n;
+    dn.n_words = n_words_n;
+    dn.offsets = offsets_n;
+    dn.nseg = Sn / 32;
+    dn.out = yn;
+
+    bool fuse = false;
+    s = ckbd_fusable(h, K, lat->dtype, C, H, W, Sa, Sn, &fuse);
+    if (s != FGMM_OK) return s;
+    const unsigned grid = grid_for(g.N, h->num_sms);
+    cudaError_t e;
+    if (fuse) {
+        fgmm_ckbd_split_kernel<uint32_t><<<grid, 256, 0, st>>>(g, K, static_cast<const uint32_t*>(lat->params),
+                                                               nullptr, static_cast<uint32_t*>(pa), nullptr,
+                                                               reinterpret_cast<uint32_t*>(pn), nullptr);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaMemsetAsync(arrivals, 0, 4 * (size_t)da.T, st);
+        if (e == cudaSuccess) {
+            CkbdFuseArgs fa;
+            da.err = dn.err = h->d_err;
+            da.stats = dn.stats = h->stats_on ? h->d_stats : nullptr;
+            da.r0 = dn.r0 = 16;
+            fa.pass[0] = da;
+            fa.pass[1] = dn;
+            fa.C = C;
+            fa.H = H;
+            fa.W = W;
+            fa.arrivals = arrivals;
+            e = launch_ws_ckbd(fa, K, st);
+        }
+        if (e == cudaSuccess) {
+            fgmm_ckbd_merge_kernel<<<grid, 256, 0, st>>>(g, ya, yn, y);
+            e = cudaGetLastError();
+        }
+        return e == cudaSuccess ? FGMM_OK : cuda_fail(h, e, "fgmm_ckbd_decode launch");
+    }
+    // the passes one after the other
+    if (g.N == 0) return FGMM_OK;
+    if (lat->dtype == FGMM_DTYPE_BF16)
+        fgmm_ckbd_split_kernel<uint16_t><<<grid, 256, 0, st>>>(g, K, static_cast<const uint16_t*>(lat->params),
+                                                               nullptr, static_cast<uint16_t*>(pa), nullptr,
+                                                               nullptr, nullptr);
+    else
+        fgmm_ckbd_split_kernel<uint32_t><<<grid, 256, 0, st>>>(g, K, static_cast<const uint32_t*>(lat->params),
+                                                               nullptr, static_cast<uint32_t*>(pa), nullptr,
+                                                               nullptr, nullptr);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = decode_planned(h, da, K, lat->dtype, st);
+    if (e == cudaSuccess) {
+        fgmm_ckbd_merge_kernel<<<grid, 256, 0, st>>>(g, ya, nullptr, y);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess && Nn > 0) {
+        if (lat->dtype == FGMM_DTYPE_BF16)
+            fgmm_ckbd_context_kernel<__nv_bfloat16><<<grid, 256, 0, st>>>(
+                g, K, static_cast<const __nv_bfloat16*>(lat->params), y, pn);
+        else
+            fgmm_ckbd_context_kernel<float><<<grid, 256, 0, st>>>(g, K, static_cast<const float*>(lat->params), y,
+                                                                  pn);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = decode_planned(h, dn, K, FGMM_DTYPE_F32, st);
+        if (e == cudaSuccess) {
+            fgmm_ckbd_merge_kernel<<<grid, 256, 0, st>>>(g, ya, yn, y);
+            e = cudaGetLastError();
+        }
+    }
+    return e == cudaSuccess ? FGMM_OK : cuda_fail(h, e, "fgmm_ckbd_decode launch");
 }
 
 }  // extern "C"

@@ -370,6 +370,25 @@ inline void launch_compact(const uint16_t* seg, int64_t cap, const int64_t* len,
 // ===========================================================================
 namespace fgmm {
 
+cudaError_t decode_planned(fgmm_handle* h, DecodeArgs& a, int K, int dtype, cudaStream_t st)
+{
+    a.err = h->d_err;
+    a.stats = h->stats_on ? h->d_stats : nullptr;
+    int lanes = 1, cluster = 1, round0 = 0, kernel = 0;
+    decode_resolve(a.nseg, h->num_sms, h->decode_lanes, h->decode_cluster, h->decode_round0, h->phi, &lanes,
+                   &cluster, &round0, &kernel);
+    if (kernel == FGMM_DEC_WS && a.T >= ((int64_t)1 << 24)) {   // streams beyond the warp-specialised kernel's range
+        lanes = 1;
+        cluster = 1;
+        round0 = 0;
+        kernel = FGMM_DEC_LANE;
+    }
+    a.r0 = round0 > 0 ? round0 : 32;
+    a.phi = h->phi;
+    a.silent = h->test_silent_stream;
+    return launch_decode(a, K, dtype, lanes, cluster, st);
+}
+
 fgmm_status ws_reserve(fgmm_handle* h, size_t bytes, cudaStream_t stream)
 {
     if (bytes <= h->ws_bytes) return FGMM_OK;
@@ -634,21 +653,7 @@ fgmm_status fgmm_decode(fgmm_handle* h, const fgmm_latent* lat, const uint16_t* 
     a.offsets = offsets;
     a.nseg = S / 32;
     a.out = symbols_out;
-    a.err = h->d_err;
-    a.stats = h->stats_on ? h->d_stats : nullptr;
-    int lanes = 1, cluster = 1, round0 = 0, kernel = 0;
-    decode_resolve(a.nseg, h->num_sms, h->decode_lanes, h->decode_cluster, h->decode_round0, h->phi, &lanes,
-                   &cluster, &round0, &kernel);
-    if (kernel == FGMM_DEC_WS && a.T >= ((int64_t)1 << 24)) {   // streams beyond the warp-specialised kernel's range
-        lanes = 1;
-        cluster = 1;
-        round0 = 0;
-        kernel = FGMM_DEC_LANE;
-    }
-    a.r0 = round0 > 0 ? round0 : 32;
-    a.phi = h->phi;
-    a.silent = h->test_silent_stream;
-    cudaError_t e = launch_decode(a, lat->K, lat->dtype, lanes, cluster, st);
+    cudaError_t e = decode_planned(h, a, lat->K, lat->dtype, st);
     return e == cudaSuccess ? FGMM_OK : cuda_fail(h, e, "fgmm_decode launch");
 }
 

@@ -121,11 +121,207 @@ __device__ __forceinline__ int round0_point(const Mix<K>& m, int i)
     return m.lo + ((i + 1) * W + R0 - 1) / R0;
 }
 
-template <int K, typename T, int CL, int SPW, int R0>
-__global__ void __launch_bounds__(32 * (32 / CL / SPW + 32 / CL * R0 / 32))
-    fgmm_dec_ws_kernel(const T* __restrict__ params, int64_t N, int32_t S, int64_t T_steps,
-                       const uint16_t* __restrict__ words, int64_t n_words, const int64_t* __restrict__ offsets,
-                       int32_t* __restrict__ out, int32_t* err, unsigned long long* stats, int mode, int silent)
+// ---------------------------------------------------------------------------
+// Checkerboard two-pass decode in one launch (MODE 1 of the kernel below).
+// Anchors are positions with h + w even; both classes are listed channel by
+// channel in raster order (the layout of fgmm_ckbd.cu), so the anchors a
+// non-anchor needs lie at most one row ahead of it, and the second pass can
+// run a few steps behind the first instead of after it.
+// ---------------------------------------------------------------------------
+struct WsPassDev {
+    const void* params;
+    int64_t N;
+    int32_t S, mode;
+    int64_t T;
+    const uint16_t* words;
+    int64_t n_words;
+    const int64_t* offsets;
+    int32_t* out;
+};
+
+struct WsFuseDev {
+    WsPassDev pass[2];
+    int64_t nseg0;          // clusters of pass 0
+    uint32_t H, W;          // C H W < 2^31 (the host checks)
+    uint32_t per_a, per_n;  // anchors / non-anchors per channel
+    uint32_t pq, pr;        // per_n = pq W + pr
+    uint32_t adv_c, adv_h, adv_r;   // pass 1's S = adv_c per_n + adv_h W + adv_r
+    const int32_t* ya;      // pass 0's output: the decoded anchors
+    uint32_t* arrivals;     // [pass 0's steps]: pass-0 CTAs that completed the step
+};
+
+// The context warp's lane q follows column i = u S + nbase + q of pass 1
+// from step to step as (c, hp, rem): channel c, and i's index within the
+// channel, k = hp W + rem (rem < W). Rows alternate floor(W/2) and
+// ceil(W/2) non-anchors, floor(W/2) first, so k sits in row 2 hp at w =
+// 2 rem + 1 when rem < floor(W/2), else in row 2 hp + 1 at w = 2 (rem -
+// floor(W/2)). Advancing by S adds the precomputed (adv_c, adv_h, adv_r)
+// with one carry and at most one wrap into the next channel (k < per_n).
+struct CkbdPos {
+    uint32_t c, hp, rem;
+};
+
+__device__ __forceinline__ CkbdPos ckbd_pos(const WsFuseDev& fz, uint32_t i)
+{
+    CkbdPos p;
+    p.c = i / fz.per_n;
+    const uint32_t k = i - p.c * fz.per_n;
+    p.hp = k / fz.W;
+    p.rem = k - p.hp * fz.W;
+    return p;
+}
+
+__device__ __forceinline__ void ckbd_advance(const WsFuseDev& fz, CkbdPos& p)
+{
+    p.c += fz.adv_c;
+    p.hp += fz.adv_h;
+    p.rem += fz.adv_r;
+    if (p.rem >= fz.W) { p.rem -= fz.W; ++p.hp; }
+    if (p.hp > fz.pq || (p.hp == fz.pq && p.rem >= fz.pr)) {   // k >= per_n = pq W + pr
+        if (p.rem >= fz.pr) { p.rem -= fz.pr; p.hp -= fz.pq; }
+        else { p.rem += fz.W - fz.pr; p.hp -= fz.pq + 1; }
+        ++p.c;
+    }
+}
+
+__device__ __forceinline__ uint32_t ckbd_row(const WsFuseDev& fz, const CkbdPos& p)
+{
+    return p.rem < fz.W / 2 ? 2 * p.hp : 2 * p.hp + 1;
+}
+
+// Index of the anchor at (c, h, w), h + w even.
+__device__ __forceinline__ uint32_t anchor_index(const WsFuseDev& fz, uint32_t c, uint32_t h, uint32_t w)
+{
+    return c * fz.per_a + (h >> 1) * fz.W + (h & 1) * ((fz.W + 1) / 2) + (w >> 1);
+}
+
+// A cursor of the context warp over pass 1's steps: at step u, lane q's
+// column u S + nbase + q (pos), and need, the pass-0 steps that must be
+// complete before the warp reads the neighbours of the step's columns: 0
+// when no column is below Nn, all of pass 0 when some but not all are,
+// else the steps that hold the anchors of channel c's rows 0 .. min(h + 2,
+// H) - 1 and of the earlier channels, (c, h) the last column's position
+// (lane SPC - 1), among them every neighbour of the columns. That bound
+// only grows from step to step, so need follows it by additions (needb =
+// need Sa >= bound).
+struct CkbdCursor {
+    CkbdPos pos;
+    uint32_t u, need, needb;
+};
+
+template <int SPC>
+__device__ __forceinline__ void cursor_need(const WsFuseDev& fz, CkbdCursor& k, uint32_t nbase)
+{
+    const uint32_t Nn = (uint32_t)fz.pass[1].N, n0 = k.u * (uint32_t)fz.pass[1].S + nbase;
+    const uint32_t rows = min(ckbd_row(fz, k.pos) + 2, fz.H);
+    const uint32_t bound = __shfl_sync(kFull, k.pos.c * fz.per_a + (rows >> 1) * fz.W + (rows & 1) * ((fz.W + 1) / 2),
+                                       SPC - 1);
+    if (n0 >= Nn) {
+        k.need = 0u;
+    } else if (n0 + SPC > Nn) {
+        k.need = (uint32_t)fz.pass[0].T;
+    } else {
+        const uint32_t Sa = (uint32_t)fz.pass[0].S;
+        while (k.needb < bound) {
+            k.needb += Sa;
+            ++k.need;
+        }
+    }
+}
+
+template <int SPC>
+__device__ __forceinline__ void cursor_next(const WsFuseDev& fz, CkbdCursor& k, uint32_t nbase)
+{
+    ckbd_advance(fz, k.pos);
+    ++k.u;
+    cursor_need<SPC>(fz, k, nbase);
+}
+
+// Polls read pass 0's arrival counts with acquire loads (measured faster
+// here than a relaxed read and a fence) and, when a poll is needed, ask for
+// the count of a step kPollAhead beyond the next one, so that one poll
+// covers several steps.
+constexpr int kPollAhead = 4;
+
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p)
+{
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Waits (warp-wide, bounded) until pass 0 has completed `need` steps, seen
+// being the count already established. The acquire is lane 0's read of the
+// step's arrival count; __syncwarp then orders the other lanes' later reads
+// of the anchors after it. On giving up: FGMM_ERR_TIMEOUT and the cluster's
+// abort flag.
+template <int CL>
+__device__ __forceinline__ void ckbd_wait(const WsFuseDev& fz, uint32_t need, uint32_t& seen, uint32_t nprog,
+                                          uint32_t* abort_flag, int32_t* err, int lane)
+{
+    if (need <= seen) return;
+    const volatile uint32_t* va = abort_flag;
+    for (uint32_t spin = 0;; ++spin) {
+        uint32_t v = 0;
+        if (lane == 0) v = ld_acquire_u32(fz.arrivals + (need - 1));
+        v = __shfl_sync(kFull, v, 0);
+        if (v >= nprog) {
+            __syncwarp();
+            seen = need;
+            return;
+        }
+        if (__any_sync(kFull, *va != 0u)) return;
+        if (spin >= kSpinLimit) {
+            if (lane == 0) set_error(err, kErrTimeout);
+            if (lane < CL) store_rank(abort_flag, (uint32_t)lane, 1u);
+            return;
+        }
+    }
+}
+
+// Issues the loads of the in-bounds 4-neighbour anchors of the non-anchor
+// at p when `take` (L2, never L1: pass 0 writes them during the launch);
+// fixed slots (up, down, left, right; zero when out of bounds) keep v in
+// registers.
+__device__ __forceinline__ void ckbd_load(const WsFuseDev& fz, bool take, const CkbdPos& p, int32_t (&v)[4], int& cnt)
+{
+    v[0] = v[1] = v[2] = v[3] = 0;
+    cnt = 0;
+    if (!take) return;
+    const uint32_t h = ckbd_row(fz, p), w = p.rem < fz.W / 2 ? 2 * p.rem + 1 : 2 * (p.rem - fz.W / 2);
+    if (h > 0) v[0] = __ldcg(fz.ya + anchor_index(fz, p.c, h - 1, w));
+    if (h + 1 < fz.H) v[1] = __ldcg(fz.ya + anchor_index(fz, p.c, h + 1, w));
+    if (w > 0) v[2] = __ldcg(fz.ya + anchor_index(fz, p.c, h, w - 1));
+    if (w + 1 < fz.W) v[3] = __ldcg(fz.ya + anchor_index(fz, p.c, h, w + 1));
+    cnt = (h > 0) + (h + 1 < fz.H) + (w > 0) + (w + 1 < fz.W);
+}
+
+// float(ctx) and -cnt of the loaded neighbours (ctx summed in 64 bits).
+__device__ __forceinline__ float2 ckbd_ctx(const int32_t (&v)[4], int cnt)
+{
+    const int64_t ctx = (int64_t)v[0] + (int64_t)v[1] + (int64_t)v[2] + (int64_t)v[3];
+    return make_float2(__ll2float_rn(ctx), -(float)cnt);
+}
+
+// MODE 0: one latent (the arguments). MODE 1: the checkerboard's two passes
+// in one launch (fz; the other arguments except err, stats and silent are
+// unused), with one more warp per CTA, the context warp: clusters below
+// fz.nseg0 decode the anchors, their context warp counting each completed
+// step in fz.arrivals; the others decode the non-anchors, their context
+// warp running a pipeline for the step the producers stage: it waits until
+// pass 0 has completed the steps that hold the columns' neighbours (polled
+// an iteration ahead, for a step kPollAhead further on), loads the
+// neighbours into registers, and an iteration later turns them into
+// (float(ctx), -cnt) in shared memory. The producers apply the stand-in
+// context to the staged hyperprior parameters as they set the step's
+// mixtures up: w' = w, mu' = fmaf(0.125, fmaf(-cnt, mu, float(ctx)), mu),
+// sigma' = 0.75 sigma, each one FP32 rounding.
+template <int K, typename T, int CL, int SPW, int R0, int MODE = 0>
+__global__ void __launch_bounds__(32 * (32 / CL / SPW + 32 / CL * R0 / 32) + (MODE == 1 ? 32 : 0))
+    fgmm_dec_ws_kernel(const T* __restrict__ params_a, int64_t N_a, int32_t S_a, int64_t T_a,
+                       const uint16_t* __restrict__ words_a, int64_t n_words_a, const int64_t* __restrict__ offsets_a,
+                       int32_t* __restrict__ out_a, int32_t* err, unsigned long long* stats, int mode_a, int silent,
+                       WsFuseDev fz)
 {
     constexpr int SPC = 32 / CL;              // streams per CTA
     constexpr int LPS = 32 / SPW;             // consumer lanes per stream
@@ -133,7 +329,7 @@ __global__ void __launch_bounds__(32 * (32 / CL / SPW + 32 / CL * R0 / 32))
     constexpr int CW = SPC / SPW;             // consumer warps
     constexpr int SPP = 32 / R0;              // streams per producer warp
     constexpr int PW = SPC / SPP;             // producer warps
-    constexpr int NT = 32 * (CW + PW);
+    constexpr int NT = 32 * (CW + PW) + (MODE == 1 ? 32 : 0);   // threads (MODE 1: + the context warp)
     constexpr int PNT = 32 * PW;              // producer threads
     // W <= 511, so the bracket interior has at most ceil(511 / R0) - 1 points
     constexpr bool kOneRound = LPS >= (511 + R0 - 1) / R0 - 1;
@@ -145,23 +341,53 @@ __global__ void __launch_bounds__(32 * (32 / CL / SPW + 32 / CL * R0 / 32))
                                                   sizeof(T) * kRing * 3 * K * SPC);     // [2][32]
     uint32_t* abort_flag = xflag + 64;                                                      // [1] (+3 pad)
     uint16_t* wsm = reinterpret_cast<uint16_t*>(xflag + 68);                                // [kWordCap]
+    float2* ctxb = reinterpret_cast<float2*>(wsm + kWordCap);   // MODE 1, pass 1: (float(ctx), -cnt) [kRing][SPC]
 
     const int rank = (int)cluster_rank();
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const bool producer = warp >= CW;
+    const bool xwarp = MODE == 1 && warp == CW + PW;   // the context warp
+    const bool producer = warp >= CW && !xwarp, consumer = warp < CW;
     const int grp = lane / LPS, j = lane % LPS;       // consumer: stream group, lane in group
     const int pi = lane % R0;                         // producer: round-0 point of this lane
-    const int wl = producer ? (warp - CW) * SPP + lane / R0 : warp * SPW + grp;   // stream slot in this CTA
+    const int wl = producer ? (warp - CW) * SPP + lane / R0 : consumer ? warp * SPW + grp : 0;   // stream slot
     const int ws = rank * SPC + wl;                   // stream within the segment
     const uint32_t bit = 1u << ws;
     const int gbase = grp * LPS;
     const uint32_t gmask = LPS == 32 ? kFull : (((1u << LPS) - 1u) << gbase);
     const int ptid = tid - 32 * CW;                   // producer thread index
-    const int64_t g = blockIdx.x / CL;
+    int64_t g = blockIdx.x / CL;
+    int pass = 0;
+    const T* params = params_a;
+    int64_t N = N_a, T_steps = T_a, n_words = n_words_a;
+    int32_t S = S_a;
+    int mode = mode_a;
+    const uint16_t* words = words_a;
+    const int64_t* offsets = offsets_a;
+    int32_t* out = out_a;
+    if constexpr (MODE == 1) {
+        if (g >= fz.nseg0) {
+            pass = 1;
+            g -= fz.nseg0;
+        }
+        const WsPassDev& P = fz.pass[pass];
+        params = static_cast<const T*>(P.params);
+        N = P.N;
+        S = P.S;
+        T_steps = P.T;
+        mode = P.mode;
+        words = P.words;
+        n_words = P.n_words;
+        offsets = P.offsets;
+        out = P.out;
+    }
+    const bool counts = MODE == 1 && pass == 0;   // pass 0 of MODE 1: counts each step's completion
+    const bool ctxw = MODE == 1 && pass == 1 && xwarp;   // pass 1's context warp
     const bool posts = !(g == 0 && ws == silent);
     const int64_t beg = offsets[g], end = offsets[g + 1];
     if (!(beg >= 0 && end <= n_words && end - beg >= 64)) {
         if (tid == 0 && rank == 0) set_error(err, kErrCorrupt);
+        if (counts)   // every step counted once for this CTA, so that no wait on it runs out
+            for (int64_t u = tid; u < T_steps; u += NT) atomicAdd(fz.arrivals + u, 1u);
         return;
     }
     const int64_t seg_len = end - beg;
@@ -177,6 +403,14 @@ __global__ void __launch_bounds__(32 * (32 / CL / SPW + 32 / CL * R0 / 32))
         RawParams<K> r;
 #pragma unroll
         for (int i = 0; i < 3 * K; ++i) r.v[i] = smem_param<T>(slot_p + i * SPC + wl);
+        if (MODE == 1 && pass == 1) {   // the stand-in context
+            const float2 cx = ctxb[(u % kRing) * SPC + wl];
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                r.v[K + k] = __fmaf_rn(0.125f, __fmaf_rn(cx.y, r.v[K + k], cx.x), r.v[K + k]);
+                r.v[2 * K + k] = __fmul_rn(r.v[2 * K + k], 0.75f);
+            }
+        }
         Mix<K> m;
         const bool ok = mix_from_params<K>(r, m);
         const bool act = u * (int64_t)S + g * 32 + ws < N;
@@ -216,17 +450,43 @@ __global__ void __launch_bounds__(32 * (32 / CL / SPW + 32 / CL * R0 / 32))
         }
     };
 
-    // prologue: parameters of steps 0 .. kLead+1, words, exchange flags,
+    // prologue: exchange flags, parameters of steps 0 .. kLead+1, words,
     // round 0 of steps 0 .. kLead-1
+    if (tid < 68) xflag[tid] = tid == 64 ? 0u : 0xffffffffu;   // tags no exchange number reaches; abort flag 0
+    // pass 1 of MODE 1: (float(ctx), -cnt) per step slot and column, after the words
+    uint32_t seen = 0, poll_k = 0, poll_v = 0;   // context warp: pass-0 steps known complete; poll in flight
+    int32_t nb[4] = {0, 0, 0, 0};                 // context warp: neighbours loaded for the next slot
+    int nbc = 0;
+    CkbdCursor cur = {}, far = {};                // context warp: the next step to load; kPollAhead steps on
+    const uint32_t nprog = (uint32_t)(fz.nseg0 * CL);
+    // context warp: waits for and loads the neighbours of step cur.u, then moves both cursors on a step
+    auto ctx_load = [&]() {
+        ckbd_wait<CL>(fz, cur.need, seen, nprog, abort_flag, err, lane);
+        ckbd_load(fz, lane < SPC && cur.u * (uint32_t)S + (uint32_t)nbase + lane < (uint32_t)N, cur.pos, nb, nbc);
+        cursor_next<SPC>(fz, cur, (uint32_t)nbase);
+        cursor_next<SPC>(fz, far, (uint32_t)nbase);
+    };
+    if constexpr (MODE == 1) {
+        seg_sync<CL>();   // flags initialised in every CTA before a context wait may raise abort
+        if (ctxw) {
+            cur.pos = ckbd_pos(fz, (uint32_t)nbase + lane);
+            cursor_need<SPC>(fz, cur, (uint32_t)nbase);
+            far = cur;
+            for (int d = 0; d < kPollAhead; ++d) cursor_next<SPC>(fz, far, (uint32_t)nbase);
+            for (int64_t p = 0; p < kLead + 2 && p < T_steps; ++p) {
+                ctx_load();
+                if (lane < SPC) ctxb[(p % kRing) * SPC + lane] = ckbd_ctx(nb, nbc);
+            }
+        }
+    }
     for (int p = 0; p < kLead + 2; ++p) {
         if (producer && p < T_steps)
-            stage_params<K, T, SPC>(ring + (p % kRing) * 3 * K * SPC, params, N, p * (int64_t)S + nbase, ptid, PNT,
-                                    mode);
+            stage_params<K, T, SPC>(ring + (p % kRing) * 3 * K * SPC, params, N, p * (int64_t)S + nbase, ptid,
+                                    PNT, mode);
         cp_async_commit();
     }
     if (staged)
         for (int64_t i = tid; i < seg_len; i += NT) wsm[i] = __ldg(words + beg + i);
-    if (tid < 68) xflag[tid] = tid == 64 ? 0u : 0xffffffffu;   // tags no exchange number reaches; abort flag 0
     cp_async_wait<1>();   // steps 0 .. kLead resident
     __syncthreads();
     if (producer)
@@ -243,7 +503,7 @@ __global__ void __launch_bounds__(32 * (32 / CL / SPW + 32 / CL * R0 / 32))
     uint32_t q0[VPL];
 #pragma unroll
     for (int v = 0; v < VPL; ++v) q0[v] = 0;
-    if (!producer && T_steps > 0) fetch(0, m, q0);
+    if (consumer && T_steps > 0) fetch(0, m, q0);
 
     for (int64_t t = 0; t < T_steps; ++t) {
         if (producer) {
@@ -253,6 +513,27 @@ __global__ void __launch_bounds__(32 * (32 / CL / SPW + 32 / CL * R0 / 32))
             cp_async_commit();
             if (t + kLead < T_steps) produce(t + kLead);
             cp_async_wait<1>();   // step t + kLead + 1 resident for the next iteration
+        } else if (xwarp) {
+            if (ctxw) {
+                // neighbours of step t + kLead + 1 (loaded an iteration ago) into its slot
+                if (t > 0 && t + kLead + 1 < T_steps && lane < SPC)
+                    ctxb[((t + kLead + 1) % kRing) * SPC + lane] = ckbd_ctx(nb, nbc);
+                if (poll_k != 0) {   // the poll issued an iteration ago
+                    if (__shfl_sync(kFull, poll_v, 0) >= nprog) {   // lane 0's acquire saw the count
+                        __syncwarp();
+                        seen = poll_k;
+                    }
+                    poll_k = 0;
+                }
+                if (t + kLead + 2 < T_steps) {
+                    ctx_load();   // step t + kLead + 2
+                    // a poll for the next step's count, or the larger one kPollAhead steps on
+                    if (t + kLead + 3 < T_steps && cur.need > seen) {
+                        poll_k = max(cur.need, far.need);
+                        if (lane == 0) poll_v = ld_acquire_u32(fz.arrivals + (poll_k - 1));
+                    }
+                }
+            }
         } else {
             const bool act = n < N;
             int32_t s = 0;
@@ -353,9 +634,13 @@ __global__ void __launch_bounds__(32 * (32 / CL / SPW + 32 / CL * R0 / 32))
             n += S;
         }
         __syncthreads();   // producers' round for step t + 2 visible; slots read
+        if (counts && xwarp && lane == 0) {   // this step's symbols stored by every consumer of the CTA
+            __threadfence();
+            atomicAdd(fz.arrivals + t, 1u);
+        }
     }
     cp_async_wait<0>();
-    const bool fail = !producer && (bad || x != kL || rp != 0);
+    const bool fail = consumer && (bad || x != kL || rp != 0);
     if (__syncthreads_or(fail) && tid == 0) set_error(err, kErrCorrupt);
     if (__syncthreads_or(badp) && tid == 0) set_error(err, kErrBadParams);
     if (stats) {
@@ -402,8 +687,104 @@ cudaError_t launch_ws(const DecodeArgs& a, cudaStream_t st)
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
+    WsFuseDev none = {};
     return cudaLaunchKernelEx(&cfg, kern, static_cast<const T*>(a.params), a.N, a.S, a.T, a.words, a.n_words,
-                              a.offsets, a.out, a.err, a.stats, mode, a.silent);
+                              a.offsets, a.out, a.err, a.stats, mode, a.silent, none);
+}
+
+// Staging mode of stage_params for fp32 or bf16 rows of N elements at base.
+template <typename T, int SPC>
+int ws_stage_mode(const void* p, int64_t N)
+{
+    const uintptr_t base = reinterpret_cast<uintptr_t>(p);
+    if (base % 16 == 0 && (N * (int64_t)sizeof(T)) % 16 == 0 && SPC * sizeof(T) >= 16) return 2;
+    if (base % 4 == 0 && (N * (int64_t)sizeof(T)) % 4 == 0 && SPC * sizeof(T) >= 4) return 1;
+    return 0;
+}
+
+// The checkerboard's two passes in one launch: 16 lanes per stream,
+// clusters of 4, a 16-point first round, fp32 parameters; pass 1's
+// context slots follow the words in shared memory. The host runs it only
+// when every cluster fits on the device at once (ws_ckbd_capacity).
+template <int K>
+struct WsCkbdShape {
+    static constexpr int CL = 4, SPW = 2, R0 = 16, SPC = 32 / CL;
+    static constexpr int NT = 32 * (SPC / SPW + SPC * R0 / 32) + 32;   // + the context warp
+    static constexpr size_t smem = sizeof(PreStep<K>) * kPre * SPC + sizeof(float) * kRing * 3 * K * SPC +
+                                   sizeof(uint32_t) * 68 + sizeof(uint16_t) * kWordCap + sizeof(float2) * kRing * SPC;
+    static_assert((sizeof(PreStep<K>) * kPre * SPC + sizeof(float) * kRing * 3 * K * SPC + sizeof(uint32_t) * 68 +
+                   sizeof(uint16_t) * kWordCap) % 8 == 0, "context slots 8-byte aligned");
+};
+
+// Clusters of the fused launch that the current device holds at once.
+template <int K>
+cudaError_t ws_ckbd_capacity_k(int* clusters)
+{
+    using Sh = WsCkbdShape<K>;
+    auto kern = fgmm_dec_ws_kernel<K, float, Sh::CL, Sh::SPW, Sh::R0, 1>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::smem);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(Sh::CL);
+    cfg.blockDim = dim3(Sh::NT);
+    cfg.dynamicSmemBytes = Sh::smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = Sh::CL;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaOccupancyMaxActiveClusters(clusters, kern, &cfg);
+}
+
+template <int K>
+cudaError_t launch_ws_ckbd_k(const CkbdFuseArgs& a, cudaStream_t st)
+{
+    using Sh = WsCkbdShape<K>;
+    constexpr int CL = Sh::CL, SPW = Sh::SPW, R0 = Sh::R0, SPC = Sh::SPC, NT = Sh::NT;
+    constexpr size_t smem = Sh::smem;
+    for (int p = 0; p < 2; ++p)
+        if (a.pass[p].T >= ((int64_t)1 << 24)) return cudaErrorInvalidValue;
+    auto kern = fgmm_dec_ws_kernel<K, float, CL, SPW, R0, 1>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    if (a.C * a.H * a.W >= ((int64_t)1 << 31)) return cudaErrorInvalidValue;
+    WsFuseDev fz = {};
+    for (int p = 0; p < 2; ++p) {
+        const DecodeArgs& d = a.pass[p];
+        fz.pass[p] = WsPassDev{d.params, d.N, d.S, ws_stage_mode<float, SPC>(d.params, d.N), d.T, d.words, d.n_words,
+                               d.offsets, d.out};
+    }
+    fz.nseg0 = a.pass[0].nseg;
+    fz.H = (uint32_t)a.H;
+    fz.W = (uint32_t)a.W;
+    fz.per_a = (uint32_t)((a.H * a.W + 1) / 2);
+    fz.per_n = (uint32_t)(a.H * a.W) - fz.per_a;
+    if (fz.per_n == 0) return cudaErrorInvalidValue;
+    fz.pq = fz.per_n / fz.W;
+    fz.pr = fz.per_n % fz.W;
+    const uint32_t Sn = (uint32_t)a.pass[1].S, rs = Sn % fz.per_n;
+    fz.adv_c = Sn / fz.per_n;
+    fz.adv_h = rs / fz.W;
+    fz.adv_r = rs % fz.W;
+    fz.ya = a.pass[0].out;
+    fz.arrivals = a.arrivals;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)((a.pass[0].nseg + a.pass[1].nseg) * CL));
+    cfg.blockDim = dim3(NT);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CL;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const DecodeArgs& d0 = a.pass[0];
+    return cudaLaunchKernelEx(&cfg, kern, static_cast<const float*>(d0.params), d0.N, d0.S, d0.T, d0.words,
+                              d0.n_words, d0.offsets, d0.out, d0.err, d0.stats, 0, d0.silent, fz);
 }
 
 template <int K, typename T, int SPW, int R0>

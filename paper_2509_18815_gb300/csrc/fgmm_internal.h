@@ -23,6 +23,7 @@ struct fgmm_handle {
     int test_silent_stream = -1;       // test hook: a stream of segment 0 that posts no refill flags
     int phi = 0;                       // Phi approximation (FGMM_PHI_*)
     int mlp_act = 0;                   // activation of the proposal network (FGMM_MLP_ACT_*)
+    int ckbd_clusters[5] = {-1, -1, -1, -1, -1};   // fused two-pass decode: resident clusters per K (-1 unknown)
     std::string last_error;
 };
 
@@ -91,6 +92,24 @@ struct DecodeArgs {
     int phi = 0;                       // Phi approximation (FGMM_PHI_*); non-A&S only on the lane decoder
 };
 void decode_config_auto(int64_t nseg, int num_sms, int* lanes, int* cluster, int* round0);
+// Checkerboard two-pass decode in one launch of the warp-specialised decoder
+// (fp32 parameters, 16 lanes per stream, clusters of 4 CTAs, 16-point first
+// round): clusters 0 .. nseg0-1 decode the anchors (pass[0], parameters
+// = the anchors' hyperprior parameters), the rest the non-anchors (pass[1],
+// parameters = the non-anchors' hyperprior parameters, to which the
+// stand-in context is applied on the fly from pass 0's decoded anchors,
+// once every pass-0 CTA has completed the steps that hold those anchors).
+// arrivals: one word per pass-0 step, zero before the launch; C H W < 2^31.
+struct CkbdFuseArgs {
+    DecodeArgs pass[2];
+    int64_t C, H, W;
+    uint32_t* arrivals;
+};
+cudaError_t launch_ws_ckbd(const CkbdFuseArgs& a, int K, cudaStream_t st);
+// Clusters of launch_ws_ckbd's kernel that the current device holds at once:
+// the fused launch runs only when all of them fit, so that every pass-1
+// cluster's wait is on pass-0 clusters that are resident.
+cudaError_t ws_ckbd_capacity(int K, int* clusters);
 // Warp-specialised decoder for fp32 / bf16 parameters: CL CTAs per segment,
 // SPW streams per consumer warp (1, 2 or 4).
 cudaError_t launch_ws_f32(const DecodeArgs& a, int K, int CL, int SPW, cudaStream_t st);
@@ -100,6 +119,10 @@ cudaError_t launch_ws_bf16(const DecodeArgs& a, int K, int CL, int SPW, cudaStre
 void decode_resolve(int64_t nseg, int num_sms, int opt_lanes, int opt_cluster, int opt_round0, int phi, int* lanes,
                     int* cluster, int* round0, int* kernel);
 cudaError_t launch_decode(const DecodeArgs& a, int K, int dtype, int lanes, int cluster, cudaStream_t st);
+// Fills a's error word, statistics and test hook from the handle, picks the
+// decoder as fgmm_decode does (the handle's options, else the automatic plan)
+// and launches it.
+cudaError_t decode_planned(fgmm_handle* h, DecodeArgs& a, int K, int dtype, cudaStream_t st);
 
 // Batch plan records shared by the batch coder (fgmm_batch.cu) and the
 // batched proposal decoder (fgmm_mlp.cu).

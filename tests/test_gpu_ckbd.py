@@ -1,7 +1,8 @@
 """Checkerboard two-pass coding on the GPU against the oracle: the split of
 parameters and symbols into anchors and non-anchors, the merge back, the
 stand-in context (bit-exact, fp32 and bf16 hyperprior parameters), the two
-streams of the two-pass encode (byte-identical) and the two-pass decode."""
+streams of the two-pass encode (byte-identical) and the two-pass decode,
+both as one fused launch and as separate calls."""
 import ctypes
 
 import numpy as np
@@ -128,3 +129,118 @@ def test_two_pass_from_cuda_graphs(bf16):
     (wa_o, _), (wn_o, _) = oracle.ckbd_encode(oracle_params(lat2.params, bf16), lat2.symbols, shape, Sa, Sn)
     np.testing.assert_array_equal(host_u16(wa[: int(ta.item())]), wa_o)
     np.testing.assert_array_equal(host_u16(wn[: int(tn.item())]), wn_o)
+
+
+def _oracle_streams(lat, shape, Sa, Sn, bf16=False):
+    po = oracle_params(lat.params, bf16)
+    (wa, oa), (wn, on) = oracle.ckbd_encode(po, lat.symbols, shape, Sa, Sn)
+    dev = lambda w, o: (torch.from_numpy(w.view(np.int16).copy()).cuda(), torch.from_numpy(o.copy()).cuda())
+    return dev(wa, oa), dev(wn, on)
+
+
+# (shape, Sa, Sn): 10 to 38 segments in all take the fused launch on a GPU
+# of 152 SMs; odd sizes, one-column and one-row channels, one-step passes
+FUSED = [((16, 32, 48), 512, 512), ((8, 16, 24), 160, 192), ((5, 9, 13), 320, 320), ((3, 7, 1), 160, 160),
+         ((2, 1, 5), 160, 160), ((24, 20, 30), 64, 1088), ((64, 64, 96), 1024, 1024)]
+
+
+@pytest.mark.parametrize("shape,Sa,Sn", FUSED)
+def test_fused_two_pass_decode(shape, Sa, Sn):
+    """fgmm_ckbd_decode of the oracle's two streams gives the latent's
+    symbols, in one launch where its plan says so, and the same symbols as
+    the separate calls (integer output: equality)."""
+    codec = _codec()
+    lat = synth.make_ckbd_latent(*shape, 3, seed=970 + Sa + Sn + sum(shape))
+    dp = dev_params(lat.params)
+    first, second = _oracle_streams(lat, shape, Sa, Sn)
+    nseg = Sa // 32 + Sn // 32
+    fused = codec.ckbd_decode_fused(3, torch.float32, shape, Sa, Sn)
+    if 10 <= nseg <= 32 and torch.cuda.get_device_properties(0).multi_processor_count >= 128:
+        assert fused
+    for _ in range(2):
+        y = codec.ckbd_decode(dp, first, second, shape, Sa, Sn)
+        np.testing.assert_array_equal(y.cpu().numpy(), lat.symbols)
+    y2 = codec.ckbd_decode_steps(dp, first, second, shape, Sa, Sn)
+    np.testing.assert_array_equal(y2.cpu().numpy(), lat.symbols)
+
+
+@pytest.mark.parametrize("K", [1, 2, 4])
+def test_fused_two_pass_decode_components(K):
+    codec = _codec()
+    shape, Sa, Sn = (12, 16, 20), 256, 320
+    lat = synth.make_ckbd_latent(*shape, K, seed=990 + K)
+    dp = dev_params(lat.params)
+    first, second = _oracle_streams(lat, shape, Sa, Sn)
+    if torch.cuda.get_device_properties(0).multi_processor_count >= 128:
+        assert codec.ckbd_decode_fused(K, torch.float32, shape, Sa, Sn)
+    y = codec.ckbd_decode(dp, first, second, shape, Sa, Sn)
+    np.testing.assert_array_equal(y.cpu().numpy(), lat.symbols)
+
+
+def test_two_pass_decode_plan():
+    """Cases outside the fused launch: bf16 parameters, too few segments for
+    its plan, a decoder option set; and argument errors."""
+    codec = _codec()
+    from paper_2509_18815_gb300 import _abi
+    from paper_2509_18815_gb300._abi import FGMM_ERR_INVALID_ARG
+    assert not codec.ckbd_decode_fused(3, torch.bfloat16, (16, 32, 48), 512, 512)
+    assert not codec.ckbd_decode_fused(3, torch.float32, (4, 16, 16), 32, 64)
+    h = codec.Handle()
+    h.check(_abi.fgmm_set_option(h.ptr, _abi.FGMM_OPT_DECODE_LANES, 16))
+    assert not codec.ckbd_decode_fused(3, torch.float32, (16, 32, 48), 512, 512, h=h)
+    lat = synth.make_ckbd_latent(16, 32, 48, 3, seed=999)
+    dp = dev_params(lat.params)
+    first, second = _oracle_streams(lat, (16, 32, 48), 512, 512)
+    y = codec.ckbd_decode(dp, first, second, (16, 32, 48), 512, 512, h=h)
+    np.testing.assert_array_equal(y.cpu().numpy(), lat.symbols)
+    h.close()
+    out = ctypes.c_int32(-1)
+    hd = codec.handle()
+    assert _abi.fgmm_ckbd_decode_plan(hd.ptr, 3, 0, 2, 4, 4, 48, 32, ctypes.byref(out)) == FGMM_ERR_INVALID_ARG
+    assert _abi.fgmm_ckbd_decode_plan(hd.ptr, 5, 0, 2, 4, 4, 32, 32, ctypes.byref(out)) == FGMM_ERR_INVALID_ARG
+    desc = codec.latent(dp)
+    assert _abi.fgmm_ckbd_decode(hd.ptr, ctypes.byref(desc), 16, 32, 47, None, 0, None, 512, None, 0, None, 512,
+                                 None, None) == FGMM_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("which", ["anchors", "non_anchors", "anchor_offsets"])
+def test_fused_two_pass_decode_reports_corrupt_streams(which):
+    """Damaged words of either pass, or an anchor segment shorter than its
+    final states, end the fused launch with an error (no wait runs out: a
+    pass-0 segment that cannot be decoded still counts its steps), and the
+    handle decodes the intact streams afterwards."""
+    codec = _codec()
+    from paper_2509_18815_gb300._abi import FgmmError
+    shape, Sa, Sn = (16, 32, 48), 512, 512
+    lat = synth.make_ckbd_latent(*shape, 3, seed=1010)
+    dp = dev_params(lat.params)
+    first, second = _oracle_streams(lat, shape, Sa, Sn)
+    assert codec.ckbd_decode_fused(3, torch.float32, shape, Sa, Sn)
+    (wa, oa), (wn, on) = first, second
+    wa2, oa2, wn2 = wa.clone(), oa.clone(), wn.clone()
+    if which == "anchors":
+        wa2[int(oa[3]) : int(oa[4]) - 64] ^= 0x5A5A
+    elif which == "non_anchors":
+        wn2[int(on[7]) : int(on[8]) - 64] ^= 0x3C3C
+    else:
+        oa2[1] = oa2[0] + 10
+    with pytest.raises(FgmmError):
+        codec.ckbd_decode(dp, (wa2, oa2), (wn2, on), shape, Sa, Sn)
+    y = codec.ckbd_decode(dp, first, second, shape, Sa, Sn)
+    np.testing.assert_array_equal(y.cpu().numpy(), lat.symbols)
+
+
+def test_fused_two_pass_decode_from_cuda_graph():
+    """The fused decode captured into a CUDA graph replays to the exact
+    symbols, and again after the captured stream buffers were overwritten
+    with a second latent's streams of the same lengths' bound."""
+    codec = _codec()
+    shape, Sa, Sn = (16, 32, 48), 512, 512
+    lat = synth.make_ckbd_latent(*shape, 3, seed=1020)
+    dp = dev_params(lat.params)
+    first, second = _oracle_streams(lat, shape, Sa, Sn)
+    gr = codec.CkbdGraphs(dp, shape, Sa, Sn)
+    gr.capture_decode(first, second)
+    for _ in range(2):
+        gr.y.fill_(-3)
+        np.testing.assert_array_equal(gr.decode().cpu().numpy(), lat.symbols)
