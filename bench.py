@@ -128,6 +128,8 @@ def parse():
                     help="launch each roofline kernel twice on small cases, for an ncu capture of DRAM bytes")
     ap.add_argument("--proposal-train-scale", type=float, default=1.0,
                     help="fraction of the training schedule in --proposal-only mode")
+    ap.add_argument("--ckbd-only", action="store_true",
+                    help="run only the checkerboard two-pass case (for profiling its fused decoder)")
     ap.add_argument("--batch-table", action="store_true",
                     help="in --batch-only mode, also time the table-based coder on the batch in chunks")
     ap.add_argument("--batch-overhead", type=float, default=0.01,
@@ -1206,6 +1208,19 @@ def run_proposal_only(args):
     print(json.dumps({f"proposal_{args.proposal_latents}x320x64x96_sigma64": res}))
 
 
+def run_ckbd_only(args):
+    """The checkerboard two-pass case alone. Its first decoder launch is the
+    fused two-pass decode of fgmm_ckbd_decode."""
+    import torch
+    from paper_2509_18815_gb300 import build, codec
+    build.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    h = codec.handle(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    print(json.dumps({"ckbd_192x32x48_k3": ckbd_case(dev, h, flush, max(args.steps, 1))}))
+
+
 def run_traffic_probe(args):
     """Each kernel that has a roofline line in the benchmark, launched once
     after one warm-up, for an ncu capture of DRAM bytes per launch: the
@@ -1266,6 +1281,8 @@ def main():
         run_gsm_only(args)
     elif args.proposal_only:
         run_proposal_only(args)
+    elif args.ckbd_only:
+        run_ckbd_only(args)
     elif args.traffic_probe:
         run_traffic_probe(args)
     elif args.impl == "reference":
