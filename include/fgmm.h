@@ -54,7 +54,8 @@ typedef enum {
     FGMM_ERR_BAD_PARAMS = 2,  /* a mixture parameter is NaN/Inf/negative weight/scale <= 0 */
     FGMM_ERR_CAPACITY = 3,    /* output buffer too small */
     FGMM_ERR_CORRUPT = 4,     /* stream fails the end-of-decode check or would read out of its segment */
-    FGMM_ERR_TIMEOUT = 5,     /* a bounded wait in a decoder gave up (the refill exchange of fgmm_dec_ws_kernel) */
+    FGMM_ERR_TIMEOUT = 5,     /* a bounded wait in a decoder gave up (the refill exchange of fgmm_dec_ws_kernel,
+                                 the two-pass decode's wait for decoded anchors) */
     FGMM_ERR_CUDA = 6,        /* a CUDA runtime call or launch failed */
     FGMM_ERR_NO_MEMORY = 7,   /* workspace allocation failed */
     FGMM_ERR_TOO_LARGE = 8    /* request exceeds the fixed scratch of fgmm_encode_noalloc */
@@ -467,6 +468,14 @@ enum { FGMM_PHI_AS = 0, FGMM_PHI_LOGISTIC = 1, FGMM_PHI_POLYA = 2 };
  * section): FGMM_MLP_ACT_PL (0, default) or FGMM_MLP_ACT_SIGMOID (1). */
 enum { FGMM_OPT_MLP_ACT = 6 };
 enum { FGMM_MLP_ACT_PL = 0, FGMM_MLP_ACT_SIGMOID = 1 };
+
+/* Test hook for the bounded wait of the one-launch two-pass decode
+ * (fgmm_ckbd_decode): with value 1 the anchor CTAs count none of their
+ * steps, so every non-anchor wait for them runs out (after about two
+ * seconds); the decode then records FGMM_ERR_TIMEOUT, releases the other
+ * waits through the clusters' abort flags, and returns. 0 (default) turns
+ * it off. The paper has no counterpart. */
+enum { FGMM_OPT_TEST_SILENT_ARRIVALS = 7 };
 fgmm_status fgmm_set_option(fgmm_handle *h, int32_t option, int64_t value);
 
 /* The decoder fgmm_decode would run for S streams (S / 32 segments) under

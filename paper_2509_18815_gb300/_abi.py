@@ -33,6 +33,7 @@ FGMM_OPT_PHI = 5
 FGMM_PHI_AS, FGMM_PHI_LOGISTIC, FGMM_PHI_POLYA = 0, 1, 2
 FGMM_PEAK_FMA, FGMM_PEAK_RCP = 0, 1
 FGMM_OPT_MLP_ACT = 6
+FGMM_OPT_TEST_SILENT_ARRIVALS = 7
 FGMM_MLP_ACT_PL, FGMM_MLP_ACT_SIGMOID = 0, 1
 FGMM_DEC_LANE, FGMM_DEC_COOP, FGMM_DEC_WIDE, FGMM_DEC_WS = 0, 1, 2, 3
 DECODE_KERNELS = {FGMM_DEC_LANE: "fgmm_dec_kernel", FGMM_DEC_COOP: "fgmm_dec_coop_kernel",

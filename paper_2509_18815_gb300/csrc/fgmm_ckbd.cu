@@ -328,6 +328,7 @@ fgmm_status fgmm_ckbd_decode(fgmm_handle* h, const fgmm_latent* lat, int64_t C, 
             fa.H = H;
             fa.W = W;
             fa.arrivals = arrivals;
+            fa.silent_arrivals = h->test_silent_arrivals;
             e = launch_ws_ckbd(fa, K, st);
         }
         if (e == cudaSuccess) {

@@ -699,6 +699,10 @@ fgmm_status fgmm_set_option(fgmm_handle* h, int32_t option, int64_t value)
             return fail(h, FGMM_ERR_INVALID_ARG, "activation must be FGMM_MLP_ACT_PL or FGMM_MLP_ACT_SIGMOID");
         h->mlp_act = (int)value;
         return FGMM_OK;
+    case FGMM_OPT_TEST_SILENT_ARRIVALS:
+        if (value != 0 && value != 1) return fail(h, FGMM_ERR_INVALID_ARG, "silent arrivals must be 0 or 1");
+        h->test_silent_arrivals = (int)value;
+        return FGMM_OK;
     case FGMM_OPT_DECODE_ROUND0:
         if (!(value == 0 || value == 16 || value == 32))
             return fail(h, FGMM_ERR_INVALID_ARG, "decode first-round points must be 0 (auto), 16 or 32");

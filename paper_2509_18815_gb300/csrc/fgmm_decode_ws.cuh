@@ -148,6 +148,7 @@ struct WsFuseDev {
     uint32_t adv_c, adv_h, adv_r;   // pass 1's S = adv_c per_n + adv_h W + adv_r
     const int32_t* ya;      // pass 0's output: the decoded anchors
     uint32_t* arrivals;     // [pass 0's steps]: pass-0 CTAs that completed the step
+    int silent_arrivals;    // test hook: pass-0 CTAs count no steps
 };
 
 // The context warp's lane q follows column i = u S + nbase + q of pass 1
@@ -250,18 +251,29 @@ __device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p)
     return v;
 }
 
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+constexpr uint64_t kArrivalWaitNs = 2000000000ull;   // a wait for anchors gives up after 2 s
+
 // Waits (warp-wide, bounded) until pass 0 has completed `need` steps, seen
 // being the count already established. The acquire is lane 0's read of the
 // step's arrival count; __syncwarp then orders the other lanes' later reads
-// of the anchors after it. On giving up: FGMM_ERR_TIMEOUT and the cluster's
-// abort flag.
+// of the anchors after it. A wait gives up after kArrivalWaitNs of the
+// global timer (polls go to L2, so a poll count would bound the time less
+// well): FGMM_ERR_TIMEOUT and the cluster's abort flag.
 template <int CL>
 __device__ __forceinline__ void ckbd_wait(const WsFuseDev& fz, uint32_t need, uint32_t& seen, uint32_t nprog,
                                           uint32_t* abort_flag, int32_t* err, int lane)
 {
     if (need <= seen) return;
     const volatile uint32_t* va = abort_flag;
-    for (uint32_t spin = 0;; ++spin) {
+    const uint64_t t0 = global_ns();
+    for (;;) {
         uint32_t v = 0;
         if (lane == 0) v = ld_acquire_u32(fz.arrivals + (need - 1));
         v = __shfl_sync(kFull, v, 0);
@@ -271,7 +283,7 @@ __device__ __forceinline__ void ckbd_wait(const WsFuseDev& fz, uint32_t need, ui
             return;
         }
         if (__any_sync(kFull, *va != 0u)) return;
-        if (spin >= kSpinLimit) {
+        if (__shfl_sync(kFull, global_ns() - t0 > kArrivalWaitNs, 0)) {
             if (lane == 0) set_error(err, kErrTimeout);
             if (lane < CL) store_rank(abort_flag, (uint32_t)lane, 1u);
             return;
@@ -386,7 +398,7 @@ __global__ void __launch_bounds__(32 * (32 / CL / SPW + 32 / CL * R0 / 32) + (MO
     const int64_t beg = offsets[g], end = offsets[g + 1];
     if (!(beg >= 0 && end <= n_words && end - beg >= 64)) {
         if (tid == 0 && rank == 0) set_error(err, kErrCorrupt);
-        if (counts)   // every step counted once for this CTA, so that no wait on it runs out
+        if (counts && !fz.silent_arrivals)   // every step counted once for this CTA, so that no wait on it runs out
             for (int64_t u = tid; u < T_steps; u += NT) atomicAdd(fz.arrivals + u, 1u);
         return;
     }
@@ -634,7 +646,7 @@ __global__ void __launch_bounds__(32 * (32 / CL / SPW + 32 / CL * R0 / 32) + (MO
             n += S;
         }
         __syncthreads();   // producers' round for step t + 2 visible; slots read
-        if (counts && xwarp && lane == 0) {   // this step's symbols stored by every consumer of the CTA
+        if (counts && xwarp && lane == 0 && !fz.silent_arrivals) {   // the step's symbols stored by every consumer
             __threadfence();
             atomicAdd(fz.arrivals + t, 1u);
         }
@@ -770,6 +782,7 @@ cudaError_t launch_ws_ckbd_k(const CkbdFuseArgs& a, cudaStream_t st)
     fz.adv_r = rs % fz.W;
     fz.ya = a.pass[0].out;
     fz.arrivals = a.arrivals;
+    fz.silent_arrivals = a.silent_arrivals;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)((a.pass[0].nseg + a.pass[1].nseg) * CL));
     cfg.blockDim = dim3(NT);

@@ -24,6 +24,7 @@ struct fgmm_handle {
     int phi = 0;                       // Phi approximation (FGMM_PHI_*)
     int mlp_act = 0;                   // activation of the proposal network (FGMM_MLP_ACT_*)
     int ckbd_clusters[5] = {-1, -1, -1, -1, -1};   // fused two-pass decode: resident clusters per K (-1 unknown)
+    int test_silent_arrivals = 0;      // test hook: the fused two-pass decode's anchor CTAs count no steps
     std::string last_error;
 };
 
@@ -104,6 +105,7 @@ struct CkbdFuseArgs {
     DecodeArgs pass[2];
     int64_t C, H, W;
     uint32_t* arrivals;
+    int silent_arrivals = 0;   // test hook: the anchor CTAs count no steps
 };
 cudaError_t launch_ws_ckbd(const CkbdFuseArgs& a, int K, cudaStream_t st);
 // Clusters of launch_ws_ckbd's kernel that the current device holds at once:

@@ -4,6 +4,7 @@ stand-in context (bit-exact, fp32 and bf16 hyperprior parameters), the two
 streams of the two-pass encode (byte-identical) and the two-pass decode,
 both as one fused launch and as separate calls."""
 import ctypes
+import time
 
 import numpy as np
 import pytest
@@ -244,3 +245,33 @@ def test_fused_two_pass_decode_from_cuda_graph():
     for _ in range(2):
         gr.y.fill_(-3)
         np.testing.assert_array_equal(gr.decode().cpu().numpy(), lat.symbols)
+
+
+def test_fused_two_pass_decode_wait_times_out_and_recovers():
+    """With the anchor CTAs counting none of their steps (a test hook), the
+    non-anchor waits for decoded anchors run out after about two seconds:
+    the launch records FGMM_ERR_TIMEOUT, releases the other waits and
+    returns, and the next decode on the same handle is exact."""
+    codec = _codec()
+    from paper_2509_18815_gb300 import _abi
+    from paper_2509_18815_gb300._abi import FGMM_ERR_TIMEOUT, FgmmError
+    shape, Sa, Sn = (5, 9, 13), 320, 320   # 20 segments: the fused launch, one step per pass
+    lat = synth.make_ckbd_latent(*shape, 3, seed=1030)
+    dp = dev_params(lat.params)
+    first, second = _oracle_streams(lat, shape, Sa, Sn)
+    h = codec.Handle()
+    try:
+        assert codec.ckbd_decode_fused(3, torch.float32, shape, Sa, Sn, h=h)
+        h.check(_abi.fgmm_set_option(h.ptr, _abi.FGMM_OPT_TEST_SILENT_ARRIVALS, 1))
+        t0 = time.monotonic()
+        with pytest.raises(FgmmError) as e:
+            codec.ckbd_decode(dp, first, second, shape, Sa, Sn, h=h)
+        assert e.value.status == FGMM_ERR_TIMEOUT
+        assert time.monotonic() - t0 < 30.0
+        h.check(_abi.fgmm_set_option(h.ptr, _abi.FGMM_OPT_TEST_SILENT_ARRIVALS, 0))
+        y = codec.ckbd_decode(dp, first, second, shape, Sa, Sn, h=h)
+        np.testing.assert_array_equal(y.cpu().numpy(), lat.symbols)
+        with pytest.raises(FgmmError):
+            h.check(_abi.fgmm_set_option(h.ptr, _abi.FGMM_OPT_TEST_SILENT_ARRIVALS, 2))
+    finally:
+        h.close()
