@@ -270,8 +270,8 @@ fgmm_status fgmm_ckbd_context(fgmm_handle *h, const fgmm_latent *lat, int64_t C,
  * latent's symbols to y (device int32 [N]). The same symbols as fgmm_ckbd_split,
  * fgmm_decode of the anchors, fgmm_ckbd_merge, fgmm_ckbd_context,
  * fgmm_decode of the non-anchors and fgmm_ckbd_merge, which it runs when it
- * cannot do better. It does better for fp32 parameters and the A&S
- * approximation when the automatic decoder plan of the Sa / 32 + Sn / 32
+ * cannot do better. It does better (fp32 or bf16 parameters, the A&S
+ * approximation) when the automatic decoder plan of the Sa / 32 + Sn / 32
  * segments is the warp-specialised decoder with 16 lanes per stream,
  * clusters of 4 and a 16-point first round, every cluster fits on the
  * device at once, each pass has fewer than 2^24 steps, C H W < 2^31, and

@@ -133,8 +133,8 @@ fgmm_status check_geom(fgmm_handle* h, int64_t C, int64_t H, int64_t W)
     return FGMM_OK;
 }
 
-// Whether fgmm_ckbd_decode runs both passes in one launch: fp32
-// parameters, the A&S approximation, no decoder option or test hook, the
+// Whether fgmm_ckbd_decode runs both passes in one launch: the A&S
+// approximation, no decoder option or test hook, the
 // automatic plan of the combined segments is the fused kernel's (16 lanes,
 // clusters of 4, 16-point first round), every cluster resident at once,
 // fewer than 2^24 steps per pass and C H W < 2^31.
@@ -144,7 +144,7 @@ fgmm_status ckbd_fusable(fgmm_handle* h, int K, int dtype, int64_t C, int64_t H,
     *fuse = false;
     const Geom g = make_geom(C, H, W);
     const int64_t Na = g.C * g.per_a, Nn = g.C * g.per_n;
-    if (dtype != FGMM_DTYPE_F32 || h->phi != FGMM_PHI_AS || h->decode_lanes != 0 || h->decode_cluster != 0 ||
+    if (h->phi != FGMM_PHI_AS || h->decode_lanes != 0 || h->decode_cluster != 0 ||
         h->decode_round0 != 0 || h->test_silent_stream >= 0 || Na == 0 || Nn == 0 ||
         steps_of(Na, Sa) >= ((int64_t)1 << 24) || steps_of(Nn, Sn) >= ((int64_t)1 << 24) ||
         g.N >= ((int64_t)1 << 31))
@@ -153,13 +153,14 @@ fgmm_status ckbd_fusable(fgmm_handle* h, int K, int dtype, int64_t C, int64_t H,
     int lanes = 1, cluster = 1, round0 = 0, kernel = 0;
     decode_resolve(nseg, h->num_sms, 0, 0, 0, FGMM_PHI_AS, &lanes, &cluster, &round0, &kernel);
     if (!(kernel == FGMM_DEC_WS && lanes == 16 && cluster == 4 && round0 == 16)) return FGMM_OK;
-    if (h->ckbd_clusters[K] < 0) {
+    const int di = dtype == FGMM_DTYPE_BF16 ? 1 : 0;
+    if (h->ckbd_clusters[di][K] < 0) {
         int n = 0;
-        cudaError_t e = ws_ckbd_capacity(K, &n);
+        cudaError_t e = ws_ckbd_capacity(K, dtype, &n);
         if (e != cudaSuccess) return cuda_fail(h, e, "checkerboard decode: occupancy query");
-        h->ckbd_clusters[K] = n;
+        h->ckbd_clusters[di][K] = n;
     }
-    *fuse = nseg <= h->ckbd_clusters[K];
+    *fuse = nseg <= h->ckbd_clusters[di][K];
     return FGMM_OK;
 }
 
@@ -273,7 +274,8 @@ fgmm_status fgmm_ckbd_decode(fgmm_handle* h, const fgmm_latent* lat, int64_t C, 
     const int K = lat->K;
     const size_t esz = lat->dtype == FGMM_DTYPE_BF16 ? 2 : 4;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    // workspace: anchor params [3K][Na] | non-anchor params [3K][Nn] fp32 |
+    // workspace: anchor params [3K][Na] | non-anchor params [3K][Nn] (room
+    // for fp32: lat's dtype in one launch, the context's fp32 otherwise) |
     // anchors [Na] | non-anchors [Nn] | pass-0 step arrivals [steps]
     const size_t b_pa = align_up(3 * (size_t)K * Na * esz, 256), b_pn = align_up(3 * (size_t)K * Nn * 4, 256);
     const size_t b_ya = align_up(4 * (size_t)Na, 256), b_yn = align_up(4 * (size_t)Nn, 256);
@@ -311,10 +313,15 @@ fgmm_status fgmm_ckbd_decode(fgmm_handle* h, const fgmm_latent* lat, int64_t C, 
     if (s != FGMM_OK) return s;
     const unsigned grid = grid_for(g.N, h->num_sms);
     cudaError_t e;
-    if (fuse) {
-        fgmm_ckbd_split_kernel<uint32_t><<<grid, 256, 0, st>>>(g, K, static_cast<const uint32_t*>(lat->params),
-                                                               nullptr, static_cast<uint32_t*>(pa), nullptr,
-                                                               reinterpret_cast<uint32_t*>(pn), nullptr);
+    if (fuse) {   // the hyperprior parameters of both classes, in lat's dtype
+        if (lat->dtype == FGMM_DTYPE_BF16)
+            fgmm_ckbd_split_kernel<uint16_t><<<grid, 256, 0, st>>>(g, K, static_cast<const uint16_t*>(lat->params),
+                                                                   nullptr, static_cast<uint16_t*>(pa), nullptr,
+                                                                   reinterpret_cast<uint16_t*>(pn), nullptr);
+        else
+            fgmm_ckbd_split_kernel<uint32_t><<<grid, 256, 0, st>>>(g, K, static_cast<const uint32_t*>(lat->params),
+                                                                   nullptr, static_cast<uint32_t*>(pa), nullptr,
+                                                                   reinterpret_cast<uint32_t*>(pn), nullptr);
         e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaMemsetAsync(arrivals, 0, 4 * (size_t)da.T, st);
         if (e == cudaSuccess) {
@@ -329,7 +336,7 @@ fgmm_status fgmm_ckbd_decode(fgmm_handle* h, const fgmm_latent* lat, int64_t C, 
             fa.W = W;
             fa.arrivals = arrivals;
             fa.silent_arrivals = h->test_silent_arrivals;
-            e = launch_ws_ckbd(fa, K, st);
+            e = launch_ws_ckbd(fa, K, lat->dtype, st);
         }
         if (e == cudaSuccess) {
             fgmm_ckbd_merge_kernel<<<grid, 256, 0, st>>>(g, ya, yn, y);

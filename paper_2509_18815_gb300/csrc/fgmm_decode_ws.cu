@@ -9,24 +9,14 @@ cudaError_t launch_ws_f32(const DecodeArgs& a, int K, int CL, int SPW, cudaStrea
     return launch_ws_t<float>(a, K, CL, SPW, st);
 }
 
-cudaError_t ws_ckbd_capacity(int K, int* clusters)
+cudaError_t ws_ckbd_capacity(int K, int dtype, int* clusters)
 {
-    switch (K) {
-    case 1: return ws_ckbd_capacity_k<1>(clusters);
-    case 2: return ws_ckbd_capacity_k<2>(clusters);
-    case 3: return ws_ckbd_capacity_k<3>(clusters);
-    default: return ws_ckbd_capacity_k<4>(clusters);
-    }
+    return dtype == FGMM_DTYPE_BF16 ? ws_ckbd_capacity_bf16(K, clusters) : ws_ckbd_capacity_t<float>(K, clusters);
 }
 
-cudaError_t launch_ws_ckbd(const CkbdFuseArgs& a, int K, cudaStream_t st)
+cudaError_t launch_ws_ckbd(const CkbdFuseArgs& a, int K, int dtype, cudaStream_t st)
 {
-    switch (K) {
-    case 1: return launch_ws_ckbd_k<1>(a, st);
-    case 2: return launch_ws_ckbd_k<2>(a, st);
-    case 3: return launch_ws_ckbd_k<3>(a, st);
-    default: return launch_ws_ckbd_k<4>(a, st);
-    }
+    return dtype == FGMM_DTYPE_BF16 ? launch_ws_ckbd_bf16(a, K, st) : launch_ws_ckbd_t<float>(a, K, st);
 }
 
 }  // namespace fgmm

@@ -715,25 +715,26 @@ int ws_stage_mode(const void* p, int64_t N)
 }
 
 // The checkerboard's two passes in one launch: 16 lanes per stream,
-// clusters of 4, a 16-point first round, fp32 parameters; pass 1's
+// clusters of 4, a 16-point first round, fp32 or bf16 hyperprior
+// parameters (the context is applied to their fp32 values); pass 1's
 // context slots follow the words in shared memory. The host runs it only
 // when every cluster fits on the device at once (ws_ckbd_capacity).
-template <int K>
+template <int K, typename T>
 struct WsCkbdShape {
     static constexpr int CL = 4, SPW = 2, R0 = 16, SPC = 32 / CL;
     static constexpr int NT = 32 * (SPC / SPW + SPC * R0 / 32) + 32;   // + the context warp
-    static constexpr size_t smem = sizeof(PreStep<K>) * kPre * SPC + sizeof(float) * kRing * 3 * K * SPC +
+    static constexpr size_t smem = sizeof(PreStep<K>) * kPre * SPC + sizeof(T) * kRing * 3 * K * SPC +
                                    sizeof(uint32_t) * 68 + sizeof(uint16_t) * kWordCap + sizeof(float2) * kRing * SPC;
-    static_assert((sizeof(PreStep<K>) * kPre * SPC + sizeof(float) * kRing * 3 * K * SPC + sizeof(uint32_t) * 68 +
+    static_assert((sizeof(PreStep<K>) * kPre * SPC + sizeof(T) * kRing * 3 * K * SPC + sizeof(uint32_t) * 68 +
                    sizeof(uint16_t) * kWordCap) % 8 == 0, "context slots 8-byte aligned");
 };
 
 // Clusters of the fused launch that the current device holds at once.
-template <int K>
+template <int K, typename T>
 cudaError_t ws_ckbd_capacity_k(int* clusters)
 {
-    using Sh = WsCkbdShape<K>;
-    auto kern = fgmm_dec_ws_kernel<K, float, Sh::CL, Sh::SPW, Sh::R0, 1>;
+    using Sh = WsCkbdShape<K, T>;
+    auto kern = fgmm_dec_ws_kernel<K, T, Sh::CL, Sh::SPW, Sh::R0, 1>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::smem);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
@@ -750,22 +751,22 @@ cudaError_t ws_ckbd_capacity_k(int* clusters)
     return cudaOccupancyMaxActiveClusters(clusters, kern, &cfg);
 }
 
-template <int K>
+template <int K, typename T>
 cudaError_t launch_ws_ckbd_k(const CkbdFuseArgs& a, cudaStream_t st)
 {
-    using Sh = WsCkbdShape<K>;
+    using Sh = WsCkbdShape<K, T>;
     constexpr int CL = Sh::CL, SPW = Sh::SPW, R0 = Sh::R0, SPC = Sh::SPC, NT = Sh::NT;
     constexpr size_t smem = Sh::smem;
     for (int p = 0; p < 2; ++p)
         if (a.pass[p].T >= ((int64_t)1 << 24)) return cudaErrorInvalidValue;
-    auto kern = fgmm_dec_ws_kernel<K, float, CL, SPW, R0, 1>;
+    auto kern = fgmm_dec_ws_kernel<K, T, CL, SPW, R0, 1>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     if (a.C * a.H * a.W >= ((int64_t)1 << 31)) return cudaErrorInvalidValue;
     WsFuseDev fz = {};
     for (int p = 0; p < 2; ++p) {
         const DecodeArgs& d = a.pass[p];
-        fz.pass[p] = WsPassDev{d.params, d.N, d.S, ws_stage_mode<float, SPC>(d.params, d.N), d.T, d.words, d.n_words,
+        fz.pass[p] = WsPassDev{d.params, d.N, d.S, ws_stage_mode<T, SPC>(d.params, d.N), d.T, d.words, d.n_words,
                                d.offsets, d.out};
     }
     fz.nseg0 = a.pass[0].nseg;
@@ -796,8 +797,30 @@ cudaError_t launch_ws_ckbd_k(const CkbdFuseArgs& a, cudaStream_t st)
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     const DecodeArgs& d0 = a.pass[0];
-    return cudaLaunchKernelEx(&cfg, kern, static_cast<const float*>(d0.params), d0.N, d0.S, d0.T, d0.words,
+    return cudaLaunchKernelEx(&cfg, kern, static_cast<const T*>(d0.params), d0.N, d0.S, d0.T, d0.words,
                               d0.n_words, d0.offsets, d0.out, d0.err, d0.stats, 0, d0.silent, fz);
+}
+
+template <typename T>
+cudaError_t ws_ckbd_capacity_t(int K, int* clusters)
+{
+    switch (K) {
+    case 1: return ws_ckbd_capacity_k<1, T>(clusters);
+    case 2: return ws_ckbd_capacity_k<2, T>(clusters);
+    case 3: return ws_ckbd_capacity_k<3, T>(clusters);
+    default: return ws_ckbd_capacity_k<4, T>(clusters);
+    }
+}
+
+template <typename T>
+cudaError_t launch_ws_ckbd_t(const CkbdFuseArgs& a, int K, cudaStream_t st)
+{
+    switch (K) {
+    case 1: return launch_ws_ckbd_k<1, T>(a, st);
+    case 2: return launch_ws_ckbd_k<2, T>(a, st);
+    case 3: return launch_ws_ckbd_k<3, T>(a, st);
+    default: return launch_ws_ckbd_k<4, T>(a, st);
+    }
 }
 
 template <int K, typename T, int SPW, int R0>

@@ -23,7 +23,8 @@ struct fgmm_handle {
     int test_silent_stream = -1;       // test hook: a stream of segment 0 that posts no refill flags
     int phi = 0;                       // Phi approximation (FGMM_PHI_*)
     int mlp_act = 0;                   // activation of the proposal network (FGMM_MLP_ACT_*)
-    int ckbd_clusters[5] = {-1, -1, -1, -1, -1};   // fused two-pass decode: resident clusters per K (-1 unknown)
+    int ckbd_clusters[2][5] = {{-1, -1, -1, -1, -1}, {-1, -1, -1, -1, -1}};   // fused two-pass decode: resident
+                                                                              // clusters per dtype and K (-1 unknown)
     int test_silent_arrivals = 0;      // test hook: the fused two-pass decode's anchor CTAs count no steps
     std::string last_error;
 };
@@ -94,8 +95,8 @@ struct DecodeArgs {
 };
 void decode_config_auto(int64_t nseg, int num_sms, int* lanes, int* cluster, int* round0);
 // Checkerboard two-pass decode in one launch of the warp-specialised decoder
-// (fp32 parameters, 16 lanes per stream, clusters of 4 CTAs, 16-point first
-// round): clusters 0 .. nseg0-1 decode the anchors (pass[0], parameters
+// (fp32 or bf16 parameters, 16 lanes per stream, clusters of 4 CTAs,
+// 16-point first round): clusters 0 .. nseg0-1 decode the anchors (pass[0], parameters
 // = the anchors' hyperprior parameters), the rest the non-anchors (pass[1],
 // parameters = the non-anchors' hyperprior parameters, to which the
 // stand-in context is applied on the fly from pass 0's decoded anchors,
@@ -107,11 +108,13 @@ struct CkbdFuseArgs {
     uint32_t* arrivals;
     int silent_arrivals = 0;   // test hook: the anchor CTAs count no steps
 };
-cudaError_t launch_ws_ckbd(const CkbdFuseArgs& a, int K, cudaStream_t st);
+cudaError_t launch_ws_ckbd(const CkbdFuseArgs& a, int K, int dtype, cudaStream_t st);
+cudaError_t launch_ws_ckbd_bf16(const CkbdFuseArgs& a, int K, cudaStream_t st);
 // Clusters of launch_ws_ckbd's kernel that the current device holds at once:
 // the fused launch runs only when all of them fit, so that every pass-1
 // cluster's wait is on pass-0 clusters that are resident.
-cudaError_t ws_ckbd_capacity(int K, int* clusters);
+cudaError_t ws_ckbd_capacity(int K, int dtype, int* clusters);
+cudaError_t ws_ckbd_capacity_bf16(int K, int* clusters);
 // Warp-specialised decoder for fp32 / bf16 parameters: CL CTAs per segment,
 // SPW streams per consumer warp (1, 2 or 4).
 cudaError_t launch_ws_f32(const DecodeArgs& a, int K, int CL, int SPW, cudaStream_t st);

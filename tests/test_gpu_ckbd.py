@@ -145,17 +145,19 @@ FUSED = [((16, 32, 48), 512, 512), ((8, 16, 24), 160, 192), ((5, 9, 13), 320, 32
          ((2, 1, 5), 160, 160), ((24, 20, 30), 64, 1088), ((64, 64, 96), 1024, 1024)]
 
 
+@pytest.mark.parametrize("bf16", [False, True])
 @pytest.mark.parametrize("shape,Sa,Sn", FUSED)
-def test_fused_two_pass_decode(shape, Sa, Sn):
+def test_fused_two_pass_decode(shape, Sa, Sn, bf16):
     """fgmm_ckbd_decode of the oracle's two streams gives the latent's
     symbols, in one launch where its plan says so, and the same symbols as
-    the separate calls (integer output: equality)."""
+    the separate calls (integer output: equality); fp32 and bf16
+    hyperprior parameters."""
     codec = _codec()
     lat = synth.make_ckbd_latent(*shape, 3, seed=970 + Sa + Sn + sum(shape))
-    dp = dev_params(lat.params)
-    first, second = _oracle_streams(lat, shape, Sa, Sn)
+    dp = dev_params(lat.params, bf16)
+    first, second = _oracle_streams(lat, shape, Sa, Sn, bf16)
     nseg = Sa // 32 + Sn // 32
-    fused = codec.ckbd_decode_fused(3, torch.float32, shape, Sa, Sn)
+    fused = codec.ckbd_decode_fused(3, torch.bfloat16 if bf16 else torch.float32, shape, Sa, Sn)
     if 10 <= nseg <= 32 and torch.cuda.get_device_properties(0).multi_processor_count >= 128:
         assert fused
     for _ in range(2):
@@ -179,13 +181,17 @@ def test_fused_two_pass_decode_components(K):
 
 
 def test_two_pass_decode_plan():
-    """Cases outside the fused launch: bf16 parameters, too few segments for
-    its plan, a decoder option set; and argument errors."""
+    """Cases outside the fused launch: too few segments for its plan, a
+    decoder option set, another Phi approximation; and argument errors."""
     codec = _codec()
     from paper_2509_18815_gb300 import _abi
     from paper_2509_18815_gb300._abi import FGMM_ERR_INVALID_ARG
-    assert not codec.ckbd_decode_fused(3, torch.bfloat16, (16, 32, 48), 512, 512)
+    assert codec.ckbd_decode_fused(3, torch.bfloat16, (16, 32, 48), 512, 512)
     assert not codec.ckbd_decode_fused(3, torch.float32, (4, 16, 16), 32, 64)
+    hp = codec.Handle()
+    hp.check(_abi.fgmm_set_option(hp.ptr, _abi.FGMM_OPT_PHI, _abi.FGMM_PHI_LOGISTIC))
+    assert not codec.ckbd_decode_fused(3, torch.float32, (16, 32, 48), 512, 512, h=hp)
+    hp.close()
     h = codec.Handle()
     h.check(_abi.fgmm_set_option(h.ptr, _abi.FGMM_OPT_DECODE_LANES, 16))
     assert not codec.ckbd_decode_fused(3, torch.float32, (16, 32, 48), 512, 512, h=h)
