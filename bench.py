@@ -472,6 +472,16 @@ def ckbd_case(dev, h, flush, reps):
     assert torch.equal(y_s, dy)
     td_steps = _events_ms(lambda: g_s.replay(), reps, flush)
     h.sync()
+    # the encode as its separate calls (split, context, two encodes), in a graph
+    g_e = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g_e, capture_error_mode="thread_local"):
+        enc_s = codec.ckbd_encode_steps(dp, dy, shape, Sa, Sn, h=h, sync=False)
+    g_e.replay()
+    h.sync()
+    assert torch.equal(enc_s[0][0][: int(enc_s[0][2].item())], first[0])
+    assert torch.equal(enc_s[1][0][: int(enc_s[1][2].item())], second[0])
+    te_steps = _events_ms(lambda: g_e.replay(), reps, flush)
+    h.sync()
     w1, o1 = codec.encode(dp, dy, 1024, h=h)
     out = torch.empty(N, dtype=torch.int32, device=dev)
     td1 = _events_ms(lambda: codec.decode(dp, w1, o1, 1024, h=h, out=out, sync=False), reps, flush)
@@ -483,14 +493,16 @@ def ckbd_case(dev, h, flush, reps):
     bits2 = 16.0 * (first[0].numel() + second[0].numel())
     return {"symbols": N, "S_per_pass": [Sa, Sn], "ms_encode": te, "ms_decode": td,
             "encode_msym_s": N / te / 1e3, "decode_msym_s": N / td / 1e3, "one_pass_ms_decode": td1,
-            "decode_fused": fused, "ms_decode_separate_calls": td_steps,
+            "decode_fused": fused, "ms_decode_separate_calls": td_steps, "ms_encode_separate_calls": te_steps,
             "host_launched": {"ms_encode": te_host, "ms_decode": td_host},
             "ideal_bits_per_symbol_one_pass": ideal1 / N, "ideal_bits_per_symbol_two_pass": (ia + inn) / N,
             "coded_bits_per_symbol_two_pass": bits2 / N,
-            "note": "each direction replayed from one CUDA graph: encode = split, context, two coder passes; "
-                    "decode = fgmm_ckbd_decode (split, both passes in one launch with the context applied as "
-                    "pass 2 loads its parameters, merge); ms_decode_separate_calls: split, pass 1, merge, "
-                    "context, pass 2, merge as separate launches (host_launched: the calls launched one by one)"}
+            "note": "each direction replayed from one CUDA graph: encode = fgmm_ckbd_encode (both passes' "
+                    "intervals with split and context in one kernel, both rANS encoders in one launch, scans, "
+                    "compactions); decode = fgmm_ckbd_decode (split, both passes in one launch with the context "
+                    "applied as pass 2 loads its parameters, merge); *_separate_calls: split, context and two "
+                    "encodes / split, pass 1, merge, context, pass 2, merge as separate launches in a graph "
+                    "(host_launched: the one-call entries launched from the host)"}
 
 
 def proposal_case(dev, h, alu_peak_tops, reps=3, n_train=10_000_000, n_latents=16, train_scale=1.0):

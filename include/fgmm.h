@@ -262,6 +262,21 @@ fgmm_status fgmm_ckbd_merge(fgmm_handle *h, int64_t C, int64_t H, int64_t W, con
 fgmm_status fgmm_ckbd_context(fgmm_handle *h, const fgmm_latent *lat, int64_t C, int64_t H, int64_t W,
                               const int32_t *y, float *params_n, void *stream);
 
+/* The whole two-pass encode in one call: from the hyperprior parameters lat
+ * (N = C H W) and the symbols y (device int32 [N]), the anchors' streams
+ * (Sa streams, coded with the anchors' hyperprior parameters) into
+ * words_a / offsets_a / *n_words_a, and the non-anchors' (Sn streams, coded
+ * with fgmm_ckbd_context's parameters) into words_n / offsets_n /
+ * *n_words_n, each as fgmm_encode writes them (the same bytes as
+ * fgmm_ckbd_split, fgmm_ckbd_context and two fgmm_encode calls). One kernel
+ * computes both passes' intervals (the split and the context included),
+ * one launch runs both passes' rANS encoders. Capacities and errors as for
+ * fgmm_encode; honours FGMM_OPT_PHI. Uses the handle's workspace. */
+fgmm_status fgmm_ckbd_encode(fgmm_handle *h, const fgmm_latent *lat, int64_t C, int64_t H, int64_t W,
+                             const int32_t *y, int32_t Sa, uint16_t *words_a, int64_t words_cap_a, int64_t *offsets_a,
+                             int64_t *n_words_a, int32_t Sn, uint16_t *words_n, int64_t words_cap_n,
+                             int64_t *offsets_n, int64_t *n_words_n, void *stream);
+
 /* The whole two-pass decode in one call: from the hyperprior parameters lat
  * (N = C H W) and the two passes' streams (words_a / offsets_a of the
  * anchors coded with Sa streams from the anchors' hyperprior parameters;

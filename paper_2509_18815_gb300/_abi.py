@@ -84,6 +84,7 @@ SIGNATURES = {
     "fgmm_ckbd_split": (I32, [P, LATP, I64, I64, I64, P, P, P, P, P, P]),
     "fgmm_ckbd_merge": (I32, [P, I64, I64, I64, P, P, P, P]),
     "fgmm_ckbd_context": (I32, [P, LATP, I64, I64, I64, P, P, P]),
+    "fgmm_ckbd_encode": (I32, [P, LATP, I64, I64, I64, P, I32, P, I64, P, P, I32, P, I64, P, P, P]),
     "fgmm_ckbd_decode": (I32, [P, LATP, I64, I64, I64, P, I64, P, I32, P, I64, P, I32, P, P]),
     "fgmm_ckbd_decode_plan": (I32, [P, I32, I32, I64, I64, I64, I32, I32, P]),
     "fgmm_gsm_tables_bytes": (I64, []),

@@ -391,13 +391,41 @@ def ckbd_context(params, y, shape, out=None, h: Handle | None = None):
     return out
 
 
-def ckbd_encode(params, y, shape, Sa: int, Sn: int, h: Handle | None = None):
-    """Two-pass encode: anchors with the hyperprior's parameters, then the
-    non-anchors with the context's. -> ((words, offsets), (words, offsets))."""
+def ckbd_encode(params, y, shape, Sa: int, Sn: int, h: Handle | None = None, sync: bool = True):
+    """Two-pass encode (fgmm_ckbd_encode): anchors with the hyperprior's
+    parameters, then the non-anchors with the context's.
+    -> ((words, offsets), (words, offsets)); with sync=False the untrimmed
+    buffers, offsets and device totals of each pass, unsynchronised."""
+    h = h or handle(params.device)
+    lat = latent(params)
+    C, H, W = shape
+    na = int(_abi.fgmm_ckbd_anchors(C, H, W))
+    nn = C * H * W - na
+    yv = y.to(torch.int32).contiguous()
+    out = []
+    for n, S in ((na, Sa), (nn, Sn)):
+        cap = encode_bound_words(n, S)
+        if cap < 0:
+            raise ValueError("S must be a positive multiple of 32")
+        out.append((torch.empty(max(cap, 1), dtype=torch.int16, device=params.device),
+                    torch.empty(S // 32 + 1, dtype=torch.int64, device=params.device),
+                    torch.empty(1, dtype=torch.int64, device=params.device), cap))
+    (wa, oa, ta, ca), (wn, on, tn, cn) = out
+    h.check(_abi.fgmm_ckbd_encode(h.ptr, ctypes.byref(lat), C, H, W, _ptr(yv), Sa, _ptr(wa), ca, _ptr(oa), _ptr(ta),
+                                  Sn, _ptr(wn), cn, _ptr(on), _ptr(tn), _stream()))
+    if not sync:
+        return (wa, oa, ta), (wn, on, tn)
+    h.sync()
+    return (wa[: int(ta.item())], oa), (wn[: int(tn.item())], on)
+
+
+def ckbd_encode_steps(params, y, shape, Sa: int, Sn: int, h: Handle | None = None, sync: bool = True):
+    """The two-pass encode as its separate library calls: split, context,
+    two encodes (the same bytes as ckbd_encode)."""
     h = h or handle(params.device)
     pa, ya, _, yn = ckbd_split(params, y, shape, h)
     pn = ckbd_context(params, y.to(torch.int32).contiguous(), shape, h=h)
-    return encode(pa, ya, Sa, h), encode(pn, yn, Sn, h)
+    return encode(pa, ya, Sa, h, sync=sync), encode(pn, yn, Sn, h, sync=sync)
 
 
 def ckbd_decode(params, first, second, shape, Sa: int, Sn: int, h: Handle | None = None, sync: bool = True,
@@ -447,8 +475,7 @@ def ckbd_decode_fused(K: int, dtype, shape, Sa: int, Sn: int, h: Handle | None =
 
 class CkbdGraphs:
     """Checkerboard two-pass coding of one latent shape replayed from CUDA
-    graphs. The encode sequence (anchor/non-anchor split, the stand-in
-    context, the two passes' encodes) and the decode sequence
+    graphs. The encode sequence (fgmm_ckbd_encode) and the decode sequence
     (fgmm_ckbd_decode) are each captured once with fixed buffers; every node
     of a replay is a library kernel, and the graphs remove the host's
     per-launch work and the gaps between kernels. params: [3, K, C H W] on
@@ -470,9 +497,7 @@ class CkbdGraphs:
         self._y_in = self._first = None
 
     def _encode_seq(self, y):
-        pa, ya, _, yn = ckbd_split(self.params, y, self.shape, self.h)
-        pn = ckbd_context(self.params, y, self.shape, h=self.h)
-        return (encode(pa, ya, self.Sa, self.h, sync=False), encode(pn, yn, self.Sn, self.h, sync=False))
+        return ckbd_encode(self.params, y, self.shape, self.Sa, self.Sn, self.h, sync=False)
 
     def _decode_seq(self):
         return ckbd_decode(self.params, self._first, self._second, self.shape, self.Sa, self.Sn, self.h, sync=False)

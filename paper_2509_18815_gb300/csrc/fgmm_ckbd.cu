@@ -25,6 +25,7 @@
 
 #include "fgmm_device.cuh"
 #include "fgmm_internal.h"
+#include "fgmm_segment.cuh"
 
 using namespace fgmm;
 
@@ -119,6 +120,77 @@ __global__ void __launch_bounds__(256) fgmm_ckbd_context_kernel(Geom g, int K, c
     }
 }
 
+// Both passes' intervals in one pass over the latent (the split, the
+// stand-in context and the interval kernel of the separate calls): symbol n
+// of class c at index i gets sf_c[i] = start | freq << 16 of its quantised-
+// CDF interval under the anchors' hyperprior parameters, or under the
+// context's parameters for a non-anchor (computed from the hyperprior
+// parameters widened to fp32 and the neighbours in y, as the context kernel
+// does), and y_c[i] = y[n].
+template <int K, typename T, int PHI>
+__global__ void __launch_bounds__(256) fgmm_ckbd_interval_kernel(Geom g, const T* __restrict__ params,
+                                                                 const int32_t* __restrict__ y,
+                                                                 uint32_t* __restrict__ sf_a, int32_t* __restrict__ y_a,
+                                                                 uint32_t* __restrict__ sf_n, int32_t* __restrict__ y_n,
+                                                                 int32_t* err)
+{
+    for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < g.N; n += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i;
+        const bool anchor = ckbd_index(g, n, i);
+        RawParams<K> r;
+#pragma unroll
+        for (int q = 0; q < 3 * K; ++q) r.v[q] = load_param(params, (int64_t)q * g.N + n);
+        const int32_t s = __ldg(y + n);
+        if (!anchor) {
+            const int64_t rr = n % (g.H * g.W), h = rr / g.W, w = rr - h * g.W;
+            int64_t ctx = 0;
+            int cnt = 0;
+            if (h > 0) { ctx += __ldg(y + n - g.W); ++cnt; }
+            if (h + 1 < g.H) { ctx += __ldg(y + n + g.W); ++cnt; }
+            if (w > 0) { ctx += __ldg(y + n - 1); ++cnt; }
+            if (w + 1 < g.W) { ctx += __ldg(y + n + 1); ++cnt; }
+            const float fc = __ll2float_rn(ctx), fn = -(float)cnt;
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                const float mu = r.v[K + k];
+                r.v[K + k] = __fmaf_rn(0.125f, __fmaf_rn(fn, mu, fc), mu);
+                r.v[2 * K + k] = __fmul_rn(r.v[2 * K + k], 0.75f);
+            }
+        }
+        Mix<K> m;
+        if (!mix_from_params<K>(r, m)) set_error(err, kErrBadParams);
+        uint32_t st, fr;
+        interval_of<K, PHI>(m, s, st, fr);
+        (anchor ? sf_a : sf_n)[i] = st | (fr << 16);
+        (anchor ? y_a : y_n)[i] = s;
+    }
+}
+
+template <typename T, int PHI>
+void launch_ckbd_interval_t(const Geom& g, int K, const void* params, const int32_t* y, uint32_t* sf_a, int32_t* y_a,
+                            uint32_t* sf_n, int32_t* y_n, int32_t* err, unsigned grid, cudaStream_t st)
+{
+    const T* p = static_cast<const T*>(params);
+    switch (K) {
+    case 1: fgmm_ckbd_interval_kernel<1, T, PHI><<<grid, 256, 0, st>>>(g, p, y, sf_a, y_a, sf_n, y_n, err); break;
+    case 2: fgmm_ckbd_interval_kernel<2, T, PHI><<<grid, 256, 0, st>>>(g, p, y, sf_a, y_a, sf_n, y_n, err); break;
+    case 3: fgmm_ckbd_interval_kernel<3, T, PHI><<<grid, 256, 0, st>>>(g, p, y, sf_a, y_a, sf_n, y_n, err); break;
+    default: fgmm_ckbd_interval_kernel<4, T, PHI><<<grid, 256, 0, st>>>(g, p, y, sf_a, y_a, sf_n, y_n, err); break;
+    }
+}
+
+template <typename T>
+void launch_ckbd_interval(const Geom& g, int K, int phi, const void* params, const int32_t* y, uint32_t* sf_a,
+                          int32_t* y_a, uint32_t* sf_n, int32_t* y_n, int32_t* err, unsigned grid, cudaStream_t st)
+{
+    if (phi == FGMM_PHI_LOGISTIC)
+        launch_ckbd_interval_t<T, kPhiLogistic>(g, K, params, y, sf_a, y_a, sf_n, y_n, err, grid, st);
+    else if (phi == FGMM_PHI_POLYA)
+        launch_ckbd_interval_t<T, kPhiPolya>(g, K, params, y, sf_a, y_a, sf_n, y_n, err, grid, st);
+    else
+        launch_ckbd_interval_t<T, kPhiAS>(g, K, params, y, sf_a, y_a, sf_n, y_n, err, grid, st);
+}
+
 unsigned grid_for(int64_t N, int sms)
 {
     const int64_t b = (N + 255) / 256;
@@ -167,6 +239,62 @@ fgmm_status ckbd_fusable(fgmm_handle* h, int K, int dtype, int64_t C, int64_t H,
 }  // namespace
 
 extern "C" {
+
+fgmm_status fgmm_ckbd_encode(fgmm_handle* h, const fgmm_latent* lat, int64_t C, int64_t H, int64_t W,
+                             const int32_t* y, int32_t Sa, uint16_t* words_a, int64_t words_cap_a, int64_t* offsets_a,
+                             int64_t* n_words_a, int32_t Sn, uint16_t* words_n, int64_t words_cap_n,
+                             int64_t* offsets_n, int64_t* n_words_n, void* stream)
+{
+    fgmm_status s = check_latent(h, lat);
+    if (s != FGMM_OK) return s;
+    s = check_geom(h, C, H, W);
+    if (s != FGMM_OK) return s;
+    if (lat->N != C * H * W) return fail(h, FGMM_ERR_INVALID_ARG, "fgmm_ckbd_encode: N != C * H * W");
+    if (Sa <= 0 || Sa % 32 != 0 || Sn <= 0 || Sn % 32 != 0)
+        return fail(h, FGMM_ERR_INVALID_ARG, "S must be a positive multiple of 32");
+    if (!offsets_a || !offsets_n || !n_words_a || !n_words_n || words_cap_a < 0 || words_cap_n < 0 ||
+        (words_cap_a > 0 && !words_a) || (words_cap_n > 0 && !words_n) || (lat->N > 0 && !y))
+        return fail(h, FGMM_ERR_INVALID_ARG, "fgmm_ckbd_encode: NULL buffer");
+    const Geom g = make_geom(C, H, W);
+    const int64_t Na = g.C * g.per_a, Nn = g.C * g.per_n;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // workspace: intervals [Na] | [Nn] | symbols [Na] | [Nn] | segment scratch
+    // of pass 1 | of pass 2 | segment lengths of pass 1 | of pass 2
+    const int64_t ga = Sa / 32, gn = Sn / 32;
+    const int64_t cap_a = encode_seg_cap(Na, Sa), cap_n = encode_seg_cap(Nn, Sn);
+    size_t off[9];
+    off[0] = 0;
+    off[1] = align_up(off[0] + 4 * (size_t)Na, 256);
+    off[2] = align_up(off[1] + 4 * (size_t)Nn, 256);
+    off[3] = align_up(off[2] + 4 * (size_t)Na, 256);
+    off[4] = align_up(off[3] + 4 * (size_t)Nn, 256);
+    off[5] = align_up(off[4] + 2 * (size_t)(ga * cap_a), 256);
+    off[6] = align_up(off[5] + 2 * (size_t)(gn * cap_n), 256);
+    off[7] = align_up(off[6] + 8 * (size_t)ga, 256);
+    off[8] = off[7] + 8 * (size_t)gn;
+    s = ws_reserve(h, off[8], st);
+    if (s != FGMM_OK) return s;
+    char* base = static_cast<char*>(h->ws);
+    uint32_t* sf_a = reinterpret_cast<uint32_t*>(base + off[0]);
+    uint32_t* sf_n = reinterpret_cast<uint32_t*>(base + off[1]);
+    int32_t* y_a = reinterpret_cast<int32_t*>(base + off[2]);
+    int32_t* y_n = reinterpret_cast<int32_t*>(base + off[3]);
+    if (g.N > 0) {
+        const unsigned grid = grid_for(g.N, h->num_sms);
+        if (lat->dtype == FGMM_DTYPE_BF16)
+            launch_ckbd_interval<__nv_bfloat16>(g, lat->K, h->phi, lat->params, y, sf_a, y_a, sf_n, y_n, h->d_err,
+                                                grid, st);
+        else
+            launch_ckbd_interval<float>(g, lat->K, h->phi, lat->params, y, sf_a, y_a, sf_n, y_n, h->d_err, grid, st);
+    }
+    EncPass pa{sf_a, y_a, Na, Sa, reinterpret_cast<uint16_t*>(base + off[4]), reinterpret_cast<int64_t*>(base + off[6]),
+               words_a, words_cap_a, offsets_a, n_words_a};
+    EncPass pn{sf_n, y_n, Nn, Sn, reinterpret_cast<uint16_t*>(base + off[5]), reinterpret_cast<int64_t*>(base + off[7]),
+               words_n, words_cap_n, offsets_n, n_words_n};
+    encode2_from_intervals(pa, pn, h->d_err, h->num_sms, st);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? FGMM_OK : cuda_fail(h, e, "fgmm_ckbd_encode launch");
+}
 
 fgmm_status fgmm_ckbd_decode_plan(fgmm_handle* h, int32_t K, int32_t dtype, int64_t C, int64_t H, int64_t W,
                                   int32_t Sa, int32_t Sn, int32_t* fused)

@@ -156,19 +156,16 @@ __device__ __forceinline__ void enc_put_pre(uint32_t& x, const EncStep& e, bool 
     if (part) x = (q << 16) + rem + e.st;
 }
 
-// Software pipelined: while step k's state chain runs, step k+1's interval
-// is already in registers with its reciprocal and escape vote, step k+2's
-// interval is read from the ring and step k + kEncPF's is in flight.
-__global__ void __launch_bounds__(32) fgmm_rans_enc_kernel(const uint32_t* __restrict__ sf,
-                                                           const int32_t* __restrict__ sym, int64_t N, int32_t S,
-                                                           int64_t T, uint16_t* __restrict__ seg_words,
-                                                           int64_t seg_cap, int64_t* __restrict__ seg_len,
-                                                           int64_t nseg)
+// Segment g of one latent, by one warp. Software pipelined: while step k's
+// state chain runs, step k+1's interval is already in registers with its
+// reciprocal and escape vote, step k+2's interval is read from the ring and
+// step k + kEncPF's is in flight.
+__device__ __forceinline__ void rans_enc_segment(uint32_t (*ring)[32], const uint32_t* __restrict__ sf,
+                                                 const int32_t* __restrict__ sym, int64_t N, int32_t S, int64_t T,
+                                                 uint16_t* __restrict__ seg_words, int64_t seg_cap,
+                                                 int64_t* __restrict__ seg_len, int64_t g)
 {
-    __shared__ uint32_t ring[kEncRing][32];
-    const int64_t g = blockIdx.x;   // one warp (segment) per block
     const int lane = threadIdx.x & 31;
-    if (g >= nseg) return;
     uint16_t* out = seg_words + g * seg_cap;
     const uint32_t lt = lanemask_lt();
     uint32_t x = kL;
@@ -210,6 +207,40 @@ __global__ void __launch_bounds__(32) fgmm_rans_enc_kernel(const uint32_t* __res
     out[base + 2 * lane] = (uint16_t)(x & 0xffffu);
     out[base + 2 * lane + 1] = (uint16_t)(x >> 16);
     if (lane == 0) seg_len[g] = base + 64;
+}
+
+__global__ void __launch_bounds__(32) fgmm_rans_enc_kernel(const uint32_t* __restrict__ sf,
+                                                           const int32_t* __restrict__ sym, int64_t N, int32_t S,
+                                                           int64_t T, uint16_t* __restrict__ seg_words,
+                                                           int64_t seg_cap, int64_t* __restrict__ seg_len,
+                                                           int64_t nseg)
+{
+    __shared__ uint32_t ring[kEncRing][32];
+    const int64_t g = blockIdx.x;   // one warp (segment) per block
+    if (g >= nseg) return;
+    rans_enc_segment(ring, sf, sym, N, S, T, seg_words, seg_cap, seg_len, g);
+}
+
+// Two latents' segments in one launch (the checkerboard's two passes): the
+// first a.nseg blocks encode latent a, the rest latent b.
+struct EncLatentDev {
+    const uint32_t* sf;
+    const int32_t* sym;
+    int64_t N;
+    int32_t S;
+    int64_t T;
+    uint16_t* seg;
+    int64_t cap;
+    int64_t* len;
+    int64_t nseg;
+};
+
+__global__ void __launch_bounds__(32) fgmm_rans_enc2_kernel(EncLatentDev a, EncLatentDev b)
+{
+    __shared__ uint32_t ring[kEncRing][32];
+    const int64_t g = blockIdx.x;
+    if (g < a.nseg) rans_enc_segment(ring, a.sf, a.sym, a.N, a.S, a.T, a.seg, a.cap, a.len, g);
+    else if (g - a.nseg < b.nseg) rans_enc_segment(ring, b.sf, b.sym, b.N, b.S, b.T, b.seg, b.cap, b.len, g - a.nseg);
 }
 
 // ---------------------------------------------------------------------------
@@ -444,6 +475,24 @@ void launch_scan(const int64_t* len, int64_t nseg, int64_t* offsets, int64_t* to
 {
     fgmm_scan_kernel<<<1, 1024, 0, st>>>(len, nseg, offsets, total_out, cap, err);
 }
+
+void encode2_from_intervals(const EncPass& a, const EncPass& b, int32_t* err, int sms, cudaStream_t st)
+{
+    const EncPass* p[2] = {&a, &b};
+    EncLatentDev d[2];
+    for (int i = 0; i < 2; ++i) {
+        const int64_t nseg = p[i]->S / 32;
+        d[i] = EncLatentDev{p[i]->sf, p[i]->sym, p[i]->N, p[i]->S, steps_of(p[i]->N, p[i]->S),
+                            p[i]->seg, seg_cap_words(steps_of(p[i]->N, p[i]->S)), p[i]->len, nseg};
+    }
+    fgmm_rans_enc2_kernel<<<(unsigned)(d[0].nseg + d[1].nseg), 32, 0, st>>>(d[0], d[1]);
+    for (int i = 0; i < 2; ++i) {
+        fgmm_scan_kernel<<<1, 1024, 0, st>>>(d[i].len, d[i].nseg, p[i]->offsets, p[i]->total, p[i]->words_cap, err);
+        launch_compact(d[i].seg, d[i].cap, d[i].len, p[i]->offsets, d[i].nseg, p[i]->words, p[i]->words_cap, sms, st);
+    }
+}
+
+int64_t encode_seg_cap(int64_t N, int32_t S) { return seg_cap_words(steps_of(N, S)); }
 
 fgmm_status check_latent(fgmm_handle* h, const fgmm_latent* lat)
 {

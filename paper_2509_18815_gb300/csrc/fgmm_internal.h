@@ -67,6 +67,25 @@ struct EncodeWs {
     int64_t cap;
 };
 fgmm_status encode_reserve(fgmm_handle* h, int64_t N, int32_t S, cudaStream_t st, EncodeWs* ws);
+// One latent of a two-latent encode: its intervals (sf[n] = start | freq <<
+// 16) and symbols, S streams, segment scratch seg ([S/32][encode_seg_cap]
+// words) and lengths len ([S/32]), and the caller's outputs.
+struct EncPass {
+    const uint32_t* sf;
+    const int32_t* sym;
+    int64_t N;
+    int32_t S;
+    uint16_t* seg;
+    int64_t* len;
+    uint16_t* words;
+    int64_t words_cap;
+    int64_t* offsets;
+    int64_t* total;
+};
+int64_t encode_seg_cap(int64_t N, int32_t S);
+// rANS encode of both latents' segments in one launch, then each latent's
+// scan and compaction (the outputs of two fgmm_encode calls).
+void encode2_from_intervals(const EncPass& a, const EncPass& b, int32_t* err, int sms, cudaStream_t st);
 void encode_from_intervals(const EncodeWs& ws, const int32_t* symbols, int64_t N, int32_t S, uint16_t* words,
                            int64_t words_cap, int64_t* offsets, int64_t* n_words_out, int32_t* err, int sms,
                            cudaStream_t st);

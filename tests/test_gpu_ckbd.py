@@ -281,3 +281,73 @@ def test_fused_two_pass_decode_wait_times_out_and_recovers():
             h.check(_abi.fgmm_set_option(h.ptr, _abi.FGMM_OPT_TEST_SILENT_ARRIVALS, 2))
     finally:
         h.close()
+
+
+@pytest.mark.parametrize("phi", ["as", "logistic", "polya"])
+@pytest.mark.parametrize("K,bf16", [(1, False), (3, True), (4, False)])
+def test_two_pass_encode_in_one_call_matches_separate_calls(K, bf16, phi):
+    """fgmm_ckbd_encode (intervals of both passes in one kernel, both rANS
+    encoders in one launch) writes the same bytes as the split, the context
+    and two fgmm_encode calls, under each Phi approximation (integer output:
+    equality); with A&S both equal the oracle's streams."""
+    codec = _codec()
+    from paper_2509_18815_gb300 import _abi
+    shape, Sa, Sn = (6, 10, 14), 96, 128
+    lat = synth.make_ckbd_latent(*shape, K, seed=1040 + K)
+    lat.symbols[::37] = 70000   # escapes in both classes
+    dp, dy = dev_params(lat.params, bf16), dev_i32(lat.symbols)
+    h = codec.Handle()
+    try:
+        code = {"as": _abi.FGMM_PHI_AS, "logistic": _abi.FGMM_PHI_LOGISTIC, "polya": _abi.FGMM_PHI_POLYA}[phi]
+        h.check(_abi.fgmm_set_option(h.ptr, _abi.FGMM_OPT_PHI, code))
+        (wa, oa), (wn, on) = codec.ckbd_encode(dp, dy, shape, Sa, Sn, h=h)
+        (wa2, oa2), (wn2, on2) = codec.ckbd_encode_steps(dp, dy, shape, Sa, Sn, h=h)
+    finally:
+        h.close()
+    np.testing.assert_array_equal(host_u16(wa), host_u16(wa2))
+    np.testing.assert_array_equal(oa.cpu().numpy(), oa2.cpu().numpy())
+    np.testing.assert_array_equal(host_u16(wn), host_u16(wn2))
+    np.testing.assert_array_equal(on.cpu().numpy(), on2.cpu().numpy())
+    if phi == "as":
+        (wa_o, oa_o), (wn_o, on_o) = oracle.ckbd_encode(oracle_params(lat.params, bf16), lat.symbols, shape, Sa, Sn)
+        np.testing.assert_array_equal(host_u16(wa), wa_o)
+        np.testing.assert_array_equal(host_u16(wn), wn_o)
+
+
+def test_two_pass_encode_errors():
+    """Argument errors are refused before any launch; a words buffer too
+    small for a pass is reported as FGMM_ERR_CAPACITY; invalid parameters as
+    FGMM_ERR_BAD_PARAMS; the handle stays usable."""
+    codec = _codec()
+    from paper_2509_18815_gb300 import _abi
+    from paper_2509_18815_gb300._abi import FGMM_ERR_BAD_PARAMS, FGMM_ERR_CAPACITY, FGMM_ERR_INVALID_ARG, FgmmError
+    shape, Sa, Sn = (4, 8, 8), 64, 64
+    lat = synth.make_ckbd_latent(*shape, 3, seed=1050)
+    dp, dy = dev_params(lat.params), dev_i32(lat.symbols)
+    h = codec.handle()
+    desc = codec.latent(dp)
+    buf = torch.zeros(4096, dtype=torch.int64, device="cuda")
+    p = buf.data_ptr()
+    assert _abi.fgmm_ckbd_encode(h.ptr, ctypes.byref(desc), 4, 8, 9, dy.data_ptr(), Sa, p, 16, p, p, Sn, p, 16, p, p,
+                                 None) == FGMM_ERR_INVALID_ARG
+    assert _abi.fgmm_ckbd_encode(h.ptr, ctypes.byref(desc), 4, 8, 8, dy.data_ptr(), 48, p, 16, p, p, Sn, p, 16, p, p,
+                                 None) == FGMM_ERR_INVALID_ARG
+    assert _abi.fgmm_ckbd_encode(h.ptr, ctypes.byref(desc), 4, 8, 8, dy.data_ptr(), Sa, p, 16, None, p, Sn, p, 16,
+                                 p, p, None) == FGMM_ERR_INVALID_ARG
+    words = torch.empty(8, dtype=torch.int16, device="cuda")
+    offs = torch.empty(3, dtype=torch.int64, device="cuda")
+    tot = torch.empty(2, dtype=torch.int64, device="cuda")
+    h.check(_abi.fgmm_ckbd_encode(h.ptr, ctypes.byref(desc), 4, 8, 8, dy.data_ptr(), Sa, words.data_ptr(), 8,
+                                  offs.data_ptr(), tot.data_ptr(), Sn, words.data_ptr(), 8, offs.data_ptr(),
+                                  tot[1:].data_ptr(), None))
+    with pytest.raises(FgmmError) as e:
+        h.sync()
+    assert e.value.status == FGMM_ERR_CAPACITY
+    bad = lat.params.copy()
+    bad[2, 0, 5] = -1.0   # a non-anchor's scale (position 5 of row 0: h + w odd)
+    with pytest.raises(FgmmError) as e:
+        codec.ckbd_encode(dev_params(bad), dy, shape, Sa, Sn)
+    assert e.value.status == FGMM_ERR_BAD_PARAMS
+    (wa, oa), (wn, on) = codec.ckbd_encode(dp, dy, shape, Sa, Sn)
+    y = codec.ckbd_decode(dp, (wa, oa), (wn, on), shape, Sa, Sn)
+    np.testing.assert_array_equal(y.cpu().numpy(), lat.symbols)
