@@ -330,7 +330,7 @@ def table_batch(dev, h, b, params, syms):
     return te, td, nmax * 512 * 2
 
 
-def batch_case(dev, h, out, name, lats, alu_peak_tops, hbm_gbs, reps=5, max_overhead=0.01, table=False):
+def batch_case(dev, h, out, name, lats, alu_peak_tops, hbm_gbs, reps=10, max_overhead=0.01, table=False):
     """Batch of latents: one persistent launch per direction replayed from a
     CUDA graph, autotuned streams per latent; adds out[name]. table: also
     time the table-based comparison coder on the same batch."""
@@ -580,7 +580,7 @@ def proposal_case(dev, h, alu_peak_tops, reps=3, n_train=10_000_000, n_latents=1
                     "the network's guess with the same fast probes and exact confirmation"}
 
 
-def throughput_workloads(dev, alu_peak_tops, hbm_gbs, reps=5):
+def throughput_workloads(dev, alu_peak_tops, hbm_gbs, reps=10):
     """Larger workloads: one 320x64x96 latent (K = 3 and 4, fp32 and bf16
     parameters, autotuned stream count, FP64 rate audit), a batch of 64
     uneven K = 3 latents (one persistent launch per direction replayed from a
@@ -667,7 +667,7 @@ def throughput_workloads(dev, alu_peak_tops, hbm_gbs, reps=5):
                [synth.make_latent(C, H, W, 3, 1004 + i) for i, (C, H, W) in enumerate(shapes)], alu_peak_tops,
                hbm_gbs, reps, table=True)
 
-    out["proposal_16x320x64x96_sigma64"] = proposal_case(dev, h, alu_peak_tops, reps=3)
+    out["proposal_16x320x64x96_sigma64"] = proposal_case(dev, h, alu_peak_tops, reps=reps)
     return out
 
 
