@@ -100,6 +100,13 @@ fgmm_status fgmm_sync_status(fgmm_handle *h, void *stream);
  * Both must be 0. Synchronous; takes about a second. */
 fgmm_status fgmm_self_check(fgmm_handle *h, uint64_t *out);
 
+/* Exhaustive measurement, on the current GPU, of how far the decoders'
+ * fast steering evaluation of one component (hardware reciprocal and exp2,
+ * no clamp or grid) can be from the coded Phi-hat at the same argument:
+ * *out = the largest |fast(zs) - Phi-hat(zs)| over every float zs = z 2^22
+ * that is not a NaN. Synchronous; a few milliseconds. */
+fgmm_status fgmm_fast_phi_bound(fgmm_handle *h, double *out);
+
 /* Phi-hat (Sec. III-B, Eq. 8, A&S 26.2.17) at n points: out[i] =
  * Phi-hat(z[i]). z and out are device float arrays of length n. */
 fgmm_status fgmm_phi(fgmm_handle *h, const float *z, float *out, int64_t n, void *stream);

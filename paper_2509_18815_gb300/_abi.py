@@ -65,6 +65,7 @@ SIGNATURES = {
     "fgmm_last_error": (ctypes.c_char_p, [P]),
     "fgmm_sync_status": (I32, [P, P]),
     "fgmm_self_check": (I32, [P, P]),
+    "fgmm_fast_phi_bound": (I32, [P, P]),
     "fgmm_phi": (I32, [P, P, P, I64, P]),
     "fgmm_phi_grid": (I32, [P, I64, P, I64, P]),
     "fgmm_freqs": (I32, [P, LATP, P, P, P]),

@@ -76,6 +76,28 @@ __global__ void self_check_div_kernel(unsigned long long* bad)
     atomicAdd(bad, nb);
 }
 
+// Largest |phi_fast_s(zs) - phi_hat_s(zs)| over every float zs that is not
+// a NaN (infinities included: (b - mu) 2^22 / sigma' can overflow), as the
+// bit pattern of a non-negative double (whose order is the integers').
+__global__ void fast_phi_bound_kernel(unsigned long long* out)
+{
+    unsigned long long best = 0;
+    for (uint64_t u = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; u < (1ull << 32);
+         u += (uint64_t)gridDim.x * blockDim.x) {
+        const float zs = __uint_as_float((uint32_t)u);
+        if (zs != zs) continue;
+        const double d = fabs((double)phi_fast_s(zs) - (double)phi_hat_s(zs));
+        const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+        best = b > best ? b : best;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long v = __shfl_xor_sync(kFull, best, o);
+        best = v > best ? v : best;
+    }
+    if ((threadIdx.x & 31) == 0) atomicMax(out, best);
+}
+
 template <int PHI>
 __global__ void phi_grid_kernel(int64_t i0, float* __restrict__ out, int64_t n)
 {
@@ -644,6 +666,22 @@ fgmm_status fgmm_self_check(fgmm_handle* h, uint64_t* out)
     if (e != cudaSuccess) return cuda_fail(h, e, "fgmm_self_check");
     out[0] = v[0];
     out[1] = v[1];
+    return FGMM_OK;
+}
+
+fgmm_status fgmm_fast_phi_bound(fgmm_handle* h, double* out)
+{
+    if (!h || !out) return FGMM_ERR_INVALID_ARG;
+    unsigned long long* d = h->d_stats + 4;   // spare counter
+    cudaError_t e = cudaMemset(d, 0, sizeof(unsigned long long));
+    if (e == cudaSuccess) {
+        fast_phi_bound_kernel<<<h->num_sms * 8, 256>>>(d);
+        e = cudaDeviceSynchronize();
+    }
+    unsigned long long v = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&v, d, sizeof v, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(h, e, "fgmm_fast_phi_bound");
+    std::memcpy(out, &v, sizeof v);
     return FGMM_OK;
 }
 

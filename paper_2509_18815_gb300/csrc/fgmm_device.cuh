@@ -298,22 +298,31 @@ __device__ __forceinline__ float ex2_approx(float a)
     return y;
 }
 
-template <int K>
-__device__ __forceinline__ float mix_cdf_fast(const Mix<K>& m, float b)
+// One component of the fast evaluation at zs = z 2^22.
+__device__ __forceinline__ float phi_fast_s(float zs)
 {
     const float kP22 = 0x1.da6712p-25f;    // p 2^-22 (zs = z 2^22)
     const float kE = -0x1.715476p-45f;     // -log2(e) / 2 * 2^-44: exp(-z^2/2) = 2^(kE zs^2)
+    const float t = rcp_approx(fmaf(kP22, fabsf(zs), 1.0f));
+    float h = fmaf(0x1.0fb844p-1f, t, -0x1.7401c6p-1f);
+    h = fmaf(h, t, 0x1.6be1c6p-1f);
+    h = fmaf(h, t, -0x1.23531cp-3f);
+    h = fmaf(h, t, 0x1.04f20cp-3f);
+    const float q = ex2_approx((zs * kE) * zs) * (h * t);
+    return zs >= 0.0f ? 1.0f - q : q;
+}
+
+// The fast evaluation's zs is the exact evaluation's (the same two
+// roundings of the same operands), so the two differ only in phi_fast_s
+// against phi_hat_s.
+template <int K>
+__device__ __forceinline__ float mix_cdf_fast(const Mix<K>& m, float b)
+{
     float acc = 0.0f;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
         const float zs = (b - m.mu[k]) * m.isg[k];
-        const float t = rcp_approx(fmaf(kP22, fabsf(zs), 1.0f));
-        float h = fmaf(0x1.0fb844p-1f, t, -0x1.7401c6p-1f);
-        h = fmaf(h, t, 0x1.6be1c6p-1f);
-        h = fmaf(h, t, -0x1.23531cp-3f);
-        h = fmaf(h, t, 0x1.04f20cp-3f);
-        const float q = ex2_approx((zs * kE) * zs) * (h * t);
-        acc = fmaf(m.w[k], zs >= 0.0f ? 1.0f - q : q, acc);
+        acc = fmaf(m.w[k], phi_fast_s(zs), acc);
     }
     return acc;
 }

@@ -57,3 +57,18 @@ def test_self_check_fast_reciprocal_and_division():
     h = codec.handle()
     h.check(_abi.fgmm_self_check(h.ptr, out))
     assert out[0] == 0 and out[1] == 0
+
+
+def test_fast_steering_phi_is_within_its_measured_bound():
+    """Over every float argument (infinities included), the decoders' fast
+    steering evaluation of one component stays within 2^-21 of the coded
+    Phi-hat at the same argument (the exhaustive maximum on GB300), and is
+    not identical to it (so the sweep compared two different functions). It
+    steers the search only; the exact check decides every symbol."""
+    need_gpu()
+    import ctypes
+    from paper_2509_18815_gb300 import _abi, codec
+    out = ctypes.c_double(-1.0)
+    h = codec.handle()
+    h.check(_abi.fgmm_fast_phi_bound(h.ptr, ctypes.byref(out)))
+    assert 0.0 < out.value <= 2.0 ** -21
