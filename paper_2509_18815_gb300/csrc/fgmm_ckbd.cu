@@ -18,6 +18,11 @@
 //   m_k = fmaf(-cnt, mu_k, float(ctx)),  mu'_k = fmaf(0.125, m_k, mu_k),
 //   sigma'_k = 0.75 sigma_k,
 // each one FP32 rounding in this order.
+//
+// fgmm_ckbd_encode computes both passes' intervals in one kernel and runs
+// both rANS encoders in one launch; fgmm_ckbd_decode runs both passes in one
+// launch of the warp-specialised decoder when the plan allows, so that the
+// non-anchors decode a few steps behind the anchors they depend on.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 

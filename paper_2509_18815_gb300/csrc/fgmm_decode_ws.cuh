@@ -22,6 +22,12 @@
 // and consumers of one CTA meet at a CTA barrier once per step. Every wait
 // is bounded: a consumer that gives up records an error and raises an abort
 // flag in all CTAs, after which no wait blocks.
+//
+// A second mode decodes the checkerboard's two passes in one launch (the
+// anchors' clusters first, then the non-anchors'), with one more warp per
+// CTA that counts the anchor steps done or, for the non-anchors, waits for
+// the anchors next to its columns and loads them for the stand-in context
+// (see fgmm_dec_ws_kernel and launch_ws_ckbd_k).
 #pragma once
 
 #include "fgmm_decode_impl.cuh"
