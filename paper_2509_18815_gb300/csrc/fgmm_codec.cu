@@ -4,8 +4,9 @@
 // runs in four launches:
 //   1. fgmm_interval_kernel: one thread per symbol computes the symbol's
 //      quantised-CDF interval (start, freq). Fully data-parallel over N.
-//   2. fgmm_rans_enc_kernel: one warp per 32-stream segment, one lane per
-//      stream, steps T-1 .. 0. The sequential part is integer-only; the
+//   2. fgmm_rans_enc_kernel: one CTA per 32-stream segment, one lane per
+//      stream, steps T-1 .. 0: a warp prepares each step's interval data in
+//      shared memory, a second runs the integer state chain; the
 //      renormalisation words of a sub-phase are compacted with a warp ballot
 //      and popc rank and appended to the segment's scratch buffer.
 //   3. fgmm_scan_kernel: exclusive prefix sum of the segment lengths.
@@ -123,21 +124,8 @@ __global__ void __launch_bounds__(256) fgmm_interval_kernel(const T* __restrict_
 }
 
 // ---------------------------------------------------------------------------
-// 2. Interleaved rANS encoder, one warp per segment.
+// 2. Interleaved rANS encoder, one segment per CTA of two warps.
 // ---------------------------------------------------------------------------
-
-// Intervals reach the warp through a shared-memory ring filled by cp.async
-// kEncPF steps ahead (4 bytes per lane; zero past N), so the dependent rANS
-// chain never waits on a global load.
-constexpr int kEncRing = 8, kEncPF = 6;   // read two steps ahead: kEncPF + 2 <= kEncRing
-
-__device__ __forceinline__ void enc_stage(uint32_t* dst, const uint32_t* __restrict__ sf, int64_t n, int64_t N)
-{
-    const uint32_t s = (uint32_t)__cvta_generic_to_shared(dst);
-    const uint32_t* src = n < N ? sf + n : sf;
-    const int bytes = n < N ? 4 : 0;
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(s), "l"(src), "r"(bytes));
-}
 
 // Step values of one interval: start, freq, freq << 16 (the renormalisation
 // bound), 1/freq rounded toward zero and the escape test.
@@ -178,67 +166,106 @@ __device__ __forceinline__ void enc_put_pre(uint32_t& x, const EncStep& e, bool 
     if (part) x = (q << 16) + rem + e.st;
 }
 
-// Segment g of one latent, by one warp. Software pipelined: while step k's
-// state chain runs, step k+1's interval is already in registers with its
-// reciprocal and escape vote, step k+2's interval is read from the ring and
-// step k + kEncPF's is in flight.
-__device__ __forceinline__ void rans_enc_segment(uint32_t (*ring)[32], const uint32_t* __restrict__ sf,
+// Segment g of one latent, by a CTA of two warps. The preparing warp turns
+// each step's interval into what the rANS step needs (start | freq << 16,
+// 1/freq rounded toward zero, the escape vote of the warp, the raw symbol of
+// an escape) and stores it in shared memory, kEncBlk steps at a time, one
+// block ahead of the state warp; the state warp then runs only the state
+// update and the word compaction. The two meet at a CTA barrier once per
+// block. Steps k = 0 .. T-1 are the symbol steps T-1 .. 0.
+constexpr int kEncBlk = 16;   // steps per hand-off block
+constexpr int kEncThreads = 64;
+
+struct EncPrepSlot {
+    uint32_t sf[32];
+    float rf[32];
+    int32_t raw[32];
+};
+
+struct EncPrepRing {
+    EncPrepSlot slot[2][kEncBlk];
+    uint32_t esc[2][kEncBlk];   // escape votes (lane mask) of each step
+};
+
+__device__ __forceinline__ void rans_enc_segment(EncPrepRing& ring, const uint32_t* __restrict__ sf,
                                                  const int32_t* __restrict__ sym, int64_t N, int32_t S, int64_t T,
                                                  uint16_t* __restrict__ seg_words, int64_t seg_cap,
                                                  int64_t* __restrict__ seg_len, int64_t g)
 {
     const int lane = threadIdx.x & 31;
+    const bool prep = threadIdx.x >= 32;
+    const int64_t n_top = (T - 1) * (int64_t)S + g * 32 + lane;   // step T-1; step T-1-k is n_top - k S
+    const int64_t nblk = (T + kEncBlk - 1) / kEncBlk;
+    // preparing warp: steps b kEncBlk .. of block b into buffer b & 1
+    auto fill = [&](int64_t b) {
+        const int buf = (int)(b & 1);
+        int64_t k = b * kEncBlk;
+        uint32_t v[kEncBlk];
+#pragma unroll
+        for (int i = 0; i < kEncBlk; ++i) {
+            const int64_t n = n_top - (k + i) * S;
+            v[i] = (k + i < T && n < N) ? __ldg(sf + n) : 0u;
+        }
+#pragma unroll
+        for (int i = 0; i < kEncBlk; ++i) {
+            const int64_t n = n_top - (k + i) * S;
+            const bool act = k + i < T && n < N;
+            const uint32_t st = v[i] & 0xffffu, fr = v[i] >> 16;
+            const bool esc = act && st + fr == kM;
+            ring.slot[buf][i].sf[lane] = v[i];
+            ring.slot[buf][i].rf[lane] = __frcp_rz((float)(fr > 0u ? fr : 1u));
+            ring.slot[buf][i].raw[lane] = esc ? __ldg(sym + n) : 0;
+            const uint32_t m = __ballot_sync(kFull, esc);
+            if (lane == 0) ring.esc[buf][i] = m;
+        }
+    };
+    if (prep && nblk > 0) fill(0);
+    __syncthreads();
     uint16_t* out = seg_words + g * seg_cap;
     const uint32_t lt = lanemask_lt();
     uint32_t x = kL;
     int64_t base = 0;
-    const int64_t n_top = (T - 1) * (int64_t)S + g * 32 + lane;   // step T-1; step T-1-k is n_top - k S
-#pragma unroll
-    for (int k = 0; k < kEncPF; ++k) {
-        if (k < T) enc_stage(&ring[k % kEncRing][lane], sf, n_top - (int64_t)k * S, N);
-        asm volatile("cp.async.commit_group;\n" ::);
-    }
-    asm volatile("cp.async.wait_group %0;\n" ::"n"(kEncPF - 2));   // steps 0 and 1 resident
-    __syncwarp();
-    EncStep cur = enc_step(T > 0 ? ring[0][lane] : 0u, n_top < N);
-    bool cur_any = __ballot_sync(kFull, cur.esc) != 0u;
-    uint32_t v1 = T > 1 ? ring[1][lane] : 0u;
-#pragma unroll 2
-    for (int64_t k = 0; k < T; ++k) {
-        const int64_t n = n_top - k * S;
-        const bool act = n < N;
-        if (k + kEncPF < T) enc_stage(&ring[(k + kEncPF) % kEncRing][lane], sf, n - (int64_t)kEncPF * S, N);
-        asm volatile("cp.async.commit_group;\n" ::);
-        asm volatile("cp.async.wait_group %0;\n" ::"n"(kEncPF - 2));   // step k+2 resident
-        __syncwarp();
-        const uint32_t v2 = k + 2 < T ? ring[(k + 2) % kEncRing][lane] : 0u;
-        const EncStep nxt = enc_step(v1, n - S < N);
-        const bool nxt_any = __ballot_sync(kFull, nxt.esc) != 0u;
-        if (cur_any) {
-            const uint32_t raw = cur.esc ? (uint32_t)__ldg(sym + n) : 0u;
-            const EncStep one = enc_step(1u << 16, false);   // raw chunk: freq 1
-            enc_put_pre(x, EncStep{raw & 0xffffu, one.fr, one.fs, one.rf, false}, cur.esc, out, base, lt);
-            enc_put_pre(x, EncStep{raw >> 16, one.fr, one.fs, one.rf, false}, cur.esc, out, base, lt);
+    const bool act0 = n_top < N;   // only step T-1 (k = 0) can hold lanes past N
+    const EncStep one = enc_step(1u << 16, false);   // raw chunk: freq 1
+    for (int64_t b = 0; b < nblk; ++b) {
+        if (prep) {
+            if (b + 1 < nblk) fill(b + 1);
+        } else {
+            const int buf = (int)(b & 1);
+            const int nk = (int)min((int64_t)kEncBlk, T - b * kEncBlk);
+#pragma unroll 4
+            for (int i = 0; i < nk; ++i) {
+                const bool act = act0 || b > 0 || i > 0;
+                const uint32_t v = ring.slot[buf][i].sf[lane];
+                const float rf = ring.slot[buf][i].rf[lane];
+                const uint32_t em = ring.esc[buf][i];
+                if (em) {
+                    const bool esc = (em >> lane) & 1u;
+                    const uint32_t raw = (uint32_t)ring.slot[buf][i].raw[lane];
+                    enc_put_pre(x, EncStep{raw & 0xffffu, one.fr, one.fs, one.rf, false}, esc, out, base, lt);
+                    enc_put_pre(x, EncStep{raw >> 16, one.fr, one.fs, one.rf, false}, esc, out, base, lt);
+                }
+                const uint32_t fr = v >> 16;
+                enc_put_pre(x, EncStep{v & 0xffffu, fr, fr << 16, rf, false}, act, out, base, lt);
+            }
         }
-        enc_put_pre(x, cur, act, out, base, lt);
-        cur = nxt;
-        cur_any = nxt_any;
-        v1 = v2;
+        __syncthreads();   // block b read, block b + 1 written
     }
-    asm volatile("cp.async.wait_group 0;\n" ::);
-    out[base + 2 * lane] = (uint16_t)(x & 0xffffu);
-    out[base + 2 * lane + 1] = (uint16_t)(x >> 16);
-    if (lane == 0) seg_len[g] = base + 64;
+    if (!prep) {
+        out[base + 2 * lane] = (uint16_t)(x & 0xffffu);
+        out[base + 2 * lane + 1] = (uint16_t)(x >> 16);
+        if (lane == 0) seg_len[g] = base + 64;
+    }
 }
 
-__global__ void __launch_bounds__(32) fgmm_rans_enc_kernel(const uint32_t* __restrict__ sf,
-                                                           const int32_t* __restrict__ sym, int64_t N, int32_t S,
-                                                           int64_t T, uint16_t* __restrict__ seg_words,
-                                                           int64_t seg_cap, int64_t* __restrict__ seg_len,
-                                                           int64_t nseg)
+__global__ void __launch_bounds__(kEncThreads) fgmm_rans_enc_kernel(const uint32_t* __restrict__ sf,
+                                                                    const int32_t* __restrict__ sym, int64_t N,
+                                                                    int32_t S, int64_t T,
+                                                                    uint16_t* __restrict__ seg_words, int64_t seg_cap,
+                                                                    int64_t* __restrict__ seg_len, int64_t nseg)
 {
-    __shared__ uint32_t ring[kEncRing][32];
-    const int64_t g = blockIdx.x;   // one warp (segment) per block
+    __shared__ EncPrepRing ring;
+    const int64_t g = blockIdx.x;   // one segment per block
     if (g >= nseg) return;
     rans_enc_segment(ring, sf, sym, N, S, T, seg_words, seg_cap, seg_len, g);
 }
@@ -257,9 +284,9 @@ struct EncLatentDev {
     int64_t nseg;
 };
 
-__global__ void __launch_bounds__(32) fgmm_rans_enc2_kernel(EncLatentDev a, EncLatentDev b)
+__global__ void __launch_bounds__(kEncThreads) fgmm_rans_enc2_kernel(EncLatentDev a, EncLatentDev b)
 {
-    __shared__ uint32_t ring[kEncRing][32];
+    __shared__ EncPrepRing ring;
     const int64_t g = blockIdx.x;
     if (g < a.nseg) rans_enc_segment(ring, a.sf, a.sym, a.N, a.S, a.T, a.seg, a.cap, a.len, g);
     else if (g - a.nseg < b.nseg) rans_enc_segment(ring, b.sf, b.sym, b.N, b.S, b.T, b.seg, b.cap, b.len, g - a.nseg);
@@ -397,9 +424,6 @@ void launch_interval_any(const fgmm_latent* lat, const int32_t* sym, uint32_t* s
     else launch_interval_phi<kPhiAS>(lat, sym, sf, err, sms, st);
 }
 
-// Warps per block for the per-segment kernels: one warp per block while the
-// segments do not fill the SMs, so that each warp has an SM to itself.
-inline int seg_threads(int64_t, int) { return 32; }
 
 
 // Per-segment scratch capacity: at most three words per lane and step (an
@@ -485,8 +509,7 @@ void encode_from_intervals(const EncodeWs& ws, const int32_t* symbols, int64_t N
                            cudaStream_t st)
 {
     const int64_t nseg = S / 32, T = steps_of(N, S);
-    const int thr = seg_threads(nseg, sms);
-    fgmm_rans_enc_kernel<<<(unsigned)((nseg * 32 + thr - 1) / thr), thr, 0, st>>>(ws.sf, symbols, N, S, T, ws.seg,
+    fgmm_rans_enc_kernel<<<(unsigned)nseg, kEncThreads, 0, st>>>(ws.sf, symbols, N, S, T, ws.seg,
                                                                                   ws.cap, ws.len, nseg);
     fgmm_scan_kernel<<<1, 1024, 0, st>>>(ws.len, nseg, offsets, n_words_out, words_cap, err);
     launch_compact(ws.seg, ws.cap, ws.len, offsets, nseg, words, words_cap, sms, st);
@@ -507,7 +530,7 @@ void encode2_from_intervals(const EncPass& a, const EncPass& b, int32_t* err, in
         d[i] = EncLatentDev{p[i]->sf, p[i]->sym, p[i]->N, p[i]->S, steps_of(p[i]->N, p[i]->S),
                             p[i]->seg, seg_cap_words(steps_of(p[i]->N, p[i]->S)), p[i]->len, nseg};
     }
-    fgmm_rans_enc2_kernel<<<(unsigned)(d[0].nseg + d[1].nseg), 32, 0, st>>>(d[0], d[1]);
+    fgmm_rans_enc2_kernel<<<(unsigned)(d[0].nseg + d[1].nseg), kEncThreads, 0, st>>>(d[0], d[1]);
     for (int i = 0; i < 2; ++i) {
         fgmm_scan_kernel<<<1, 1024, 0, st>>>(d[i].len, d[i].nseg, p[i]->offsets, p[i]->total, p[i]->words_cap, err);
         launch_compact(d[i].seg, d[i].cap, d[i].len, p[i]->offsets, d[i].nseg, p[i]->words, p[i]->words_cap, sms, st);
@@ -921,8 +944,7 @@ extern "C" fgmm_status fgmm_encode_noalloc(const fgmm_latent* lat, const int32_t
         return FGMM_ERR_CUDA;
     }
     launch_interval_any(lat, symbols, sf, status_out, sms, st);
-    const int thr = seg_threads(nseg, sms);
-    fgmm_rans_enc_kernel<<<(unsigned)((nseg * 32 + thr - 1) / thr), thr, 0, st>>>(sf, symbols, N, S, T, seg, cap,
+    fgmm_rans_enc_kernel<<<(unsigned)nseg, kEncThreads, 0, st>>>(sf, symbols, N, S, T, seg, cap,
                                                                                   len, nseg);
     fgmm_scan_kernel<<<1, 1024, 0, st>>>(len, nseg, offsets, n_words_out, words_cap, status_out);
     launch_compact(seg, cap, len, offsets, nseg, words, words_cap, sms, st);
