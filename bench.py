@@ -45,17 +45,17 @@ ROTATE_SETS = 16
 # the decoder the plan names, from the ncu capture of the traffic probe
 # (profiles/traffic_roofline_kernels.md); valid for the kernel as captured
 # there (null for any other plan).
-DECODE_TRAFFIC_BYTES = {"fgmm_dec_ws_kernel/16/4/16": 10821888}   # "kernel/lanes/cluster/round0": bytes per launch
+DECODE_TRAFFIC_BYTES = {"fgmm_dec_ws_kernel/16/4/16": 10793728}   # "kernel/lanes/cluster/round0": bytes per launch
 # DRAM bytes per symbol of each roofline row's kernels (K = 3, fp32
 # parameters), from the same capture: a launch's bytes divided by its
 # symbols; rows multiply by their own symbol count. Other parameter types
 # and K were not captured (null).
 TRAFFIC_PER_SYMBOL = {
-    "encode": 44.60,                       # interval + rANS encode + scan + compaction, one latent
-    "fgmm_dec_ws_kernel": 36.68,           # warp-specialised decoder
+    "encode": 44.55,                       # interval + rANS encode + scan + compaction, one latent
+    "fgmm_dec_ws_kernel": 36.65,           # warp-specialised decoder
     "batch_encode": 40.68,                 # fgmm_batch_enc_kt_kernel + scan + batch compaction
     "fgmm_batch_dec_kt_kernel": 38.48,     # batch decoder
-    "fgmm_batch_dec_prop_kernel": 38.31,   # batched proposal decoder
+    "fgmm_batch_dec_prop_kernel": 38.26,   # batched proposal decoder
 }
 TRAFFIC_SOURCE = "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch of bench.py --traffic-probe"
 
