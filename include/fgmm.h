@@ -299,9 +299,11 @@ fgmm_status fgmm_ckbd_encode(fgmm_handle *h, const fgmm_latent *lat, int64_t C, 
  * device at once, each pass has fewer than 2^24 steps, C H W < 2^31, and
  * no decoder option or test hook is set (fgmm_ckbd_decode_plan): then one
  * launch decodes both passes, the non-anchors' streams starting as soon as
- * the anchors next to their symbols are decoded (each waiting for them is
- * bounded: FGMM_ERR_TIMEOUT from fgmm_sync_status if it runs out), with
- * the context applied as their parameters are loaded. Uses the handle's
+ * the anchors next to their symbols are decoded, with the context applied
+ * as their parameters are loaded. Each wait for anchors gives up after
+ * about 2 s (FGMM_ERR_TIMEOUT from fgmm_sync_status): work on other streams
+ * that keeps the anchor clusters off the GPU that long makes the decode
+ * fail, so give it a GPU that can hold all its clusters. Uses the handle's
  * workspace (anchor parameters, non-anchor parameters, the two passes'
  * symbols). Stream errors are reported as by fgmm_decode. */
 fgmm_status fgmm_ckbd_decode(fgmm_handle *h, const fgmm_latent *lat, int64_t C, int64_t H, int64_t W,
