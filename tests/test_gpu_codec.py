@@ -74,6 +74,21 @@ def test_escapes():
     _check_latent(lat.params, s, 128)
 
 
+@pytest.mark.parametrize("T", [2, 15, 16, 17, 31, 33])
+def test_step_counts_around_encoder_blocks_with_escapes(T):
+    """The rANS encoder's preparing warp hands steps to its state warp 16 at
+    a time: step counts on both sides of those blocks, a ragged last step,
+    and whole steps of escapes at both ends of the encode (step T-1, coded
+    first, and step 0, coded last), against the oracle."""
+    S = 64
+    N = T * S - 7
+    lat = synth.make_latent(1, 1, N, 3, seed=700 + T, escape_stress=0.05)
+    s = lat.symbols.copy()
+    s[:S] = 70000 + np.arange(S)          # step 0
+    s[(T - 1) * S:] = -70000               # step T-1 (57 symbols)
+    _check_latent(lat.params, s, S)
+
+
 def test_extreme_params():
     lat = synth.make_latent(4, 32, 32, 4, seed=301, sigma_max=64.0)
     p = lat.params.copy()
