@@ -375,6 +375,71 @@ __global__ void __launch_bounds__(256) fgmm_compact_kernel(const uint16_t* __res
 }
 
 // ---------------------------------------------------------------------------
+// 3+4. Scan and compaction in one launch, for up to kScanCompactMax
+// segments: block g sums the lengths of the segments before it (its offset)
+// and of all of them (the total), writes offsets[g] (block 0 also
+// offsets[nseg], the total and the capacity error) and copies its segment
+// when it fits: the offsets, total, error and words of fgmm_scan_kernel
+// followed by fgmm_compact_kernel, without the dependent round trips
+// between the two launches.
+// ---------------------------------------------------------------------------
+constexpr int64_t kScanCompactMax = 1024;
+
+__global__ void __launch_bounds__(256) fgmm_scan_compact_kernel(const uint16_t* __restrict__ seg_words,
+                                                                int64_t seg_cap, const int64_t* __restrict__ seg_len,
+                                                                int64_t nseg, int64_t* __restrict__ offsets,
+                                                                int64_t* total_out, uint16_t* __restrict__ words,
+                                                                int64_t cap, int32_t* err)
+{
+    __shared__ int64_t part[2][8];
+    const int64_t g = blockIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    int64_t before = 0, all = 0;
+    for (int64_t i = tid; i < nseg; i += blockDim.x) {
+        const int64_t v = seg_len[i];
+        all += v;
+        if (i < g) before += v;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        before += __shfl_xor_sync(kFull, before, o);
+        all += __shfl_xor_sync(kFull, all, o);
+    }
+    if (lane == 0) {
+        part[0][wid] = before;
+        part[1][wid] = all;
+    }
+    __syncthreads();
+    before = 0;
+    all = 0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) {
+        before += part[0][w];
+        all += part[1][w];
+    }
+    const int64_t len = seg_len[g];
+    if (tid == 0) {
+        offsets[g] = before;
+        if (g == 0) {
+            offsets[nseg] = all;
+            *total_out = all;
+            if (all > cap) set_error(err, kErrCapacity);
+        }
+    }
+    if (before + len > cap) return;   // the capacity error is recorded by block 0
+    const uint16_t* src = seg_words + g * seg_cap;
+    uint16_t* d = words + before;
+    for (int64_t i = 8 * (int64_t)tid; i < len; i += 8 * (int64_t)blockDim.x) {
+        // i + 8 <= seg_cap: segments hold a multiple of 8 words
+        const uint4 v = *reinterpret_cast<const uint4*>(src + i);
+        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int e = 0; e < 8; ++e)
+            if (i + e < len) d[i + e] = (uint16_t)(w[e >> 1] >> (16 * (e & 1)));
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Host-side dispatch helpers.
 // ---------------------------------------------------------------------------
 inline int grid_for(int64_t n, int threads, int max_blocks)
@@ -438,6 +503,21 @@ inline void launch_compact(const uint16_t* seg, int64_t cap, const int64_t* len,
     const int64_t items = nseg * ((cap + kCompactChunk - 1) / kCompactChunk);
     fgmm_compact_kernel<<<grid_for(items * 32, 256, sms * 8), 256, 0, st>>>(seg, cap, len, offsets, nseg, words,
                                                                             words_cap);
+}
+
+// Offsets, total and compaction of nseg segments: one launch for up to
+// kScanCompactMax segments, else the scan and the compaction kernels.
+inline void launch_scan_compact(const uint16_t* seg, int64_t cap, const int64_t* len, int64_t nseg,
+                                int64_t* offsets, int64_t* total, uint16_t* words, int64_t words_cap, int32_t* err,
+                                int sms, cudaStream_t st)
+{
+    if (nseg >= 1 && nseg <= kScanCompactMax) {
+        fgmm_scan_compact_kernel<<<(unsigned)nseg, 256, 0, st>>>(seg, cap, len, nseg, offsets, total, words,
+                                                                 words_cap, err);
+        return;
+    }
+    fgmm_scan_kernel<<<1, 1024, 0, st>>>(len, nseg, offsets, total, words_cap, err);
+    launch_compact(seg, cap, len, offsets, nseg, words, words_cap, sms, st);
 }
 
 }  // namespace
@@ -511,8 +591,7 @@ void encode_from_intervals(const EncodeWs& ws, const int32_t* symbols, int64_t N
     const int64_t nseg = S / 32, T = steps_of(N, S);
     fgmm_rans_enc_kernel<<<(unsigned)nseg, kEncThreads, 0, st>>>(ws.sf, symbols, N, S, T, ws.seg,
                                                                                   ws.cap, ws.len, nseg);
-    fgmm_scan_kernel<<<1, 1024, 0, st>>>(ws.len, nseg, offsets, n_words_out, words_cap, err);
-    launch_compact(ws.seg, ws.cap, ws.len, offsets, nseg, words, words_cap, sms, st);
+    launch_scan_compact(ws.seg, ws.cap, ws.len, nseg, offsets, n_words_out, words, words_cap, err, sms, st);
 }
 
 void launch_scan(const int64_t* len, int64_t nseg, int64_t* offsets, int64_t* total_out, int64_t cap, int32_t* err,
@@ -532,8 +611,8 @@ void encode2_from_intervals(const EncPass& a, const EncPass& b, int32_t* err, in
     }
     fgmm_rans_enc2_kernel<<<(unsigned)(d[0].nseg + d[1].nseg), kEncThreads, 0, st>>>(d[0], d[1]);
     for (int i = 0; i < 2; ++i) {
-        fgmm_scan_kernel<<<1, 1024, 0, st>>>(d[i].len, d[i].nseg, p[i]->offsets, p[i]->total, p[i]->words_cap, err);
-        launch_compact(d[i].seg, d[i].cap, d[i].len, p[i]->offsets, d[i].nseg, p[i]->words, p[i]->words_cap, sms, st);
+        launch_scan_compact(d[i].seg, d[i].cap, d[i].len, d[i].nseg, p[i]->offsets, p[i]->total, p[i]->words,
+                            p[i]->words_cap, err, sms, st);
     }
 }
 
