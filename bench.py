@@ -750,7 +750,9 @@ def run_fgmm(args):
     def dec():
         h.check(_abi.fgmm_decode(h.ptr, L, words.data_ptr(), cap, offsets.data_ptr(), S, out.data_ptr(), sptr))
 
-    launches_per_step = 4 + 1   # interval, rANS encode, scan, compaction; decode
+    # interval, rANS encode, scan and compaction (one launch up to 1,024
+    # segments, else two); decode
+    launches_per_step = (3 if S // 32 <= 1024 else 4) + 1
     alu_peaks = measure_alu_peaks(dev, h)
 
     # correctness gate and algorithmic work (CDF evaluations) outside timing
