@@ -351,3 +351,22 @@ def test_two_pass_encode_errors():
     (wa, oa), (wn, on) = codec.ckbd_encode(dp, dy, shape, Sa, Sn)
     y = codec.ckbd_decode(dp, (wa, oa), (wn, on), shape, Sa, Sn)
     np.testing.assert_array_equal(y.cpu().numpy(), lat.symbols)
+
+
+def test_two_pass_empty_latent():
+    """An empty latent (C = 0): the one-call encode writes each pass's flush
+    blocks, the same bytes as the separate calls, and the one-call decode
+    returns no symbols without a launch error."""
+    codec = _codec()
+    shape, Sa, Sn = (0, 4, 4), 160, 160
+    dp = torch.zeros((3, 3, 0), dtype=torch.float32, device="cuda")
+    dy = torch.zeros(0, dtype=torch.int32, device="cuda")
+    (wa, oa), (wn, on) = codec.ckbd_encode(dp, dy, shape, Sa, Sn)
+    (wa2, oa2), (wn2, on2) = codec.ckbd_encode_steps(dp, dy, shape, Sa, Sn)
+    assert wa.numel() == 64 * (Sa // 32) and wn.numel() == 64 * (Sn // 32)
+    np.testing.assert_array_equal(host_u16(wa), host_u16(wa2))
+    np.testing.assert_array_equal(host_u16(wn), host_u16(wn2))
+    np.testing.assert_array_equal(oa.cpu().numpy(), oa2.cpu().numpy())
+    np.testing.assert_array_equal(on.cpu().numpy(), on2.cpu().numpy())
+    y = codec.ckbd_decode(dp, (wa, oa), (wn, on), shape, Sa, Sn)
+    assert y.numel() == 0
